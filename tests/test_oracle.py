@@ -1,0 +1,354 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix.
+
+Nothing here compares the oracle with itself: every check uses a closed form,
+an exact special case, brute force, an independent library (numpy.fft,
+scipy.special, scipy.integrate's QUADPACK) or a number printed in the paper.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+from scipy import integrate
+from scipy.special import erf, gamma, gammainc
+
+import oracle
+from paper_1501_04438_gb300 import workloads as wl
+
+from closed_forms import (coulomb2d_gaussian, coulomb3d_gaussian, dipolar3d_gaussian,
+                          poisson2d_gaussian)
+
+GOLDEN = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_tables.json")))
+
+
+def relmax(a, b):
+    return float(np.max(np.abs(a - b)) / np.max(np.abs(b)))
+
+
+# --- Gauss-Legendre ------------------------------------------------------------
+
+def test_gauss_legendre_exact_for_polynomials():
+    for m in (5, 12, 20):
+        x, w = oracle.gauss_legendre(m)
+        for k in range(2 * m):
+            exact = 0.0 if k % 2 else 2.0 / (k + 1)
+            assert abs(np.dot(w, x ** k) - exact) < 1e-14
+
+
+# --- FFT -----------------------------------------------------------------------
+
+@pytest.mark.parametrize("n", [1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 12, 15, 16, 25, 27, 30, 32, 45, 60, 64, 81, 97, 100, 128])
+def test_fft_matches_naive_dft(n):
+    rng = np.random.default_rng(n)
+    a = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+    j = np.arange(n)
+    for sign in (-1, 1):
+        F = np.exp(sign * 2j * np.pi * np.outer(j, j) / n)
+        ref = F @ a
+        got = oracle.fftn(a, sign)
+        assert np.max(np.abs(got - ref)) <= 1e-13 * max(1.0, np.max(np.abs(ref)))
+
+
+def test_fftn_matches_numpy():
+    rng = np.random.default_rng(7)
+    for shape in [(6, 10, 8), (12, 20), (5, 9, 16)]:
+        a = rng.standard_normal(shape) + 1j * rng.standard_normal(shape)
+        assert np.max(np.abs(oracle.fftn(a, -1) - np.fft.fftn(a))) < 1e-12
+        assert np.max(np.abs(oracle.fftn(a, +1) - np.fft.ifftn(a) * a.size)) < 1e-12
+
+
+# --- Gaussian sums (Sec. 3) -----------------------------------------------------
+
+def _indep_eval(w, tau, r):
+    return np.sum(w[None, :] * np.exp(-(tau[None, :] * r[:, None]) ** 2), axis=1)
+
+
+def test_gs_coulomb_relative_error_on_interval():
+    """E_rel of Sec. 3.2 on [delta, 2 sqrt(3)] at an independent random sample."""
+    delta = 1e-3
+    w, tau, S, err = oracle.gs("coulomb3d", delta=delta)
+    rng = np.random.default_rng(1)
+    r = delta * (2 * np.sqrt(3) / delta) ** rng.uniform(0, 1, 20000)
+    e = np.max(np.abs(1.0 - r * _indep_eval(w, tau, r)))
+    assert e < 2e-15, e
+    assert err <= 1e-15 and 60 < S < 120
+
+
+def test_gs_coulomb_converges_exponentially():
+    errs = [oracle.gs("coulomb3d", S=S)[3] for S in (50, 60, 70, 80)]
+    for a, b in zip(errs, errs[1:]):
+        assert b < a / 100.0
+
+
+def test_gs_coulomb_moment():
+    """int_delta^R r^2 e^{-r^2} U_GS(r) dr = (e^{-delta^2} - e^{-R^2})/2 if U_GS = 1/r."""
+    delta, R = 1e-3, 2 * np.sqrt(3)
+    w, tau, _, _ = oracle.gs("coulomb3d", delta=delta)
+    f = lambda r: r * r * np.exp(-r * r) * float(_indep_eval(w, tau, np.array([r]))[0])
+    val, _ = integrate.quad(f, delta, R, epsabs=1e-17, epsrel=2e-14, limit=200)
+    assert abs(val - 0.5 * (np.exp(-delta ** 2) - np.exp(-R ** 2))) < 2e-14
+
+
+def test_gs_log_absolute_error_on_interval():
+    """E_abs of Sec. 3.3 for ln r on [delta, 2 sqrt(2)]."""
+    delta = 1e-3
+    w, tau, S, err = oracle.gs("poisson2d", delta=delta)
+    rng = np.random.default_rng(2)
+    r = delta * (2 * np.sqrt(2) / delta) ** rng.uniform(0, 1, 20000)
+    e = np.max(np.abs(np.log(r) - _indep_eval(w, tau, r)))
+    assert e < 1.5e-13, e
+    assert err <= 1e-13
+
+
+def test_gs_log_converges():
+    errs = [oracle.gs("poisson2d", S=S)[3] for S in (60, 100, 140, 180)]
+    for a, b in zip(errs, errs[1:]):
+        assert b < a / 5.0
+
+
+# --- 1-D factors of Eq. tensor ---------------------------------------------------
+
+def test_factor_tau_zero_is_exact():
+    # period 4: int_{-2}^{2} cos(pi k y / 2) dy = 4 delta_k0
+    assert abs(oracle.factor(0.0, 0.0) - 4.0) < 1e-15
+    for k in range(1, 40):
+        assert abs(oracle.factor(0.0, 2 * np.pi * k / 4)) < 1e-14
+    # period 6: 2 sin(2 omega)/omega
+    for k in range(1, 20):
+        om = 2 * np.pi * k / 6
+        assert abs(oracle.factor(0.0, om) - 2 * np.sin(2 * om) / om) < 1e-14
+
+
+def test_factor_zero_frequency_is_erf():
+    for tau in (0.05, 0.5, 1.0, 2.0, 3.0, 5.0, 30.0, 1000.0, 8000.0):
+        ref = np.sqrt(np.pi) * erf(2 * tau) / tau
+        assert abs(oracle.factor(tau, 0.0) - ref) <= 2e-15 * ref
+
+
+def test_factor_large_tau_is_gaussian_transform():
+    for tau in (4.0, 10.0, 100.0, 5000.0):
+        for om in (0.0, 1.0, 17.0, 150.0, 400.0):
+            ref = np.sqrt(np.pi) / tau * np.exp(-om * om / (4 * tau * tau))
+            assert abs(oracle.factor(tau, om) - ref) <= 1e-15 * np.sqrt(np.pi) / tau + 1e-15 * ref
+
+
+def test_factor_matches_quadpack_oscillatory():
+    """scipy's QUADPACK QAWO rule for cosine weights (the paper computes these
+    integrals with QUADPACK as well)."""
+    rng = np.random.default_rng(3)
+    for _ in range(40):
+        tau = rng.uniform(0.01, 4.0)
+        om = rng.uniform(0.0, 400.0)
+        val, _ = integrate.quad(lambda y: np.exp(-tau * tau * y * y), 0.0, 2.0, weight="cos", wvar=om,
+                                epsabs=1e-16, epsrel=1e-14, limit=500)
+        assert abs(oracle.factor(tau, om) - 2 * val) < 5e-14
+
+
+# --- Taylor correction coefficients (Sec. 2.3) ----------------------------------
+
+def _moment(m, tau, delta):
+    if tau == 0.0:
+        return delta ** (m + 1) / (m + 1)
+    a = (m + 1) / 2.0
+    return gamma(a) * gammainc(a, (tau * delta) ** 2) / (2.0 * tau ** (m + 1))
+
+
+@pytest.mark.parametrize("kernel", ["coulomb3d", "coulomb2d", "poisson2d"])
+def test_taylor_coefficients_incomplete_gamma(kernel):
+    """c0, c2 against the same integrals through the regularised incomplete gamma."""
+    d = oracle.KERNEL_DIM[kernel]
+    delta = 1e-3
+    w, tau, _, _ = oracle.gs(kernel, delta=delta)
+    c0, c2 = oracle.taylor_coeffs(kernel, w, tau, delta)
+    area = 4 * np.pi if d == 3 else 2 * np.pi
+    ref = []
+    for m in (d - 1, d + 1):
+        gs = sum(wq * _moment(m, tq, delta) for wq, tq in zip(w, tau))
+        if kernel == "poisson2d":
+            exact = delta ** (m + 1) * (np.log(delta) / (m + 1) - 1.0 / (m + 1) ** 2)
+        else:
+            exact = delta ** m / m
+        ref.append(exact - gs)
+    assert abs(c0 - area * ref[0]) <= 1e-9 * abs(c0)
+    assert abs(c2 - area / (2 * d) * ref[1]) <= 1e-8 * abs(c2)
+
+
+# --- I_1 pipeline ----------------------------------------------------------------
+
+def test_i1_matches_direct_sum_of_eq_I1FFT():
+    """Eq. rho_hat by an explicit trapezoid sum and Eq. I1FFT by an explicit sum
+    over all modes (O(N^2)), against the oracle's FFT path, 3D n=6 and 2D n=8."""
+    rng = np.random.default_rng(4)
+    for kernel, n, L in (("coulomb3d", 6, 1.0), ("coulomb2d", 8, 2.0), ("poisson2d", 8, 1.5)):
+        d = oracle.KERNEL_DIM[kernel]
+        rho = rng.standard_normal((n,) * d)
+        u, i1, i2, info = oracle.apply(kernel, rho, L, parts=True)
+        kh, _ = oracle.kernel_hat(kernel, n, L)
+        Nt, P, a = 2 * n, 4.0, -2.0
+        h = 2.0 / n
+        xs = -1.0 + (np.arange(n) + 1) * h              # unit-box grid points
+        ks = np.arange(-Nt // 2, Nt // 2)
+        # rho_hat_k = (1/P^d) sum_j h^d rho_j exp(-2 pi i k (x_j - a)/P)
+        E = np.exp(-2j * np.pi * np.outer(ks, xs - a) / P)   # [k, j]
+        if d == 3:
+            rh = np.einsum("aj,bk,cl,jkl->abc", E, E, E, rho[::-1, ::-1, ::-1].transpose(2, 1, 0)[::-1, ::-1, ::-1])
+        # simpler: build with index order matching rho[z][y][x]
+        if d == 3:
+            rh = np.einsum("za,yb,xc,abc->zyx", E, E, E, rho) * (h / P) ** 3
+            K = kh[np.abs(ks)[:, None, None], np.abs(ks)[None, :, None], np.abs(ks)[None, None, :]]
+            I1 = np.real(np.einsum("za,yb,xc,zyx->abc", np.conj(E), np.conj(E), np.conj(E), rh * K))
+            s = L * L / (4 * np.pi)
+        else:
+            rh = np.einsum("ya,xb,ab->yx", E, E, rho) * (h / P) ** 2
+            K = kh[np.abs(ks)[:, None], np.abs(ks)[None, :]]
+            I1 = np.real(np.einsum("ya,xb,yx->ab", np.conj(E), np.conj(E), rh * K))
+            s = L / (2 * np.pi) if kernel == "coulomb2d" else -L * L / (2 * np.pi)
+        assert relmax(i1, s * I1) < 1e-13
+
+
+def test_i1_per_term_separable_closed_form():
+    """For rho = exp(-|x|^2/sigma^2) supported in B_1, Eq. I1InteSt3 is a sum over
+    q of products of 1-D integrals int_{-2}^{2} e^{-tau^2 y^2} e^{-(x-y)^2/s^2} dy,
+    each an erf difference.  The oracle's spectral I_1 must reproduce it."""
+    L, n, sigma = 8.0, 48, 1.2
+    su = sigma / L
+    rho = wl.coulomb3d_gaussian(n, L, sigma)
+    u, i1, i2, info = oracle.apply("coulomb3d", rho, L, parts=True)
+    w, tau, _, _ = oracle.gs("coulomb3d")
+    xs = (-L + (np.arange(n) + 1) * 2 * L / n) / L
+
+    def one_d(x):
+        a = tau[:, None] ** 2 + 1.0 / su ** 2
+        b = x[None, :] / (su ** 2 * a)
+        c = (x[None, :] ** 2) * tau[:, None] ** 2 / (1.0 + tau[:, None] ** 2 * su ** 2)
+        sa = np.sqrt(a)
+        return np.exp(-c) * np.sqrt(np.pi) / (2 * sa) * (erf(sa * (2 - b)) - erf(sa * (-2 - b)))
+
+    g = one_d(xs)                      # [q, i]
+    idx = [0, 5, n // 2 - 1, n // 2, 30, n - 1]
+    s = L * L / (4 * np.pi)
+    for iz in idx:
+        for iy in idx:
+            ref = s * np.einsum("q,q,qx->x", w, g[:, iz] * g[:, iy], g)
+            assert np.max(np.abs(i1[iz, iy] - ref)) < 2e-14 * np.max(np.abs(i1))
+
+
+# --- whole evaluation against the paper's tables ----------------------------------
+
+def _table_case(kernel, entry):
+    L, n, s = entry["L"], entry["n"], entry["sigma"]
+    d = 3 if kernel.endswith("3d") or kernel == "coulomb3d_shift" else 2
+    x0 = entry.get("x0", [0, 0, 0])
+    if d == 3:
+        X, Y, Z = wl.mesh((n, n, n), L)
+        X, Y, Z = X - x0[0], Y - x0[1], Z - x0[2]
+        r = np.sqrt(X * X + Y * Y + Z * Z)
+        rho = np.exp(-r * r / s ** 2)
+        if kernel == "dipolar3d":
+            dv = GOLDEN["dipolar_vectors"]
+            return rho, dipolar3d_gaussian(X, Y, Z, s, dv["n"], dv["m"])
+        return rho, coulomb3d_gaussian(r, s)
+    X, Y = wl.mesh((n, n), L)
+    r = np.sqrt(X * X + Y * Y)
+    rho = np.exp(-r * r / s ** 2)
+    return rho, (coulomb2d_gaussian(r, s) if kernel == "coulomb2d" else poisson2d_gaussian(r, s))
+
+
+CASES = [(k, e) for k in ("coulomb3d", "coulomb3d_shift", "coulomb2d", "poisson2d", "dipolar3d") for e in GOLDEN[k]]
+
+
+@pytest.mark.parametrize("kernel,entry", CASES, ids=[f"{k}-L{e['L']}-n{e['n']}" for k, e in CASES])
+def test_paper_table(kernel, entry):
+    rho, ue = _table_case(kernel, entry)
+    okern = "coulomb3d" if kernel == "coulomb3d_shift" else kernel
+    kw = {}
+    if kernel == "dipolar3d":
+        kw = dict(dip_n=GOLDEN["dipolar_vectors"]["n"], dip_m=GOLDEN["dipolar_vectors"]["m"])
+    u, info = oracle.apply(okern, rho, entry["L"], **kw)
+    E = relmax(u, ue)
+    if entry.get("floor"):
+        # machine-precision floor: same order as the paper's
+        assert E < 30 * entry["E"], E
+    elif kernel == "dipolar3d":
+        # reading of the source derivative differs from the paper's in the
+        # under-resolved rows; magnitude only
+        assert entry["E"] / 5 < E < entry["E"] * 2, E
+    else:
+        assert abs(E - entry["E"]) <= 0.002 * entry["E"], (E, entry["E"])
+
+
+def test_config1_closed_form():
+    """3D Coulomb, [-8,8]^3, n=32, rho = exp(-|x|^2): error against the erf form
+    is the method's discretisation error at h = 1/2."""
+    rho = wl.coulomb3d_gaussian(32, 8.0, 1.0)
+    X, Y, Z = wl.mesh((32, 32, 32), 8.0)
+    ue = coulomb3d_gaussian(np.sqrt(X * X + Y * Y + Z * Z), 1.0)
+    u, _ = oracle.apply("coulomb3d", rho, 8.0)
+    E = relmax(u, ue)
+    assert 1e-8 < E < 1e-5, E
+
+
+# --- invariants ---------------------------------------------------------------------
+
+@pytest.mark.parametrize("kernel", ["coulomb3d", "coulomb2d", "poisson2d", "dipolar3d"])
+@pytest.mark.parametrize("mode", [0, 1])
+def test_linear_and_symmetric(kernel, mode):
+    d = oracle.KERNEL_DIM[kernel]
+    n = 10 if d == 3 else 24
+    rng = np.random.default_rng(5)
+    a = rng.standard_normal((n,) * d)
+    b = rng.standard_normal((n,) * d)
+    kw = dict(taylor_mode=mode, dip_n=(0.6, 0.0, 0.8), dip_m=(0.0, 1.0, 0.0))
+    # the additive ln L term of Sec. 2.1 is symmetric too: (mass a)(sum b)
+    ua, _ = oracle.apply(kernel, a, 3.0, **kw)
+    ub, _ = oracle.apply(kernel, b, 3.0, **kw)
+    uab, _ = oracle.apply(kernel, 2.0 * a - 0.5 * b, 3.0, **kw)
+    assert relmax(uab, 2.0 * ua - 0.5 * ub) < 1e-13
+    if kernel == "dipolar3d" and mode == 0:
+        # the n-grid derivative does not commute with pad-convolve-crop, so the
+        # literal dipolar operator is symmetric only for resolved densities
+        return
+    assert abs(np.dot(a.ravel(), ub.ravel()) - np.dot(ua.ravel(), b.ravel())) < 1e-12 * np.abs(a).sum() * np.abs(ub).max()
+
+
+@pytest.mark.parametrize("kernel", ["coulomb3d", "coulomb2d", "poisson2d"])
+def test_padding_2n_equals_3n_when_resolved(kernel):
+    """Remark after Eq. tensor: 4-periodic and 6-periodic extensions coincide on B_3."""
+    d = oracle.KERNEL_DIM[kernel]
+    n, L = (48, 8.0) if d == 3 else (96, 8.0)
+    rho = wl.coulomb3d_gaussian(n, L, 1.2) if d == 3 else wl.mixture((n, n), L, [(np.zeros(2), np.full(2, 1.2), 1.0)])
+    u2, _ = oracle.apply(kernel, rho, L, pad=2)
+    u3, _ = oracle.apply(kernel, rho, L, pad=3)
+    assert relmax(u3, u2) < 1e-13
+
+
+@pytest.mark.parametrize("kernel", ["coulomb3d", "coulomb2d", "poisson2d", "dipolar3d"])
+def test_folded_correction_equals_literal_when_resolved(kernel):
+    """The Laplacian of Algorithm 1 step 3 on the n-grid versus folded into the
+    padded-grid multiplier: same values for a resolved density."""
+    d = oracle.KERNEL_DIM[kernel]
+    n, L = (48, 8.0) if d == 3 else (96, 8.0)
+    rho = wl.coulomb3d_gaussian(n, L, 1.2) if d == 3 else wl.mixture((n, n), L, [(np.array([1.0, -0.5]), np.full(2, 1.2), 1.0)])
+    u0, _ = oracle.apply(kernel, rho, L, taylor_mode=0)
+    u1, _ = oracle.apply(kernel, rho, L, taylor_mode=1)
+    assert relmax(u1, u0) < 1e-13
+
+
+def test_hartree_gradient_central_differences():
+    """Gradient of E = 1/2 h^d <rho, U rho>, rho = |psi|^2, against central
+    differences with step 1e-6 in the real and imaginary parts."""
+    n, L = 8, 4.0
+    rng = np.random.default_rng(6)
+    psi = rng.standard_normal((n, n, n)) + 1j * rng.standard_normal((n, n, n))
+    E, g, _ = oracle.hartree("coulomb3d", psi, L)
+    hstep = 1e-6
+    for idx in [(0, 0, 0), (3, 4, 5), (7, 1, 2)]:
+        for unit in (1.0, 1j):
+            p = psi.copy()
+            p[idx] += hstep * unit
+            Ep = oracle.hartree("coulomb3d", p, L)[0]
+            p[idx] -= 2 * hstep * unit
+            Em = oracle.hartree("coulomb3d", p, L)[0]
+            fd = (Ep - Em) / (2 * hstep)
+            an = g[idx].real if unit == 1.0 else g[idx].imag
+            assert abs(fd - an) < 1e-7 * np.max(np.abs(g))
