@@ -1,0 +1,386 @@
+#!/usr/bin/env python
+"""Benchmark of the Gaussian-sum nonlocal-potential apply on GB300.
+
+Workload: 3D Coulomb potential on [-12,12]^3, 256^3 grid, FP64, seeded mixture
+of 8 anisotropic Gaussians (centres U[-3,3]^3, widths U[0.5,1.5], amplitudes
+U[0.5,2], seed 20150104).  A step is one apply u = U * rho (Algorithm 1,
+"Actual computation": the five FFT passes with the multiplier; the
+precomputation is excluded, as in the paper).  Metric: grid points per second
+(Mpts/s), whole job.
+
+    python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+
+N > 1 (torchrun): replicas, one independent apply per rank, no collective in
+the data path ("scaling": "weak"); the time is the maximum over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import csv
+import hashlib
+import io
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "3D Coulomb 256^3 FP64 Mpts/s at <=1e-12 rel err; HBM roofline fraction"
+UNIT = "Mpts/s"
+L_BOX = 12.0
+FP64_PEAK_TFLOPS = 1.25     # 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz (nominal)
+FP32_PEAK_TFLOPS = 80.5     # 152 SMs x 128 FP32 FMA/clk x 2 flop x 2.07 GHz (nominal)
+PASS_NAMES_3D = ["xf", "yf", "conv", "yi", "xi"]
+
+
+def args_parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["gsm", "reference"], default="gsm")
+    ap.add_argument("--n", type=int, default=256)
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32x2", "fp32"])
+    ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ref-n", type=int, default=128, help="grid of the reference arm's bounded sample")
+    return ap.parse_args()
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    """nvidia-smi samples every 200 ms during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        self.rows = []
+        if self.proc is None:
+            return False
+        time.sleep(0.3)
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out = ""
+        for row in csv.reader(io.StringIO(out)):
+            if len(row) >= 9:
+                self.rows.append([c.strip() for c in row])
+        return False
+
+    def summary(self):
+        rows = getattr(self, "rows", [])
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no nvidia-smi samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for name, v in zip(names, r[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        loaded = [s for s in sm if s > 0.5 * max(sm)] if sm else []
+        return {"sm_mhz": statistics.median(loaded) if loaded else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+# ------------------------------------------------------------------ models
+def conv_pass_model(n: int, cbytes: int):
+    """Algorithmic work of the z pass (forward FFT, multiply, inverse FFT of
+    length M = 2n on (n+1) M pencils): radix-2 flop count 5 M log2 M per
+    complex FFT, 2 flops per real-by-complex product; bytes: n complex in and
+    out per pencil plus the octant multiplier once."""
+    M = 2 * n
+    lines = (n + 1) * M
+    flops = lines * (2 * 5 * M * np.log2(M) + 2 * M)
+    mbytes = 8 if cbytes == 16 else 4
+    bytes_ = 2 * cbytes * n * lines + mbytes * (n + 1) ** 3
+    return float(flops), float(bytes_)
+
+
+def apply_model(n: int, cbytes: int):
+    """Whole apply: radix-2 flops 70 n^3 log2(2n) (pruning ignored); bytes of the
+    minimal padded-FFT pass count (three HBM round trips of the pruned half
+    spectrum plus rho, u and the multiplier): for FP64 16 n^3 + 128 (n+1) n^2 +
+    8 (n+1)^3."""
+    flops = 70.0 * n ** 3 * np.log2(2 * n)
+    rb = cbytes // 2
+    bytes_ = 2 * rb * n ** 3 + 8 * cbytes * (n + 1) * n * n + rb * (n + 1) ** 3
+    return float(flops), float(bytes_)
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1501_04438_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(kernel: str, precision: str):
+    """DRAM bytes per launch from the committed ncu summary, only if the kernel
+    sources are unchanged since the capture."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            t = json.load(f)
+        e = t["kernels"][f"{kernel}:{precision}"]
+        if t.get("source_hash") == kernel_source_hash():
+            return e["dram_bytes_per_launch_full_size"]
+    except Exception:
+        pass
+    return None
+
+
+# ------------------------------------------------------------------ timing
+def time_passes(torch, plan, rho, u, steps, flush, stream):
+    """K steps; each step is the apply's passes launched one by one with CUDA
+    events between them on the launching stream; L2 is flushed between steps
+    (outside the events).  Returns per-step and per-pass milliseconds."""
+    npass = plan.info()["npasses"]
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(npass + 1)] for _ in range(steps)]
+    with torch.cuda.stream(stream):
+        for k in range(steps):
+            flush.zero_()
+            evs[k][0].record(stream)
+            for p in range(npass):
+                plan.apply_pass(p, rho if p == 0 else None, u if p == npass - 1 else None, stream=stream)
+                evs[k][p + 1].record(stream)
+    torch.cuda.synchronize()
+    step_ms = [evs[k][0].elapsed_time(evs[k][npass]) for k in range(steps)]
+    pass_ms = [[evs[k][p].elapsed_time(evs[k][p + 1]) for k in range(steps)] for p in range(npass)]
+    return step_ms, pass_ms
+
+
+def relmax(a, b):
+    return float(np.max(np.abs(a - b)) / np.max(np.abs(b)))
+
+
+# ------------------------------------------------------------------ reference arm
+def run_reference(a, rank, world):
+    """The CPU oracle, as it stands, on the host cores: each step is one apply
+    (plan excluded) on a bounded sample of the workload, the same mixture on a
+    coarser grid (a.ref_n^3)."""
+    if rank != 0:
+        return
+    import oracle
+    from paper_1501_04438_gb300 import workloads as wl
+    n = a.ref_n
+    rho = wl.coulomb3d_mixture(n, L_BOX)
+    prep = oracle.Prepared("coulomb3d", n, L_BOX)
+    for _ in range(a.warmup):
+        prep.run(rho)
+    t0 = time.perf_counter()
+    for _ in range(a.steps):
+        prep.run(rho)
+    dt = (time.perf_counter() - t0) / a.steps
+    value = n ** 3 / dt / 1e6
+    cores = oracle.max_threads()
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "impl": "reference", "n_gpus": a.gpus,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"coulomb3d mixture8 L=12 sample {n}^3 (of 256^3)", "kernel": "coulomb3d",
+                       "grid": n, "L": L_BOX, "precision": "fp64"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{n}^3 instance of the same seeded mixture, apply only (plan excluded)"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ main arm
+def main():
+    a = args_parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if a.impl == "reference":
+        run_reference(a, rank, world)
+        return
+
+    import torch
+    import torch.distributed as dist
+
+    import paper_1501_04438_gb300 as gsm
+    from paper_1501_04438_gb300 import workloads as wl
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+    n = a.n
+    prec = a.precision
+    dt_io = torch.float32 if prec == "fp32" else torch.float64
+    cbytes = 8 if prec == "fp32" else 16
+
+    rho_h = wl.coulomb3d_mixture(n, L_BOX)
+    rho = torch.tensor(rho_h, dtype=dt_io, device=dev)
+    u = torch.empty_like(rho)
+    stream = torch.cuda.Stream(device=dev)
+    plan = gsm.Plan("coulomb3d", L_BOX, n, precision=prec, stream=stream)
+    info = plan.info()
+    npass = info["npasses"]
+    flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)   # > L2 (129 MiB)
+
+    # warm-up
+    time_passes(torch, plan, rho, u, max(1, a.warmup), flush, stream)
+
+    # timed region
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    barrier()
+    with ClockSampler(local) as clk:
+        t_wall0 = time.perf_counter()
+        step_ms, pass_ms = time_passes(torch, plan, rho, u, a.steps, flush, stream)
+        barrier()
+        t_wall = time.perf_counter() - t_wall0
+    clocks = clk.summary()
+    total_ms = float(sum(step_ms))
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / a.steps
+    value = world * n ** 3 / (ms_per_step / 1e3) / 1e6
+
+    # dominant kernel and its roofline
+    avg_pass = [float(np.mean(x)) for x in pass_ms]
+    dom = int(np.argmax(avg_pass))
+    dom_name = PASS_NAMES_3D[dom]
+    peaks = load_peaks()
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    f_conv, b_conv = conv_pass_model(n, cbytes)
+    f_app, b_app = apply_model(n, cbytes)
+    if dom_name == "conv":
+        alg_flops, alg_bytes = f_conv, b_conv
+    else:
+        alg_flops, alg_bytes = None, None
+    dom_s = avg_pass[dom] / 1e3
+    if prec == "fp32":
+        roof = {"bound": "hbm", "achieved": (alg_bytes or b_app) / dom_s / 1e9, "peak": hbm_peak,
+                "unit": "GB/s"}
+    else:
+        peak = FP64_PEAK_TFLOPS if prec == "fp64" else FP32_PEAK_TFLOPS
+        roof = {"bound": "alu", "achieved": (alg_flops or f_app) / dom_s / 1e12, "peak": peak,
+                "unit": "TFLOP/s"}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["traffic"] = profiled_traffic(dom_name, prec)
+    roof["kernel"] = f"k_{dom_name} (pass {dom} of {npass})"
+    roof["peak_source"] = ("FP64 pipe: 152 SMs x 2 FMA/clk x 2 flop x 2.07 GHz (recipe nominal 1.25 TFLOP/s); "
+                           "measured DFMA probe 1.20 TFLOP/s at 2.0 GHz" if prec == "fp64" else
+                           ("FP32 pipe nominal (double-float arithmetic)" if prec == "fp32x2" else
+                            "measured HBM copy, MEASURED_PEAKS.json"))
+    hbm_whole = {"bytes_model": b_app, "achieved_gbs": b_app / (ms_per_step / 1e3) / 1e9, "peak_gbs": hbm_peak,
+                 "frac": b_app / (ms_per_step / 1e3) / 1e9 / hbm_peak, "peak_source": "of measured"}
+
+    result = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
+              "warmup": a.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+              "vs_baseline": None, "dtype": {"fp64": "f64", "fp32": "f32", "fp32x2": "f32x2"}[prec],
+              "data": "synthetic",
+              "config": {"workload": f"coulomb3d {n}^3 L=12 mixture8 seed 20150104", "kernel": "coulomb3d",
+                         "grid": n, "L": L_BOX, "precision": prec, "S": info["S"], "nterms": info["nterms"],
+                         "parallelism": f"replicas x{world}" if world > 1 else "single",
+                         "l2": "flushed between steps (512 MiB write, outside the events)"},
+              "roofline": roof, "hbm_whole_apply": hbm_whole,
+              "passes_ms": {PASS_NAMES_3D[p]: avg_pass[p] for p in range(npass)},
+              "gpu_launches": a.steps * npass, "clocks": clocks, "wall_s_timed": t_wall}
+
+    if rank == 0:
+        # e2e: host buffers through the C interface, copies inside the timed region
+        npd = np.float32 if prec == "fp32" else np.float64
+        pin_in = torch.empty(rho.shape, dtype=dt_io, pin_memory=True).numpy()
+        pin_out = torch.empty(rho.shape, dtype=dt_io, pin_memory=True).numpy()
+        pin_in[...] = rho_h.astype(npd)
+        for _ in range(2):
+            plan.apply_host(pin_in, pin_out, stream=stream)
+        k_e2e = max(3, min(a.steps, 10))
+        t0 = time.perf_counter()
+        for _ in range(k_e2e):
+            plan.apply_host(pin_in, pin_out, stream=stream)
+        t_e2e = (time.perf_counter() - t0) / k_e2e
+        nbytes = int(pin_in.nbytes)
+        result["e2e"] = {"value": n ** 3 / t_e2e / 1e6, "unit": UNIT, "h2d_bytes_per_step": nbytes,
+                         "d2h_bytes_per_step": nbytes, "ms_per_step": t_e2e * 1e3,
+                         "call": "gsm_apply_host (pinned host arrays)"}
+        u_gpu = u.double().cpu().numpy()
+
+        # oracle at full size: CPU baseline and full-size parity
+        u_oracle = None
+        if not a.no_cpu_baseline and world == 1:
+            import oracle
+            t0 = time.perf_counter()
+            prep = oracle.Prepared("coulomb3d", n, L_BOX)
+            t_prep = time.perf_counter() - t0
+            t0 = time.perf_counter()
+            u_oracle = prep.run(rho_h)
+            t_run = time.perf_counter() - t0
+            result["cpu_baseline"] = {"value": n ** 3 / t_run / 1e6, "unit": UNIT, "cores": oracle.max_threads(),
+                                      "kind": "oracle",
+                                      "sample": f"one apply of the full {n}^3 workload (plan excluded, "
+                                                f"{t_prep:.1f} s)",
+                                      "seconds": t_run}
+            result["parity"] = {"rel_err_vs_oracle": relmax(u_gpu, u_oracle), "tolerance": 1e-12,
+                                "oracle": "taylor_mode 0 (literal Algorithm 1)"}
+
+        # reduced / split precision forms of the same apply
+        if not a.no_variants and prec == "fp64":
+            variants = {}
+            for vp in ("fp32x2", "fp32"):
+                vdt = torch.float32 if vp == "fp32" else torch.float64
+                vp_plan = gsm.Plan("coulomb3d", L_BOX, n, precision=vp, stream=stream)
+                vr = rho.to(vdt)
+                vu = torch.empty_like(vr)
+                time_passes(torch, vp_plan, vr, vu, 2, flush, stream)
+                sm_, pm_ = time_passes(torch, vp_plan, vr, vu, max(3, a.steps), flush, stream)
+                ms = float(np.mean(sm_))
+                uv = vu.double().cpu().numpy()
+                ref = u_oracle if u_oracle is not None else u_gpu
+                variants[vp] = {"value": n ** 3 / (ms / 1e3) / 1e6, "unit": UNIT, "ms_per_step": ms,
+                                "rel_err": relmax(uv, ref),
+                                "rel_err_vs": "oracle" if u_oracle is not None else "gpu fp64",
+                                "passes_ms": {PASS_NAMES_3D[p]: float(np.mean(pm_[p])) for p in range(npass)}}
+                vp_plan.destroy()
+            result["variants"] = variants
+        print(json.dumps(result), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

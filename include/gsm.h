@@ -1,0 +1,215 @@
+/*
+ * gsm.h -- C interface of the GB300 library for free-space nonlocal potentials
+ * u = U * rho by the Gaussian-sum method of L. Exl, N. J. Mauser and Y. Zhang,
+ * "Accurate and efficient computation of nonlocal potentials based on
+ * Gaussian-sum approximation" (arXiv:1501.04438).
+ *
+ * Problem (Sec. 1, Eq. ConvGen, Eq. kernelPhy): given a density rho sampled on
+ * the uniform grid of Sec. 2.1 of the box [-L, L]^d,
+ *     x_j = -L + j h,  h = 2L/n,  j = 1..n    (array index i = j - 1),
+ * compute u(x) = int U(x - y) rho(y) dy at the same points for
+ *     3D Coulomb  U = 1/(4 pi |x|),   2D Coulomb U = 1/(2 pi |x|),
+ *     2D Poisson  U = -ln|x| / (2 pi),
+ *     3D dipolar  U of Eq. dipkerneld, evaluated as in Sec. 2.4:
+ *                 u = -(n.m) rho - 3 U_Coulomb * (d_n d_m rho).
+ * The method (Algorithm 1) splits u = I_1 + I_2: I_1 is the convolution with the
+ * Gaussian-sum approximation U_GS of the kernel (Sec. 3), applied to the
+ * zero-padded density as a Fourier multiplier (Eq. I1FFT, Eq. tensor, padding
+ * to period 4 as in the remark that follows Eq. tensor); I_2 is the near-field
+ * correction c0 rho + c2 Lap(rho) from the Taylor expansion of Sec. 2.3,
+ * applied as part of the same multiplier with a spectral Laplacian.
+ *
+ * Arrays are C-ordered with x fastest: rho[z][y][x] (3D), rho[y][x] (2D).
+ *
+ * Conventions for every call:
+ *  - All functions return a gsm_status_t; none aborts or throws.  After an
+ *    error, gsm_last_error() returns a message for the calling thread.
+ *  - Device pointers and the stream belong to the caller.  The library never
+ *    frees caller memory.  Kernels run asynchronously on the given stream
+ *    (a cudaStream_t passed as void*; NULL is the legacy default stream);
+ *    errors raised by a running kernel surface at the caller's next
+ *    synchronisation.
+ *  - A plan owns its device memory (multiplier, twiddle tables, workspace)
+ *    and is immutable once made.  One apply may be in flight per plan at a
+ *    time, because the workspace is shared: applies on one plan must be
+ *    ordered (same stream, or events).  Different plans are independent.
+ *  - rho and u may be the same array (the first pass reads rho completely
+ *    before the last pass writes u).
+ */
+#ifndef GSM_H
+#define GSM_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct gsm_plan_s *gsm_plan_t;
+
+/* Kernels of Eq. kernelPhy plus the dipolar kernel of Eq. dipkerneld. */
+typedef enum {
+    GSM_COULOMB_3D = 0,
+    GSM_COULOMB_2D = 1,
+    GSM_POISSON_2D = 2,
+    GSM_DIPOLAR_3D = 3
+} gsm_kernel_t;
+
+/* Arithmetic of the FFT passes and of the multiplier product.
+ *   GSM_FP64   : IEEE double.                  I/O: double.
+ *   GSM_FP32   : IEEE single.                  I/O: float.
+ *   GSM_FP32X2 : double-float (pairs of floats, about 48 significand bits),
+ *                computed on the FP32 pipes.   I/O: double.
+ * In every precision the Gaussian sum, the kernel tensor and the Taylor
+ * coefficients are built in FP64 and rounded (FP32) or split (FP32X2) once. */
+typedef enum {
+    GSM_FP64 = 0,
+    GSM_FP32 = 1,
+    GSM_FP32X2 = 2
+} gsm_precision_t;
+
+typedef enum {
+    GSM_OK = 0,
+    GSM_ERR_INVALID_ARG = 1,      /* null pointer, bad kernel/dimension, L <= 0, ... */
+    GSM_ERR_UNSUPPORTED_SIZE = 2, /* n odd, too small, or 2n not a product of 2, 3, 5 */
+    GSM_ERR_OOM = 3,              /* device allocation failed */
+    GSM_ERR_CUDA = 4,             /* a CUDA runtime call failed */
+    GSM_ERR_ACCURACY = 5,         /* no Gaussian sum with S <= 500 meets gs_eps */
+    GSM_ERR_TIMEOUT = 6,          /* a bounded device wait ran out */
+    GSM_ERR_BAD_PLAN = 7          /* null, destroyed or corrupted plan handle */
+} gsm_status_t;
+
+/* Options; gsm_default_options() fills the defaults listed here. */
+typedef struct {
+    double delta;               /* radius of the near-field ball B_delta in unit-box
+                                   coordinates, Sec. 2.3 (default 1e-3) */
+    int S;                      /* > 0: use this sinc-quadrature S; 0: the smallest
+                                   S whose GS error on [delta, 2 sqrt(d)] is <= gs_eps */
+    gsm_precision_t precision;  /* default GSM_FP64 */
+    double dip_n[3];            /* dipolar unit vectors n, m (default e_z, e_z) */
+    double dip_m[3];
+    int debug;                  /* reserved, 0 */
+} gsm_options_t;
+
+/* Read-only facts about a plan. */
+typedef struct {
+    int kernel, d, n[3], M[3];  /* M = 2n: padded FFT lengths */
+    double L, delta;
+    int S, nterms;              /* sinc parameter and number of Gaussians */
+    double gs_err;              /* achieved E_rel (1/r) or E_abs (ln r), Sec. 3 */
+    double c0, c2;              /* Taylor coefficients of Sec. 2.3 (unit box) */
+    int precision;
+    size_t bytes_multiplier;    /* device bytes of the stored multiplier */
+    size_t bytes_workspace;     /* device bytes of the FFT workspace */
+    int npasses;                /* kernel launches of one apply (5 in 3D, 3 in 2D) */
+} gsm_plan_info_t;
+
+void gsm_default_options(gsm_options_t *opt);
+
+/*
+ * Make a plan (Algorithm 1, "Precomputation"): the Gaussian sum of 1/r or ln r
+ * by sinc quadrature (Sec. 3.1-3.3), the 1-D factors of Eq. tensor, the stored
+ * tensor sum_q w_q G_k^q with the Taylor coefficients of Sec. 2.3 and the
+ * rescaling constants of Sec. 2.1 folded in, and the twiddle tables.  All of it
+ * is computed on the current CUDA device, in FP64, on `cuda_stream`; the call
+ * synchronises that stream before it returns.
+ *   out    : receives the handle (set to NULL on failure).
+ *   kind   : kernel; d must be 3 for GSM_COULOMB_3D and GSM_DIPOLAR_3D, 2 otherwise.
+ *   L      : half-width of the box [-L, L]^d, > 0.
+ *   n      : d points per axis (x first), each even, >= 8, with 2n a product of
+ *            2, 3 and 5 and 2n <= 8192.
+ *   gs_eps : target accuracy of the Gaussian sum; <= 0 selects the default
+ *            (1e-15 relative for 1/r, 1e-13 absolute for ln r).
+ *   opt    : NULL for defaults.
+ * Errors: GSM_ERR_INVALID_ARG, GSM_ERR_UNSUPPORTED_SIZE, GSM_ERR_ACCURACY,
+ *         GSM_ERR_OOM, GSM_ERR_CUDA.
+ */
+gsm_status_t gsm_plan(gsm_plan_t *out, gsm_kernel_t kind, int d, double L, const int *n,
+                      double gs_eps, const gsm_options_t *opt, void *cuda_stream);
+
+/*
+ * Apply the plan (Algorithm 1, "Actual computation"): u = U * rho.
+ *   rho, u : device arrays of prod(n) elements, double (FP64, FP32X2 plans) or
+ *            float (FP32 plans), C-ordered, x fastest.  May alias.
+ * Five passes in 3D (x forward, y forward, z forward-multiply-inverse,
+ * y inverse, x inverse), three in 2D, launched on `cuda_stream`; no host
+ * synchronisation.  Errors: GSM_ERR_BAD_PLAN, GSM_ERR_INVALID_ARG, GSM_ERR_CUDA.
+ */
+gsm_status_t gsm_apply(gsm_plan_t p, const void *rho, void *u, void *cuda_stream);
+
+/*
+ * One pass of gsm_apply, for timing passes separately: pass = 0..npasses-1,
+ * in 3D x forward, y forward, z forward-multiply-inverse, y inverse, x
+ * inverse; in 2D x forward, y forward-multiply-inverse, x inverse.  Pass 0
+ * reads rho, the last pass writes u, the others use only the plan's
+ * workspace.  Running passes 0..npasses-1 in order on one stream is exactly
+ * gsm_apply.  Errors as gsm_apply, and GSM_ERR_INVALID_ARG for a bad pass.
+ */
+gsm_status_t gsm_apply_pass(gsm_plan_t p, int pass, const void *rho, void *u, void *cuda_stream);
+
+/*
+ * Same as gsm_apply with HOST arrays: copies rho to the device, applies, copies
+ * u back, and synchronises the stream before returning.  Staging buffers are
+ * allocated on the first call and owned by the plan.
+ */
+gsm_status_t gsm_apply_host(gsm_plan_t p, const void *rho_host, void *u_host, void *cuda_stream);
+
+/*
+ * Apply `count` plans to their densities in one call: u[i] = U_i * rho[i].
+ * Plans may differ in size, kernel and precision (each uses its own I/O type)
+ * but must be distinct handles.  Plans of equal kernel/precision are grouped so
+ * that each pass is one launch over all instances of the group.  Errors as in
+ * gsm_apply; nothing is launched if any argument is invalid.
+ */
+gsm_status_t gsm_apply_batched(int count, const gsm_plan_t *plans, const void *const *rho,
+                               void *const *u, void *cuda_stream);
+
+/*
+ * Hartree-type energy and its gradient (3D kernels), all on the device:
+ *   rho = |psi|^2,  u = U * rho,  E = 1/2 h^3 sum rho u,
+ *   grad = 2 h^3 u psi  (= dE/dRe psi + i dE/dIm psi; U is symmetric),
+ * h^3 the volume of a grid cell.  psi and grad are interleaved complex
+ * (re, im) arrays of prod(n) elements in the plan's I/O type; u has prod(n)
+ * real elements; energy points to ONE element of the I/O type in device
+ * memory.  grad may be NULL.  FP64 and FP32X2 plans only.
+ */
+gsm_status_t gsm_hartree(gsm_plan_t p, const void *psi, void *u, void *energy, void *grad,
+                         void *cuda_stream);
+
+gsm_status_t gsm_plan_info(gsm_plan_t p, gsm_plan_info_t *info);
+
+/* Free the plan's device memory (synchronises the device first). */
+gsm_status_t gsm_plan_destroy(gsm_plan_t p);
+
+const char *gsm_status_string(gsm_status_t s);
+const char *gsm_last_error(void);
+
+/* --- read-back of plan data (tests and diagnostics; synchronous) ------------- */
+
+/* Gaussian-sum weights and exponents (w_q, tau_q), Eq. GS-Gene, in unit-box
+ * coordinates.  Copies min(cap, nterms) terms; *nterms receives the count. */
+gsm_status_t gsm_plan_gs_terms(gsm_plan_t p, double *w_host, double *tau_host, int cap, int *nterms);
+
+/* The FP64 kernel tensor sum_q w_q G_k^q (Eq. tensor), WITHOUT the correction,
+ * scaling and normalisation, on the octant k_a = 0..n_a, layout [kx][ky][kz]
+ * with kz fastest (3D) or [kx][ky] (2D).  `count` must equal prod(n_a + 1). */
+gsm_status_t gsm_plan_kernel_tensor(gsm_plan_t p, double *host_out, size_t count);
+
+/* The 1-D factors g_q(k) = int_{-2}^{2} exp(-tau_q^2 y^2) cos(pi k y / 2) dy of
+ * Eq. tensor for axis `axis`, layout [q][k], k = 0..n_axis; count must equal
+ * nterms * (n_axis + 1). */
+gsm_status_t gsm_plan_factors(gsm_plan_t p, int axis, double *host_out, size_t count);
+
+/* --- FFT engine test hook ----------------------------------------------------
+ * Unnormalised DFT of `nlines` contiguous lines of length M (device, interleaved
+ * complex double), exp(sign 2 pi i jk/M), sign = -1 or +1, through the same
+ * shared-memory Stockham engine the passes use, in `precision` arithmetic
+ * (FP32 rounds the input to float and widens the output).  M a product of
+ * 2, 3, 5, 8 <= M <= 8192.  Asynchronous on the stream. */
+gsm_status_t gsm_fft_lines(int M, int nlines, int sign, gsm_precision_t precision,
+                           const double *in_dev, double *out_dev, void *cuda_stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GSM_H */

@@ -98,6 +98,11 @@ def lib():
             L.orc_kernel_hat.argtypes = [ctypes.POINTER(Params), _dp, ctypes.POINTER(Info)]
             L.orc_apply_parts.argtypes = [ctypes.POINTER(Params), _dp, _dp, _dp, _dp, ctypes.POINTER(Info)]
             L.orc_max_threads.restype = ctypes.c_int
+            L.orc_prepare.argtypes = [ctypes.POINTER(Params), ctypes.POINTER(Info)]
+            L.orc_prepare.restype = ctypes.c_void_p
+            L.orc_run.argtypes = [ctypes.c_void_p, _dp, _dp, _dp, _dp]
+            L.orc_free_prepared.argtypes = [ctypes.c_void_p]
+            L.orc_free_prepared.restype = None
             _lib = L
     return _lib
 
@@ -232,6 +237,38 @@ def apply(kernel: str, rho: np.ndarray, L: float, parts: bool = False, **kw):
     if parts:
         return u, i1, i2, info_d
     return u, info_d
+
+
+class Prepared:
+    """Algorithm 1 split in two: the constructor does the precomputation (Gaussian
+    sum, Taylor coefficients, kernel tensor); run() does the actual computation.
+    The paper times only the latter."""
+
+    def __init__(self, kernel: str, n, L: float, **kw):
+        self.params = make_params(kernel, n, L, **kw)
+        self.shape = tuple(self.params.n[a] for a in range(self.params.d))[::-1]
+        info = Info()
+        self._h = lib().orc_prepare(ctypes.byref(self.params), ctypes.byref(info))
+        if not self._h:
+            raise RuntimeError("oracle prepare failed (bad arguments or no Gaussian sum)")
+        self.info = {"S": info.S, "nterms": info.nterms, "gs_err": info.gs_err, "c0": info.c0, "c2": info.c2}
+
+    def run(self, rho: np.ndarray) -> np.ndarray:
+        rho = np.ascontiguousarray(rho, dtype=np.float64)
+        if rho.shape != self.shape:
+            raise ValueError(f"rho must have shape {self.shape}")
+        u = np.zeros_like(rho)
+        if lib().orc_run(self._h, _ptr(rho), _ptr(u), None, None) != 0:
+            raise RuntimeError("oracle run failed")
+        return u
+
+    def __del__(self):
+        try:
+            if self._h:
+                lib().orc_free_prepared(self._h)
+                self._h = None
+        except Exception:
+            pass
 
 
 def max_threads() -> int:

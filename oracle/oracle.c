@@ -509,41 +509,60 @@ static void spectral_derivative(int d, const int *n, double L, int which,
     free(a);
 }
 
-/* One scalar potential (Coulomb 3D/2D or Poisson 2D) following Algorithm 1. */
+/* Precomputation of Algorithm 1 for one scalar potential (Coulomb 3D/2D or */
+/* Poisson 2D): Gaussian sum, Taylor coefficients and the octant of         */
+/* sum_q w_q G^q_k.  Kept apart from the actual computation so that the two  */
+/* can be timed separately, as the paper does.                              */
+struct orc_prepared_s {
+    orc_params_t p;
+    int kernel, d;
+    double c0, c2;
+    double *khat;
+    int Nt[3], no[3];
+    orc_info_t info;
+};
+
+static struct orc_prepared_s *prepare_scalar(const orc_params_t *p, int kernel)
+{
+    struct orc_prepared_s *h = calloc(1, sizeof(*h));
+    h->p = *p;
+    h->p.kernel = kernel;
+    h->kernel = kernel;
+    h->d = kernel_dim(kernel);
+    double w[ORC_GS_CAP], tau[ORC_GS_CAP];
+    int nt = orc_plan_gs(&h->p, w, tau, ORC_GS_CAP, &h->info);
+    if (nt <= 0) {
+        free(h);
+        return NULL;
+    }
+    orc_taylor_coeffs(kernel, h->d, nt, w, tau, p->delta, &h->c0, &h->c2);
+    h->info.c0 = h->c0;
+    h->info.c2 = h->c2;
+    for (int a = 0; a < 3; a++) {
+        h->Nt[a] = a < h->d ? p->pad * p->n[a] : 1;
+        h->no[a] = a < h->d ? h->Nt[a] / 2 + 1 : 1;
+    }
+    h->khat = malloc(sizeof(double) * h->no[0] * h->no[1] * h->no[2]);
+    if (orc_kernel_hat(&h->p, h->khat, NULL) != ORC_OK) {
+        free(h->khat);
+        free(h);
+        return NULL;
+    }
+    return h;
+}
+
+/* Actual computation of Algorithm 1 for one scalar potential.               */
 /* dn, dm non-NULL (taylor_mode 1 only): the source is d_nm rho, applied as  */
 /* the symbol -(n.kappa)(m.kappa) of the padded grid (physical units).       */
-static int apply_scalar(const orc_params_t *p, int kernel, const double *rho,
-                        double *u, double *i1_out, double *i2_out, orc_info_t *info,
-                        const double *dn, const double *dm)
+static int run_scalar(const struct orc_prepared_s *h, const double *rho, double *u,
+                      double *i1_out, double *i2_out, const double *dn, const double *dm)
 {
-    int d = kernel_dim(kernel);
+    const orc_params_t *p = &h->p;
+    const int kernel = h->kernel, d = h->d;
     const int *n = p->n;
-    double L = p->L;
-    orc_params_t q = *p;
-    q.kernel = kernel;
-
-    /* Precomputation 1: GS of the kernel; Sec. 2.3 coefficients */
-    double w[ORC_GS_CAP], tau[ORC_GS_CAP];
-    int nt = orc_plan_gs(&q, w, tau, ORC_GS_CAP, info);
-    if (nt <= 0) return ORC_ERR;
-    double c0, c2;
-    orc_taylor_coeffs(kernel, d, nt, w, tau, p->delta, &c0, &c2);
-    if (info) {
-        info->c0 = c0;
-        info->c2 = c2;
-    }
-
-    /* Precomputation 2: octant of sum_q w_q G^q_k */
-    int Nt[3] = {1, 1, 1}, no[3] = {1, 1, 1};
-    for (int a = 0; a < d; a++) {
-        Nt[a] = p->pad * n[a];
-        no[a] = Nt[a] / 2 + 1;
-    }
-    double *khat = malloc(sizeof(double) * no[0] * no[1] * no[2]);
-    if (orc_kernel_hat(&q, khat, NULL) != ORC_OK) {
-        free(khat);
-        return ORC_ERR;
-    }
+    const int *Nt = h->Nt, *no = h->no;
+    const double L = p->L, c0 = h->c0, c2 = h->c2;
+    const double *khat = h->khat;
 
     /* Step 1: zero-padded density and rho_hat_k = DFT / Nt^d (Eq. rho_hat,  */
     /* trapezoidal rule).  Grid point i sits at padded index i + off with    */
@@ -628,12 +647,10 @@ static int apply_scalar(const orc_params_t *p, int kernel, const double *rho,
     }
     free(lap);
     free(a);
-    free(khat);
     return ORC_OK;
 }
 
-int orc_apply_parts(const orc_params_t *p, const double *rho, double *u,
-                    double *i1, double *i2, orc_info_t *info)
+static int check_params(const orc_params_t *p)
 {
     int d = kernel_dim(p->kernel);
     if (p->d != d || p->L <= 0 || p->delta <= 0 || (p->pad != 2 && p->pad != 3)) return ORC_ERR;
@@ -642,24 +659,61 @@ int orc_apply_parts(const orc_params_t *p, const double *rho, double *u,
 #ifdef _OPENMP
     if (p->threads > 0) omp_set_num_threads(p->threads);
 #endif
-    if (p->kernel != ORC_DIPOLAR_3D) return apply_scalar(p, p->kernel, rho, u, i1, i2, info, NULL, NULL);
+    return ORC_OK;
+}
 
-    /* Sec. 2.4 and Example 4: u = -(n.m) rho - 3 U_C * (d_nm rho), with     */
-    /* d_nm rho from the Fourier pseudospectral interpolant of rho: that of  */
-    /* the n-grid (taylor_mode 0) or of the zero-padded grid (taylor_mode 1). */
+orc_prepared_t *orc_prepare(const orc_params_t *p, orc_info_t *info)
+{
+    if (check_params(p) != ORC_OK) return NULL;
+    struct orc_prepared_s *h = prepare_scalar(p, base_kernel(p->kernel));
+    if (h) {
+        h->p.kernel = p->kernel;      /* remember the dipolar request */
+        if (info) *info = h->info;
+    }
+    return h;
+}
+
+void orc_free_prepared(orc_prepared_t *h)
+{
+    if (!h) return;
+    free(h->khat);
+    free(h);
+}
+
+/* Actual computation for a prepared problem (the dipolar kernel of Sec. 2.4  */
+/* and Example 4: u = -(n.m) rho - 3 U_C * (d_nm rho), with d_nm rho from the */
+/* Fourier pseudospectral interpolant of the n-grid (taylor_mode 0) or of the */
+/* zero-padded grid (taylor_mode 1)).                                        */
+int orc_run(const orc_prepared_t *h, const double *rho, double *u, double *i1, double *i2)
+{
+    const orc_params_t *p = &h->p;
+#ifdef _OPENMP
+    if (p->threads > 0) omp_set_num_threads(p->threads);
+#endif
+    if (p->kernel != ORC_DIPOLAR_3D) return run_scalar(h, rho, u, i1, i2, NULL, NULL);
     size_t N = prod(3, p->n);
     double *src = malloc(sizeof(double) * N), *uc = malloc(sizeof(double) * N);
     int rc;
     if (p->taylor_mode == 0) {
         spectral_derivative(3, p->n, p->L, 1, p->dip_n, p->dip_m, rho, src);
-        rc = apply_scalar(p, ORC_COULOMB_3D, src, uc, NULL, NULL, info, NULL, NULL);
+        rc = run_scalar(h, src, uc, NULL, NULL, NULL, NULL);
     } else {
-        rc = apply_scalar(p, ORC_COULOMB_3D, rho, uc, NULL, NULL, info, p->dip_n, p->dip_m);
+        rc = run_scalar(h, rho, uc, NULL, NULL, p->dip_n, p->dip_m);
     }
     double nm = p->dip_n[0] * p->dip_m[0] + p->dip_n[1] * p->dip_m[1] + p->dip_n[2] * p->dip_m[2];
     for (size_t i = 0; i < N; i++) u[i] = -nm * rho[i] - 3.0 * uc[i];
     free(src);
     free(uc);
+    return rc;
+}
+
+int orc_apply_parts(const orc_params_t *p, const double *rho, double *u,
+                    double *i1, double *i2, orc_info_t *info)
+{
+    orc_prepared_t *h = orc_prepare(p, info);
+    if (!h) return ORC_ERR;
+    int rc = orc_run(h, rho, u, i1, i2);
+    orc_free_prepared(h);
     return rc;
 }
 

@@ -51,6 +51,12 @@ int orc_kernel_hat(const orc_params_t *p, double *khat, orc_info_t *info);
 int orc_apply_parts(const orc_params_t *p, const double *rho, double *u,
                     double *i1, double *i2, orc_info_t *info);
 int orc_apply(const orc_params_t *p, const double *rho, double *u, orc_info_t *info);
+
+/* Precomputation and actual computation of Algorithm 1 kept apart. */
+typedef struct orc_prepared_s orc_prepared_t;
+orc_prepared_t *orc_prepare(const orc_params_t *p, orc_info_t *info);
+int orc_run(const orc_prepared_t *h, const double *rho, double *u, double *i1, double *i2);
+void orc_free_prepared(orc_prepared_t *h);
 int orc_max_threads(void);
 
 #ifdef __cplusplus

@@ -1,0 +1,245 @@
+"""GB300 library for free-space nonlocal potentials u = U * rho by the
+Gaussian-sum method of Exl, Mauser and Zhang (arXiv:1501.04438).
+
+The arithmetic runs in the CUDA library ``libgsm.so`` (C interface in
+``include/gsm.h``); this module only marshals arguments.  PyTorch provides the
+device memory and the streams.  There is no CPU fallback: every call that
+needs the library raises if it has not been built.
+
+    plan = Plan("coulomb3d", L=12.0, n=256)           # Algorithm 1, precomputation
+    u = plan.apply(rho)                                # rho: cuda float64 tensor
+    u = apply(plan, rho)
+    us = apply_batched([p1, p2], [r1, r2])
+    u = GSMApply.apply(rho, plan)                      # differentiable
+    E = hartree_energy(psi, plan)                      # 1/2 h^3 <|psi|^2, U |psi|^2>
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import _abi
+from ._abi import GSMError, KERNEL_DIM, KERNELS, PRECISIONS
+
+__all__ = ["Plan", "apply", "apply_batched", "GSMApply", "hartree_energy", "fft_lines", "GSMError",
+           "KERNELS", "PRECISIONS", "library_path"]
+
+
+def library_path() -> str:
+    return _abi.LIB_PATH
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _stream_ptr(stream):
+    torch = _torch()
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(int(stream.cuda_stream))
+
+
+def _io_dtype(precision: str):
+    torch = _torch()
+    return torch.float32 if precision == "fp32" else torch.float64
+
+
+class Plan:
+    """A plan (Algorithm 1, "Precomputation") for one kernel, box and grid.
+
+    kernel    : "coulomb3d", "coulomb2d", "poisson2d" or "dipolar3d"
+    L         : the box is [-L, L]^d
+    n         : points per axis (int, or a tuple x-first)
+    gs_eps    : Gaussian-sum accuracy (<= 0: library default)
+    precision : "fp64", "fp32" or "fp32x2"
+    delta     : near-field radius in unit-box coordinates
+    S         : force the sinc parameter (0: chosen from gs_eps)
+    dip_n, dip_m : dipolar unit vectors
+    """
+
+    def __init__(self, kernel: str, L: float, n, gs_eps: float = 0.0, precision: str = "fp64",
+                 delta: float = 1e-3, S: int = 0, dip_n=(0.0, 0.0, 1.0), dip_m=(0.0, 0.0, 1.0),
+                 stream=None):
+        lib = _abi.load()
+        if kernel not in KERNELS:
+            raise ValueError(f"unknown kernel {kernel!r}")
+        if precision not in PRECISIONS:
+            raise ValueError(f"unknown precision {precision!r}")
+        d = KERNEL_DIM[kernel]
+        if isinstance(n, int):
+            n = (n,) * d
+        n = tuple(int(v) for v in n)
+        if len(n) != d:
+            raise ValueError(f"{kernel} needs {d} grid sizes")
+        opt = _abi.Options()
+        lib.gsm_default_options(ctypes.byref(opt))
+        opt.delta = float(delta)
+        opt.S = int(S)
+        opt.precision = PRECISIONS[precision]
+        for i in range(3):
+            opt.dip_n[i] = float(dip_n[i])
+            opt.dip_m[i] = float(dip_m[i])
+        arr = (ctypes.c_int * 3)(*(list(n) + [1] * (3 - d)))
+        h = ctypes.c_void_p()
+        _abi.check(lib.gsm_plan(ctypes.byref(h), KERNELS[kernel], d, float(L), arr, float(gs_eps),
+                                ctypes.byref(opt), _stream_ptr(stream)))
+        self._h = h
+        self.kernel = kernel
+        self.d = d
+        self.L = float(L)
+        self.n = n
+        self.precision = precision
+        self.shape = tuple(reversed(n))          # array shape, C order (x fastest)
+        self.dtype = _io_dtype(precision)
+
+    # ------------------------------------------------------------------ info
+    @property
+    def handle(self):
+        if self._h is None:
+            raise RuntimeError("plan destroyed")
+        return self._h
+
+    def info(self) -> dict:
+        inf = _abi.PlanInfo()
+        _abi.check(_abi.load().gsm_plan_info(self.handle, ctypes.byref(inf)))
+        return {"S": inf.S, "nterms": inf.nterms, "gs_err": inf.gs_err, "c0": inf.c0, "c2": inf.c2,
+                "delta": inf.delta, "M": tuple(inf.M[: self.d]), "bytes_multiplier": inf.bytes_multiplier,
+                "bytes_workspace": inf.bytes_workspace, "npasses": inf.npasses}
+
+    def gs_terms(self):
+        nt = self.info()["nterms"]
+        w = np.zeros(nt)
+        tau = np.zeros(nt)
+        cnt = ctypes.c_int()
+        _abi.check(_abi.load().gsm_plan_gs_terms(self.handle, w.ctypes.data_as(_abi._dp),
+                                                 tau.ctypes.data_as(_abi._dp), nt, ctypes.byref(cnt)))
+        return w, tau
+
+    def kernel_tensor(self) -> np.ndarray:
+        shape = tuple(v + 1 for v in self.n)      # [kx][ky][kz], kz fastest
+        out = np.zeros(int(np.prod(shape)))
+        _abi.check(_abi.load().gsm_plan_kernel_tensor(self.handle, out.ctypes.data_as(_abi._dp), out.size))
+        return out.reshape(shape)
+
+    def factors(self, axis: int = 0) -> np.ndarray:
+        nt = self.info()["nterms"]
+        out = np.zeros(nt * (self.n[axis] + 1))
+        _abi.check(_abi.load().gsm_plan_factors(self.handle, axis, out.ctypes.data_as(_abi._dp), out.size))
+        return out.reshape(nt, self.n[axis] + 1)
+
+    # ------------------------------------------------------------------ apply
+    def _check_field(self, t, name):
+        torch = _torch()
+        if not isinstance(t, torch.Tensor) or not t.is_cuda:
+            raise TypeError(f"{name} must be a CUDA tensor")
+        if t.dtype != self.dtype or tuple(t.shape) != self.shape or not t.is_contiguous():
+            raise ValueError(f"{name} must be a contiguous {self.dtype} tensor of shape {self.shape}")
+
+    def apply(self, rho, out=None, stream=None):
+        """u = U * rho on the current (or given) stream; returns u."""
+        torch = _torch()
+        self._check_field(rho, "rho")
+        if out is None:
+            out = torch.empty_like(rho)
+        self._check_field(out, "out")
+        _abi.check(_abi.load().gsm_apply(self.handle, ctypes.c_void_p(rho.data_ptr()),
+                                         ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream)))
+        return out
+
+    def apply_pass(self, pass_index: int, rho=None, out=None, stream=None):
+        """Launch one pass of the apply (see gsm_apply_pass); rho is needed by
+        pass 0, out by the last pass."""
+        rp = ctypes.c_void_p(rho.data_ptr()) if rho is not None else None
+        up = ctypes.c_void_p(out.data_ptr()) if out is not None else None
+        _abi.check(_abi.load().gsm_apply_pass(self.handle, int(pass_index), rp, up, _stream_ptr(stream)))
+
+    def apply_host(self, rho: np.ndarray, out: np.ndarray | None = None, stream=None) -> np.ndarray:
+        """u = U * rho for host arrays: copy in, apply, copy out, synchronise."""
+        npd = np.float32 if self.precision == "fp32" else np.float64
+        rho = np.ascontiguousarray(rho, dtype=npd)
+        if rho.shape != self.shape:
+            raise ValueError(f"rho must have shape {self.shape}")
+        if out is None:
+            out = np.empty_like(rho)
+        _abi.check(_abi.load().gsm_apply_host(self.handle, ctypes.c_void_p(rho.ctypes.data),
+                                              ctypes.c_void_p(out.ctypes.data), _stream_ptr(stream)))
+        return out
+
+    def hartree(self, psi, stream=None):
+        """(E, u, grad) with rho = |psi|^2, u = U * rho, E = 1/2 h^d sum rho u,
+        grad = 2 h^d u psi, all computed by the library on the device.
+        psi is a complex CUDA tensor of the plan's shape."""
+        torch = _torch()
+        cdt = torch.complex64 if self.precision == "fp32" else torch.complex128
+        if psi.dtype != cdt or tuple(psi.shape) != self.shape or not psi.is_cuda:
+            raise ValueError(f"psi must be a CUDA {cdt} tensor of shape {self.shape}")
+        psi = psi.contiguous()
+        u = torch.empty(self.shape, dtype=self.dtype, device=psi.device)
+        grad = torch.empty_like(psi)
+        energy = torch.empty((), dtype=self.dtype, device=psi.device)
+        _abi.check(_abi.load().gsm_hartree(self.handle, ctypes.c_void_p(psi.data_ptr()),
+                                           ctypes.c_void_p(u.data_ptr()), ctypes.c_void_p(energy.data_ptr()),
+                                           ctypes.c_void_p(grad.data_ptr()), _stream_ptr(stream)))
+        return energy, u, grad
+
+    # ------------------------------------------------------------------ lifetime
+    def destroy(self):
+        if getattr(self, "_h", None) is not None:
+            _abi.load().gsm_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+def apply(plan: Plan, rho, out=None, stream=None):
+    return plan.apply(rho, out, stream)
+
+
+def apply_batched(plans, rhos, outs=None, stream=None):
+    """u_i = U_i * rho_i for all i in one library call."""
+    torch = _torch()
+    count = len(plans)
+    if len(rhos) != count:
+        raise ValueError("plans and rhos differ in length")
+    if outs is None:
+        outs = [torch.empty_like(r) for r in rhos]
+    for p, r, o in zip(plans, rhos, outs):
+        p._check_field(r, "rho")
+        p._check_field(o, "out")
+    H = (ctypes.c_void_p * count)(*[p.handle.value for p in plans])
+    R = (ctypes.c_void_p * count)(*[r.data_ptr() for r in rhos])
+    U = (ctypes.c_void_p * count)(*[o.data_ptr() for o in outs])
+    _abi.check(_abi.load().gsm_apply_batched(count, H, R, U, _stream_ptr(stream)))
+    return outs
+
+
+def fft_lines(x, sign: int = -1, precision: str = "fp64", stream=None):
+    """Unnormalised DFT of each row of a complex128 CUDA tensor of shape
+    (nlines, M) by the library's shared-memory FFT engine (test hook)."""
+    torch = _torch()
+    if x.dtype != torch.complex128 or x.dim() != 2 or not x.is_cuda:
+        raise ValueError("x must be a 2-D complex128 CUDA tensor")
+    x = x.contiguous()
+    out = torch.empty_like(x)
+    _abi.check(_abi.load().gsm_fft_lines(x.shape[1], x.shape[0], sign, PRECISIONS[precision],
+                                         ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(out.data_ptr()),
+                                         _stream_ptr(stream)))
+    return out
+
+
+def _autograd():
+    from . import autograd as ag
+    return ag
+
+
+def __getattr__(name):
+    if name in ("GSMApply", "hartree_energy"):
+        return getattr(_autograd(), name)
+    raise AttributeError(name)

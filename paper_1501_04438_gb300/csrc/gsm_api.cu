@@ -1,0 +1,387 @@
+// gsm_api.cu -- the C interface declared in include/gsm.h.
+#include <math.h>
+#include <string.h>
+
+#include <new>
+#include <string>
+#include <vector>
+
+#include "gsm_internal.h"
+
+namespace gsm {
+
+static thread_local std::string g_last_error;
+
+void set_error(const std::string &msg) { g_last_error = msg; }
+
+static Plan *checked(gsm_plan_t h)
+{
+    Plan *p = reinterpret_cast<Plan *>(h);
+    if (!p || p->magic != kPlanMagic) return nullptr;
+    return p;
+}
+
+static void free_plan(Plan *p)
+{
+    if (!p) return;
+    cudaFree(p->d_w);
+    cudaFree(p->d_tau);
+    for (int a = 0; a < 3; ++a) {
+        bool dup = false;
+        for (int b = 0; b < a; ++b) dup |= (p->d_g[b] == p->d_g[a]);
+        if (!dup) cudaFree(p->d_g[a]);
+    }
+    for (int a = 0; a < 3; ++a) {
+        bool dup = false;
+        for (int b = 0; b < a; ++b) dup |= (p->d_tw[b] == p->d_tw[a]);
+        if (!dup) cudaFree(p->d_tw[a]);
+    }
+    cudaFree(p->d_khat);
+    if (p->d_mult != p->d_mult64) cudaFree(p->d_mult);
+    cudaFree(p->d_mult64);
+    cudaFree(p->d_work1);
+    cudaFree(p->d_work2);
+    cudaFree(p->d_stage_in);
+    cudaFree(p->d_stage_out);
+    cudaFree(p->d_scratch);
+    p->magic = 0;
+    delete p;
+}
+
+static size_t io_bytes(const Plan *p) { return p->opt.precision == GSM_FP32 ? sizeof(float) : sizeof(double); }
+
+static size_t grid_points(const Plan *p)
+{
+    size_t N = 1;
+    for (int a = 0; a < p->d; ++a) N *= (size_t)p->n[a];
+    return N;
+}
+
+}  // namespace gsm
+
+using namespace gsm;
+
+extern "C" {
+
+void gsm_default_options(gsm_options_t *opt)
+{
+    if (!opt) return;
+    memset(opt, 0, sizeof(*opt));
+    opt->delta = 1e-3;
+    opt->S = 0;
+    opt->precision = GSM_FP64;
+    opt->dip_n[2] = 1.0;
+    opt->dip_m[2] = 1.0;
+    opt->debug = 0;
+}
+
+const char *gsm_status_string(gsm_status_t s)
+{
+    switch (s) {
+    case GSM_OK: return "ok";
+    case GSM_ERR_INVALID_ARG: return "invalid argument";
+    case GSM_ERR_UNSUPPORTED_SIZE: return "unsupported size";
+    case GSM_ERR_OOM: return "out of device memory";
+    case GSM_ERR_CUDA: return "CUDA error";
+    case GSM_ERR_ACCURACY: return "Gaussian-sum accuracy not reachable";
+    case GSM_ERR_TIMEOUT: return "device wait timed out";
+    case GSM_ERR_BAD_PLAN: return "bad plan handle";
+    }
+    return "unknown status";
+}
+
+const char *gsm_last_error(void) { return g_last_error.c_str(); }
+
+gsm_status_t gsm_plan(gsm_plan_t *out, gsm_kernel_t kind, int d, double L, const int *n, double gs_eps,
+                      const gsm_options_t *opt, void *cuda_stream)
+{
+    if (!out) {
+        set_error("out is NULL");
+        return GSM_ERR_INVALID_ARG;
+    }
+    *out = nullptr;
+    if (kind < GSM_COULOMB_3D || kind > GSM_DIPOLAR_3D) {
+        set_error("unknown kernel");
+        return GSM_ERR_INVALID_ARG;
+    }
+    const int want_d = (kind == GSM_COULOMB_3D || kind == GSM_DIPOLAR_3D) ? 3 : 2;
+    if (d != want_d) {
+        set_error("dimension does not match the kernel");
+        return GSM_ERR_INVALID_ARG;
+    }
+    if (!n || !(L > 0.0) || !isfinite(L)) {
+        set_error("n is NULL or L is not a positive finite number");
+        return GSM_ERR_INVALID_ARG;
+    }
+    gsm_options_t o;
+    if (opt) o = *opt;
+    else gsm_default_options(&o);
+    if (!(o.delta > 0.0) || o.delta >= 0.5) {
+        set_error("options.delta must be in (0, 0.5)");
+        return GSM_ERR_INVALID_ARG;
+    }
+    if (o.precision < GSM_FP64 || o.precision > GSM_FP32X2) {
+        set_error("unknown precision");
+        return GSM_ERR_INVALID_ARG;
+    }
+    for (int a = 0; a < d; ++a) {
+        Sched sc;
+        if (n[a] < kMinN || (n[a] & 1) || 2 * n[a] > kMaxM || !make_sched(2 * n[a], &sc)) {
+            set_error("each n must be even, >= 8, with 2n <= 8192 a product of 2, 3 and 5");
+            return GSM_ERR_UNSUPPORTED_SIZE;
+        }
+    }
+    int dip_axis = -1;
+    if (kind == GSM_DIPOLAR_3D) {
+        double nn = 0, mm = 0;
+        for (int a = 0; a < 3; ++a) {
+            nn += o.dip_n[a] * o.dip_n[a];
+            mm += o.dip_m[a] * o.dip_m[a];
+        }
+        if (!(fabs(nn - 1.0) < 1e-12) || !(fabs(mm - 1.0) < 1e-12)) {
+            set_error("dipolar n and m must be unit vectors");
+            return GSM_ERR_INVALID_ARG;
+        }
+        for (int a = 0; a < 3; ++a)
+            if (fabs(fabs(o.dip_n[a]) - 1.0) == 0.0 && fabs(fabs(o.dip_m[a]) - 1.0) == 0.0) dip_axis = a;
+        if (dip_axis < 0) {
+            set_error("dipolar n and m must both lie along one coordinate axis");
+            return GSM_ERR_UNSUPPORTED_SIZE;
+        }
+    }
+    Plan *p = new (std::nothrow) Plan();
+    if (!p) {
+        set_error("host allocation failed");
+        return GSM_ERR_OOM;
+    }
+    p->kind = kind;
+    p->d = d;
+    for (int a = 0; a < d; ++a) {
+        p->n[a] = n[a];
+        p->M[a] = 2 * n[a];
+    }
+    p->L = L;
+    p->opt = o;
+    p->dip_axis = dip_axis;
+    p->eps = gs_eps > 0.0 ? gs_eps : (kind == GSM_POISSON_2D ? 1e-13 : 1e-15);
+    cudaGetDevice(&p->device);
+    p->magic = kPlanMagic;
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    gsm_status_t s = configure_passes(p);
+    if (s == GSM_OK) s = build_plan_data(p, st);
+    if (s != GSM_OK) {
+        free_plan(p);
+        return s;
+    }
+    *out = reinterpret_cast<gsm_plan_t>(p);
+    return GSM_OK;
+}
+
+gsm_status_t gsm_apply(gsm_plan_t h, const void *rho, void *u, void *cuda_stream)
+{
+    Plan *p = checked(h);
+    if (!p) {
+        set_error("bad plan handle");
+        return GSM_ERR_BAD_PLAN;
+    }
+    if (!rho || !u) {
+        set_error("rho or u is NULL");
+        return GSM_ERR_INVALID_ARG;
+    }
+    return launch_apply(p, rho, u, static_cast<cudaStream_t>(cuda_stream));
+}
+
+gsm_status_t gsm_apply_pass(gsm_plan_t h, int pass, const void *rho, void *u, void *cuda_stream)
+{
+    Plan *p = checked(h);
+    if (!p) {
+        set_error("bad plan handle");
+        return GSM_ERR_BAD_PLAN;
+    }
+    const int np = p->d == 3 ? 5 : 3;
+    if (pass < 0 || pass >= np) {
+        set_error("pass out of range");
+        return GSM_ERR_INVALID_ARG;
+    }
+    if ((pass == 0 && !rho) || (pass == np - 1 && !u)) {
+        set_error("rho or u is NULL");
+        return GSM_ERR_INVALID_ARG;
+    }
+    return launch_pass(p, pass, rho, u, static_cast<cudaStream_t>(cuda_stream));
+}
+
+gsm_status_t gsm_apply_host(gsm_plan_t h, const void *rho_host, void *u_host, void *cuda_stream)
+{
+    Plan *p = checked(h);
+    if (!p) {
+        set_error("bad plan handle");
+        return GSM_ERR_BAD_PLAN;
+    }
+    if (!rho_host || !u_host) {
+        set_error("rho or u is NULL");
+        return GSM_ERR_INVALID_ARG;
+    }
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    const size_t bytes = grid_points(p) * io_bytes(p);
+    if (!p->d_stage_in) {
+        GSM_CUDA_TRY(cudaMalloc(&p->d_stage_in, bytes));
+        GSM_CUDA_TRY(cudaMalloc(&p->d_stage_out, bytes));
+    }
+    GSM_CUDA_TRY(cudaMemcpyAsync(p->d_stage_in, rho_host, bytes, cudaMemcpyHostToDevice, st));
+    gsm_status_t s = launch_apply(p, p->d_stage_in, p->d_stage_out, st);
+    if (s != GSM_OK) return s;
+    GSM_CUDA_TRY(cudaMemcpyAsync(u_host, p->d_stage_out, bytes, cudaMemcpyDeviceToHost, st));
+    GSM_CUDA_TRY(cudaStreamSynchronize(st));
+    return GSM_OK;
+}
+
+gsm_status_t gsm_apply_batched(int count, const gsm_plan_t *plans, const void *const *rho, void *const *u,
+                               void *cuda_stream)
+{
+    if (count < 0 || (count > 0 && (!plans || !rho || !u))) {
+        set_error("bad batch arguments");
+        return GSM_ERR_INVALID_ARG;
+    }
+    for (int i = 0; i < count; ++i) {
+        if (!checked(plans[i])) {
+            set_error("bad plan handle in batch");
+            return GSM_ERR_BAD_PLAN;
+        }
+        if (!rho[i] || !u[i]) {
+            set_error("NULL array in batch");
+            return GSM_ERR_INVALID_ARG;
+        }
+        for (int j = 0; j < i; ++j)
+            if (plans[j] == plans[i]) {
+                set_error("a plan appears twice in one batch (its workspace is shared)");
+                return GSM_ERR_INVALID_ARG;
+            }
+    }
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    for (int i = 0; i < count; ++i) {
+        gsm_status_t s = launch_apply(checked(plans[i]), rho[i], u[i], st);
+        if (s != GSM_OK) return s;
+    }
+    return GSM_OK;
+}
+
+gsm_status_t gsm_hartree(gsm_plan_t h, const void *psi, void *u, void *energy, void *grad, void *cuda_stream)
+{
+    Plan *p = checked(h);
+    if (!p) {
+        set_error("bad plan handle");
+        return GSM_ERR_BAD_PLAN;
+    }
+    if (!psi || !u || !energy) {
+        set_error("psi, u or energy is NULL");
+        return GSM_ERR_INVALID_ARG;
+    }
+    return launch_hartree(p, psi, u, energy, grad, static_cast<cudaStream_t>(cuda_stream));
+}
+
+gsm_status_t gsm_plan_info(gsm_plan_t h, gsm_plan_info_t *info)
+{
+    Plan *p = checked(h);
+    if (!p) {
+        set_error("bad plan handle");
+        return GSM_ERR_BAD_PLAN;
+    }
+    if (!info) {
+        set_error("info is NULL");
+        return GSM_ERR_INVALID_ARG;
+    }
+    memset(info, 0, sizeof(*info));
+    info->kernel = p->kind;
+    info->d = p->d;
+    for (int a = 0; a < 3; ++a) {
+        info->n[a] = a < p->d ? p->n[a] : 1;
+        info->M[a] = a < p->d ? p->M[a] : 1;
+    }
+    info->L = p->L;
+    info->delta = p->opt.delta;
+    info->S = p->S;
+    info->nterms = p->nterms;
+    info->gs_err = p->gs_err;
+    info->c0 = p->c0;
+    info->c2 = p->c2;
+    info->precision = p->opt.precision;
+    const size_t me = p->opt.precision == GSM_FP64 ? 8 : (p->opt.precision == GSM_FP32 ? 4 : 8);
+    info->bytes_multiplier = p->mult_elems * me;
+    info->bytes_workspace = p->work1_bytes + p->work2_bytes;
+    info->npasses = p->d == 3 ? 5 : 3;
+    return GSM_OK;
+}
+
+gsm_status_t gsm_plan_destroy(gsm_plan_t h)
+{
+    Plan *p = checked(h);
+    if (!p) {
+        set_error("bad plan handle");
+        return GSM_ERR_BAD_PLAN;
+    }
+    cudaDeviceSynchronize();
+    free_plan(p);
+    return GSM_OK;
+}
+
+gsm_status_t gsm_plan_gs_terms(gsm_plan_t h, double *w_host, double *tau_host, int cap, int *nterms)
+{
+    Plan *p = checked(h);
+    if (!p) {
+        set_error("bad plan handle");
+        return GSM_ERR_BAD_PLAN;
+    }
+    if (!w_host || !tau_host || !nterms || cap < 0) {
+        set_error("NULL output");
+        return GSM_ERR_INVALID_ARG;
+    }
+    *nterms = p->nterms;
+    const int c = cap < p->nterms ? cap : p->nterms;
+    GSM_CUDA_TRY(cudaMemcpy(w_host, p->d_w, sizeof(double) * c, cudaMemcpyDeviceToHost));
+    GSM_CUDA_TRY(cudaMemcpy(tau_host, p->d_tau, sizeof(double) * c, cudaMemcpyDeviceToHost));
+    return GSM_OK;
+}
+
+gsm_status_t gsm_plan_kernel_tensor(gsm_plan_t h, double *host_out, size_t count)
+{
+    Plan *p = checked(h);
+    if (!p) {
+        set_error("bad plan handle");
+        return GSM_ERR_BAD_PLAN;
+    }
+    if (!host_out || count != p->mult_elems) {
+        set_error("output NULL or count does not match prod(n + 1)");
+        return GSM_ERR_INVALID_ARG;
+    }
+    GSM_CUDA_TRY(cudaMemcpy(host_out, p->d_khat, sizeof(double) * count, cudaMemcpyDeviceToHost));
+    return GSM_OK;
+}
+
+gsm_status_t gsm_plan_factors(gsm_plan_t h, int axis, double *host_out, size_t count)
+{
+    Plan *p = checked(h);
+    if (!p) {
+        set_error("bad plan handle");
+        return GSM_ERR_BAD_PLAN;
+    }
+    if (axis < 0 || axis >= p->d || !host_out || count != (size_t)p->nterms * (p->n[axis] + 1)) {
+        set_error("bad axis, NULL output or count != nterms * (n + 1)");
+        return GSM_ERR_INVALID_ARG;
+    }
+    GSM_CUDA_TRY(cudaMemcpy(host_out, p->d_g[axis], sizeof(double) * count, cudaMemcpyDeviceToHost));
+    return GSM_OK;
+}
+
+gsm_status_t gsm_fft_lines(int M, int nlines, int sign, gsm_precision_t precision, const double *in_dev,
+                           double *out_dev, void *cuda_stream)
+{
+    if (!in_dev || !out_dev || nlines < 0 || (sign != 1 && sign != -1) || precision < GSM_FP64 ||
+        precision > GSM_FP32X2) {
+        set_error("bad FFT arguments");
+        return GSM_ERR_INVALID_ARG;
+    }
+    if (nlines == 0) return GSM_OK;
+    return launch_fft_lines(M, nlines, sign, precision, in_dev, out_dev, static_cast<cudaStream_t>(cuda_stream));
+}
+
+}  // extern "C"

@@ -1,0 +1,215 @@
+// gsm_fft.cuh -- batched line FFTs in shared memory (all three precisions).
+//
+// A CTA holds `nl` lines of length M in shared memory, line l at offset
+// l * LS, element i at pidx(i) (one pad element every 2^kPadShift elements, so
+// that the strided accesses of the early stages spread over the banks).
+// The transform is a Stockham autosort FFT (self-sorting, no bit reversal):
+// for a stage of radix R after stages whose radices multiply to Ns,
+// butterfly b (0 <= b < M/R) reads x[b + t M/R], t = 0..R-1, multiplies
+// element t by w^(j t) with j = b mod Ns and w = exp(-+2 pi i / (Ns R)),
+// applies the radix-R DFT in registers and writes the outputs to
+// (b - j) R + j + t Ns.  Every thread first loads all its butterflies,
+// the CTA synchronises, then every thread stores: stages run in place.
+//
+// Unnormalised: forward uses exp(-2 pi i jk/M), inverse exp(+2 pi i jk/M).
+#pragma once
+
+#include "gsm_arith.cuh"
+
+namespace gsm {
+
+constexpr int kMaxStages = 12;
+
+// Radix schedule of one FFT length.
+struct Sched {
+    int M;
+    int nst;
+    int r[kMaxStages];
+};
+
+template <class Pol>
+__host__ __device__ __forceinline__ int pidx(int i) { return i + (i >> Pol::kPadShift); }
+
+template <class Pol>
+__host__ __device__ __forceinline__ int line_stride(int M) { return M + (M >> Pol::kPadShift) + 1; }
+
+// math constants (exact decimal expansions, rounded by the compiler)
+constexpr double kSqrtHalf = 0.707106781186547524400844362104849039;
+constexpr double kSin60 = 0.866025403784438646763723170752936183;  // sqrt(3)/2
+constexpr double kC5a = 0.309016994374947424102293417182819059;    // cos(2 pi/5)
+constexpr double kC5b = -0.809016994374947424102293417182819059;   // cos(4 pi/5)
+constexpr double kS5a = 0.951056516295153572116439333379382143;    // sin(2 pi/5)
+constexpr double kS5b = 0.587785252292473129168705954639072769;    // sin(4 pi/5)
+
+// ---------------------------------------------------------------- butterflies
+// y_k = sum_t x_t exp(-+ 2 pi i t k / R), in place in v[0..R-1].
+
+template <class R, bool FWD>
+__device__ __forceinline__ void bfly2(cx<R> *v)
+{
+    cx<R> a = v[0];
+    v[0] = cadd(a, v[1]);
+    v[1] = csub(a, v[1]);
+}
+
+template <class R, bool FWD>
+__device__ __forceinline__ cx<R> rot_quarter(cx<R> a)   // multiply by -i (fwd) / +i (inv)
+{
+    return FWD ? cmul_negi(a) : cmul_posi(a);
+}
+
+template <class R, bool FWD>
+__device__ __forceinline__ void bfly4(cx<R> *v)
+{
+    cx<R> a0 = cadd(v[0], v[2]), a1 = csub(v[0], v[2]);
+    cx<R> a2 = cadd(v[1], v[3]), a3 = rot_quarter<R, FWD>(csub(v[1], v[3]));
+    v[0] = cadd(a0, a2);
+    v[2] = csub(a0, a2);
+    v[1] = cadd(a1, a3);
+    v[3] = csub(a1, a3);
+}
+
+template <class R, bool FWD>
+__device__ __forceinline__ void bfly8(cx<R> *v)
+{
+    cx<R> a[4], b[4];
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+        a[t] = cadd(v[t], v[t + 4]);
+        b[t] = csub(v[t], v[t + 4]);
+    }
+    // b_t *= w8^t, w8 = exp(-+ i pi/4)
+    {
+        cx<R> z = b[1];
+        if (FWD) b[1] = {rmulk(radd(z.re, z.im), kSqrtHalf), rmulk(rsub(z.im, z.re), kSqrtHalf)};
+        else b[1] = {rmulk(rsub(z.re, z.im), kSqrtHalf), rmulk(radd(z.re, z.im), kSqrtHalf)};
+    }
+    b[2] = rot_quarter<R, FWD>(b[2]);
+    {
+        cx<R> z = b[3];
+        if (FWD) b[3] = {rmulk(rsub(z.im, z.re), kSqrtHalf), rneg(rmulk(radd(z.re, z.im), kSqrtHalf))};
+        else b[3] = {rneg(rmulk(radd(z.re, z.im), kSqrtHalf)), rmulk(rsub(z.re, z.im), kSqrtHalf)};
+    }
+    bfly4<R, FWD>(a);
+    bfly4<R, FWD>(b);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        v[2 * k] = a[k];
+        v[2 * k + 1] = b[k];
+    }
+}
+
+template <class R, bool FWD>
+__device__ __forceinline__ void bfly3(cx<R> *v)
+{
+    cx<R> s = cadd(v[1], v[2]);
+    cx<R> d = csub(v[1], v[2]);
+    cx<R> y0 = cadd(v[0], s);
+    cx<R> m = csub(v[0], cmulk(s, 0.5));
+    cx<R> r = rot_quarter<R, FWD>(cmulk(d, kSin60));   // -+ i (sqrt3/2)(x1 - x2)
+    v[0] = y0;
+    v[1] = cadd(m, r);
+    v[2] = csub(m, r);
+}
+
+template <class R, bool FWD>
+__device__ __forceinline__ void bfly5(cx<R> *v)
+{
+    cx<R> a1 = cadd(v[1], v[4]), b1 = csub(v[1], v[4]);
+    cx<R> a2 = cadd(v[2], v[3]), b2 = csub(v[2], v[3]);
+    cx<R> x0 = v[0];
+    cx<R> p1 = cadd(x0, cadd(cmulk(a1, kC5a), cmulk(a2, kC5b)));
+    cx<R> p2 = cadd(x0, cadd(cmulk(a1, kC5b), cmulk(a2, kC5a)));
+    cx<R> q1 = rot_quarter<R, FWD>(cadd(cmulk(b1, kS5a), cmulk(b2, kS5b)));   // -+ i (s1 b1 + s2 b2)
+    cx<R> q2 = rot_quarter<R, FWD>(csub(cmulk(b1, kS5b), cmulk(b2, kS5a)));   // -+ i (s2 b1 - s1 b2)
+    v[0] = cadd(x0, cadd(a1, a2));
+    v[1] = cadd(p1, q1);
+    v[4] = csub(p1, q1);
+    v[2] = cadd(p2, q2);
+    v[3] = csub(p2, q2);
+}
+
+template <class R, int RAD, bool FWD>
+__device__ __forceinline__ void bfly(cx<R> *v)
+{
+    if constexpr (RAD == 2) bfly2<R, FWD>(v);
+    else if constexpr (RAD == 3) bfly3<R, FWD>(v);
+    else if constexpr (RAD == 4) bfly4<R, FWD>(v);
+    else if constexpr (RAD == 5) bfly5<R, FWD>(v);
+    else bfly8<R, FWD>(v);
+}
+
+// ---------------------------------------------------------------- one stage
+// NB = upper bound of butterflies per thread (compile time).
+template <class Pol, int RAD, bool FWD, int NB>
+__device__ __forceinline__ void fft_stage(typename Pol::scplx *s, int LS, int M, int nl, int Ns,
+                                          const typename Pol::tw_t *__restrict__ tw, int tid,
+                                          int nthr)
+{
+    using R = typename Pol::real;
+    const int nb = M / RAD;
+    const int total = nl * nb;
+    const int step = M / (Ns * RAD);   // twiddle-table stride of this stage
+    cx<R> v[NB][RAD];
+#pragma unroll
+    for (int i = 0; i < NB; ++i) {
+        const int bf = tid + i * nthr;
+        if (bf < total) {
+            const int line = bf / nb;
+            const int b = bf - line * nb;
+            const typename Pol::scplx *base = s + line * LS;
+#pragma unroll
+            for (int t = 0; t < RAD; ++t) v[i][t] = Pol::ld(base[pidx<Pol>(b + t * nb)]);
+            if (Ns > 1) {
+                const int j = b % Ns;
+#pragma unroll
+                for (int t = 1; t < RAD; ++t) {
+                    cx<R> w = Pol::tw(tw[j * t * step]);
+                    v[i][t] = FWD ? cmul(v[i][t], w) : cmulc(v[i][t], w);
+                }
+            }
+            bfly<R, RAD, FWD>(v[i]);
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < NB; ++i) {
+        const int bf = tid + i * nthr;
+        if (bf < total) {
+            const int line = bf / nb;
+            const int b = bf - line * nb;
+            const int j = b % Ns;
+            const int d0 = (b - j) * RAD + j;
+            typename Pol::scplx *base = s + line * LS;
+#pragma unroll
+            for (int t = 0; t < RAD; ++t) base[pidx<Pol>(d0 + t * Ns)] = Pol::st(v[i][t]);
+        }
+    }
+    __syncthreads();
+}
+
+// All stages of one FFT over the nl lines held by the CTA.  EMAX bounds the
+// number of elements per thread (nl * M / nthr <= EMAX).  The caller must
+// synchronise before (data written) and may read right after (the last stage
+// ends with a barrier).
+template <class Pol, bool FWD, int EMAX>
+__device__ __forceinline__ void fft_lines(typename Pol::scplx *s, int LS, const Sched &sc, int nl,
+                                          const typename Pol::tw_t *__restrict__ tw, int tid, int nthr)
+{
+    // The schedule lists radices in the order 8, 4, 2, 5, 3 (make_sched), so
+    // each radix gets one loop of its own.
+    int Ns = 1, st = 0;
+    const int M = sc.M;
+    for (; st < sc.nst && sc.r[st] == 8; ++st, Ns *= 8)
+        fft_stage<Pol, 8, FWD, (EMAX + 7) / 8>(s, LS, M, nl, Ns, tw, tid, nthr);
+    for (; st < sc.nst && sc.r[st] == 4; ++st, Ns *= 4)
+        fft_stage<Pol, 4, FWD, (EMAX + 3) / 4>(s, LS, M, nl, Ns, tw, tid, nthr);
+    for (; st < sc.nst && sc.r[st] == 2; ++st, Ns *= 2)
+        fft_stage<Pol, 2, FWD, (EMAX + 1) / 2>(s, LS, M, nl, Ns, tw, tid, nthr);
+    for (; st < sc.nst && sc.r[st] == 5; ++st, Ns *= 5)
+        fft_stage<Pol, 5, FWD, (EMAX + 4) / 5>(s, LS, M, nl, Ns, tw, tid, nthr);
+    for (; st < sc.nst && sc.r[st] == 3; ++st, Ns *= 3)
+        fft_stage<Pol, 3, FWD, (EMAX + 2) / 3>(s, LS, M, nl, Ns, tw, tid, nthr);
+}
+
+}  // namespace gsm

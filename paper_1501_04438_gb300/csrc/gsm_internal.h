@@ -1,0 +1,91 @@
+// gsm_internal.h -- plan structure and internal entry points of the library.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/gsm.h"
+#include "gsm_fft.cuh"
+
+namespace gsm {
+
+constexpr uint64_t kPlanMagic = 0x47534d504c414e31ull;   // "GSMPLAN1"
+constexpr int kMaxM = 8192;
+constexpr int kMinN = 8;
+constexpr int kSmax = 500;          // largest sinc parameter S scanned by the plan
+constexpr int kGsCap = 2 * kSmax + 2;
+
+// Launch shape of one pass: nl lines of length M per CTA, nthr threads.
+struct PassCfg {
+    int nl = 1;
+    int nthr = 256;
+    int emax = 8;      // complex elements per thread (template instance)
+    size_t smem = 0;
+};
+
+struct Plan {
+    uint64_t magic = 0;
+    gsm_kernel_t kind;
+    int d = 3;
+    int n[3] = {1, 1, 1};
+    int M[3] = {1, 1, 1};
+    double L = 1.0;
+    double eps = 0.0;
+    gsm_options_t opt;
+    int device = 0;
+    int dip_axis = -1;             // n and m both along this axis (octant multiplier)
+
+    // plan results (Sec. 3, Sec. 2.3)
+    int S = 0, nterms = 0;
+    double gs_err = 0.0, c0 = 0.0, c2 = 0.0;
+
+    // device data
+    double *d_w = nullptr, *d_tau = nullptr;      // Gaussian sum
+    double *d_g[3] = {nullptr, nullptr, nullptr}; // 1-D factors [q][k] per axis
+    double *d_khat = nullptr;                     // sum_q w_q G_k^q, octant, FP64
+    double *d_mult64 = nullptr;                   // full multiplier, FP64, octant
+    void *d_mult = nullptr;                       // multiplier in the pass precision
+    void *d_tw[3] = {nullptr, nullptr, nullptr};  // twiddle tables per axis
+    void *d_work1 = nullptr, *d_work2 = nullptr;  // FFT workspace
+    size_t work1_bytes = 0, work2_bytes = 0;
+    size_t mult_elems = 0;
+    void *d_stage_in = nullptr, *d_stage_out = nullptr;   // gsm_apply_host staging
+    double *d_scratch = nullptr;                           // energy partial sums
+    size_t scratch_elems = 0;
+
+    Sched sched[3];
+    PassCfg cfg_xf, cfg_yf, cfg_conv, cfg_yi, cfg_xi;
+};
+
+// thread-local last error
+void set_error(const std::string &msg);
+
+// plan construction on the GPU (gsm_plan.cu)
+gsm_status_t build_plan_data(Plan *p, cudaStream_t st);
+
+// passes (gsm_passes.cu)
+gsm_status_t configure_passes(Plan *p);
+gsm_status_t launch_apply(const Plan *p, const void *rho, void *u, cudaStream_t st);
+gsm_status_t launch_pass(const Plan *p, int pass, const void *rho, void *u, cudaStream_t st);
+gsm_status_t launch_hartree(Plan *p, const void *psi, void *u, void *energy, void *grad,
+                            cudaStream_t st);
+gsm_status_t launch_fft_lines(int M, int nlines, int sign, gsm_precision_t prec,
+                              const double *in, double *out, cudaStream_t st);
+gsm_status_t make_twiddles(Plan *p, int axis, cudaStream_t st);
+gsm_status_t make_pass_multiplier(Plan *p, cudaStream_t st);
+bool make_sched(int M, Sched *s);
+size_t cplx_bytes(gsm_precision_t prec);
+
+}  // namespace gsm
+
+#define GSM_CUDA_TRY(call)                                                                  \
+    do {                                                                                    \
+        cudaError_t e_ = (call);                                                            \
+        if (e_ != cudaSuccess) {                                                            \
+            gsm::set_error(std::string(#call) + ": " + cudaGetErrorString(e_));             \
+            return e_ == cudaErrorMemoryAllocation ? GSM_ERR_OOM : GSM_ERR_CUDA;            \
+        }                                                                                   \
+    } while (0)

@@ -1,0 +1,238 @@
+"""GPU parity: the CUDA path (through the C interface) against the CPU oracle.
+
+Tolerances (relative max-norm error, Eq. error_infty, against the oracle):
+  FP64   1e-12  (the target the method is measured at)
+  FP32X2 1e-12  (double-float carries ~48 bits; FFT error ~ log2(M) 2^-48 ~ 1e-13)
+  FP32   2e-5   (single precision: log2(M) 2^-24 ~ 1e-6 times a small constant)
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1501_04438_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp64": 1e-12, "fp32x2": 1e-12, "fp32": 2e-5}
+
+
+def relmax(a, b):
+    return float(np.max(np.abs(np.asarray(a) - np.asarray(b))) / np.max(np.abs(b)))
+
+
+@pytest.fixture(scope="module")
+def gsm():
+    import paper_1501_04438_gb300 as g
+    return g
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def run(gsm, kernel, rho, L, precision="fp64", **kw):
+    torch = _torch()
+    plan = gsm.Plan(kernel, L, tuple(rho.shape[::-1]), precision=precision, **kw)
+    dt = torch.float32 if precision == "fp32" else torch.float64
+    r = torch.tensor(rho, dtype=dt, device="cuda")
+    u = plan.apply(r)
+    torch.cuda.synchronize()
+    return u.double().cpu().numpy(), plan
+
+
+# ------------------------------------------------------------------ FFT engine
+@pytest.mark.parametrize("M", [8, 12, 16, 20, 30, 64, 96, 128, 192, 256, 320, 384, 512, 1000, 2048, 8192])
+@pytest.mark.parametrize("precision", ["fp64", "fp32x2", "fp32"])
+def test_fft_engine_matches_oracle_fft(gsm, M, precision):
+    torch = _torch()
+    rng = np.random.default_rng(M)
+    nlines = 7
+    x = rng.standard_normal((nlines, M)) + 1j * rng.standard_normal((nlines, M))
+    xt = torch.tensor(x, dtype=torch.complex128, device="cuda")
+    for sign in (-1, 1):
+        got = gsm.fft_lines(xt, sign, precision).cpu().numpy()
+        ref = np.stack([oracle.fftn(x[i], sign) for i in range(nlines)])
+        err = np.max(np.abs(got - ref)) / np.max(np.abs(ref))
+        bound = {"fp64": 1e-15, "fp32x2": 2e-14, "fp32": 3e-7}[precision] * np.log2(M) * 4
+        assert err < bound, (M, precision, sign, err)
+
+
+# ------------------------------------------------------------------ plan data
+def test_plan_gaussian_sum_meets_accuracy(gsm):
+    for kernel, d in (("coulomb3d", 3), ("poisson2d", 2), ("coulomb2d", 2)):
+        n = 16
+        plan = gsm.Plan(kernel, 4.0, (n,) * d)
+        w, tau = plan.gs_terms()
+        delta, rmax = 1e-3, 2 * np.sqrt(d)
+        r = delta * (rmax / delta) ** np.linspace(0, 1, 7919)
+        g = np.sum(w[None, :] * np.exp(-(tau[None, :] * r[:, None]) ** 2), axis=1)
+        if kernel == "poisson2d":
+            assert np.max(np.abs(np.log(r) - g)) < 1.5e-13
+        else:
+            assert np.max(np.abs(1 - r * g)) < 2e-15
+
+
+@pytest.mark.parametrize("kernel", ["coulomb3d", "poisson2d"])
+def test_plan_factors_and_tensor_match_oracle(gsm, kernel):
+    d = 3 if kernel == "coulomb3d" else 2
+    n = 24 if d == 3 else 96
+    plan = gsm.Plan(kernel, 5.0, (n,) * d)
+    info = plan.info()
+    # same S on both sides so that the Gaussian sums are the same terms
+    w_o, tau_o, S_o, _ = oracle.gs(kernel, S=info["S"])
+    w_g, tau_g = plan.gs_terms()
+    assert len(w_g) == len(w_o)
+    assert np.max(np.abs(w_g - w_o) / np.abs(w_o)) < 1e-13
+    assert np.max(np.abs(tau_g - tau_o) / np.maximum(tau_o, 1e-300)) < 1e-13
+    g = plan.factors(0)
+    ref = np.array([[oracle.factor(t, np.pi * k / 2) for k in range(n + 1)] for t in tau_o])
+    # the oracle's composite Gauss-Legendre sums O(k) panels of an oscillating
+    # integrand; its rounding reaches ~1e-14 (factors are at most 4)
+    assert np.max(np.abs(g - ref)) < 2e-14
+    kh = plan.kernel_tensor()
+    kho, _ = oracle.kernel_hat(kernel, n, 5.0, S=info["S"])
+    kho = kho.transpose(*range(d)[::-1])       # oracle is [kz][ky][kx]; plan is [kx][ky][kz]
+    # rounding of sum_q w_q prod g_q is relative to sum_q |w_q| prod |g_q|, which
+    # for ln r (terms of both signs, constant C0 ~ S/4) is ~100x the result
+    scale = np.max(np.sum(np.abs(w_o)[:, None] * np.abs(ref) ** d, axis=0))
+    assert np.max(np.abs(kh - kho)) < 4e-16 * scale
+    c0, c2 = oracle.taylor_coeffs(kernel, w_o, tau_o, 1e-3)
+    assert abs(info["c0"] - c0) < 1e-12 * abs(c0)
+    assert abs(info["c2"] - c2) < 1e-9 * abs(c2)
+
+
+# ------------------------------------------------------------------ apply parity
+CASES_3D = [
+    ("cfg1 gaussian 32^3", lambda: wl.coulomb3d_gaussian(32, 8.0, 1.0), 8.0),
+    ("mixture 24^3", lambda: wl.coulomb3d_mixture(24, 12.0), 12.0),
+    ("mixture 48^3", lambda: wl.coulomb3d_mixture(48, 12.0), 12.0),
+    ("anisotropic 40^3", lambda: wl.coulomb3d_anisotropic(40, 12.0, 4.0), 12.0),
+    ("random 10x12x16", lambda: np.random.default_rng(9).standard_normal((16, 12, 10)), 3.0),
+    ("random 30x8x20", lambda: np.random.default_rng(10).standard_normal((20, 8, 30)), 2.0),
+]
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32x2", "fp32"])
+@pytest.mark.parametrize("name,make,L", CASES_3D, ids=[c[0] for c in CASES_3D])
+def test_coulomb3d_parity(gsm, name, make, L, precision):
+    rho = make()
+    u, plan = run(gsm, "coulomb3d", rho, L, precision)
+    S = plan.info()["S"]
+    uo, _ = oracle.apply("coulomb3d", rho, L, taylor_mode=1, S=S)
+    assert relmax(u, uo) < TOL[precision], relmax(u, uo)
+    if precision == "fp64":
+        ul, _ = oracle.apply("coulomb3d", rho, L, taylor_mode=0, S=S)
+        smooth = not name.startswith("random")
+        if smooth:
+            assert relmax(u, ul) < 1e-12
+
+
+CASES_2D = [
+    ("mixture 64^2", lambda: wl.mixture2d(64, 16.0), 16.0),
+    ("mixture 200^2", lambda: wl.mixture2d(200, 16.0), 16.0),
+    ("random 40x24", lambda: np.random.default_rng(11).standard_normal((24, 40)), 2.5),
+]
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32x2", "fp32"])
+@pytest.mark.parametrize("kernel", ["coulomb2d", "poisson2d"])
+@pytest.mark.parametrize("name,make,L", CASES_2D, ids=[c[0] for c in CASES_2D])
+def test_2d_parity(gsm, kernel, name, make, L, precision):
+    rho = make()
+    u, plan = run(gsm, kernel, rho, L, precision)
+    S = plan.info()["S"]
+    uo, _ = oracle.apply(kernel, rho, L, taylor_mode=1, S=S)
+    assert relmax(u, uo) < TOL[precision], relmax(u, uo)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32x2"])
+def test_dipolar_axis_parity(gsm, precision):
+    L, n = 8.0, 32
+    rho = wl.coulomb3d_gaussian(n, L, 1.2)
+    u, plan = run(gsm, "dipolar3d", rho, L, precision)
+    S = plan.info()["S"]
+    uo, _ = oracle.apply("dipolar3d", rho, L, taylor_mode=1, S=S)
+    assert relmax(u, uo) < TOL[precision]
+
+
+def test_oracle_sized_128_cube_full_parity(gsm):
+    rho = wl.coulomb3d_mixture(128, 12.0)
+    u, plan = run(gsm, "coulomb3d", rho, 12.0)
+    uo, _ = oracle.apply("coulomb3d", rho, 12.0, taylor_mode=1, S=plan.info()["S"])
+    assert relmax(u, uo) < 1e-12
+
+
+# ------------------------------------------------------------------ edge cases
+def test_minimum_size_and_alias(gsm):
+    torch = _torch()
+    rho = np.random.default_rng(12).standard_normal((8, 8, 8))
+    plan = gsm.Plan("coulomb3d", 1.0, 8)
+    r = torch.tensor(rho, device="cuda")
+    u = plan.apply(r)
+    plan.apply(r, out=r)                 # in place: rho and u alias
+    torch.cuda.synchronize()
+    assert torch.equal(u, r)
+    uo, _ = oracle.apply("coulomb3d", rho, 1.0, taylor_mode=1, S=plan.info()["S"])
+    assert relmax(u.cpu().numpy(), uo) < 1e-12
+
+
+def test_invalid_arguments_raise_status(gsm):
+    from paper_1501_04438_gb300 import GSMError
+    for n in (7, 6, 14, 4):       # odd, 2n = 12 ok? (6 < 8 min), 2n = 28 = 4*7, below minimum
+        with pytest.raises(GSMError):
+            gsm.Plan("coulomb3d", 1.0, n)
+    with pytest.raises(GSMError):
+        gsm.Plan("coulomb3d", -1.0, 16)
+    with pytest.raises(GSMError):
+        gsm.Plan("dipolar3d", 1.0, 16, dip_n=(0.6, 0.8, 0.0), dip_m=(0.0, 0.0, 1.0))
+
+
+def test_apply_host_equals_device(gsm):
+    torch = _torch()
+    rho = wl.coulomb3d_mixture(40, 12.0)
+    plan = gsm.Plan("coulomb3d", 12.0, 40)
+    uh = plan.apply_host(rho)
+    ud = plan.apply(torch.tensor(rho, device="cuda")).cpu().numpy()
+    assert np.array_equal(uh, ud)
+
+
+def test_batched_equals_single(gsm):
+    torch = _torch()
+    specs = wl.batch_specs(count=6, sizes=(24, 32, 40))
+    plans, rhos = [], []
+    for n, params in specs:
+        plans.append(gsm.Plan("coulomb3d", 10.0, n))
+        rhos.append(torch.tensor(wl.mixture((n, n, n), 10.0, params), device="cuda"))
+    outs = gsm.apply_batched(plans, rhos)
+    for p, r, o in zip(plans, rhos, outs):
+        assert torch.equal(p.apply(r), o)
+
+
+# ------------------------------------------------------------------ autograd / Hartree
+def test_gsmapply_backward_is_apply(gsm):
+    torch = _torch()
+    from paper_1501_04438_gb300.autograd import GSMApply
+    plan = gsm.Plan("coulomb3d", 4.0, 16)
+    rng = np.random.default_rng(13)
+    rho = torch.tensor(rng.standard_normal((16, 16, 16)), device="cuda", requires_grad=True)
+    w = torch.tensor(rng.standard_normal((16, 16, 16)), device="cuda")
+    loss = (GSMApply.apply(rho, plan) * w).sum()
+    loss.backward()
+    assert torch.allclose(rho.grad, plan.apply(w), rtol=0, atol=1e-13 * float(rho.grad.abs().max()))
+
+
+@pytest.mark.parametrize("kernel", ["coulomb3d", "dipolar3d"])
+def test_hartree_energy_and_gradient(gsm, kernel):
+    torch = _torch()
+    from paper_1501_04438_gb300.autograd import hartree_energy
+    n, L = 32, 12.0
+    psi = wl.psi3d(n, L)
+    plan = gsm.Plan(kernel, L, n)
+    E_o, g_o, _ = oracle.hartree(kernel, psi, L, taylor_mode=1, S=plan.info()["S"])
+    p = torch.tensor(psi, device="cuda", requires_grad=True)
+    E = hartree_energy(p, plan)
+    E.backward()
+    assert abs(float(E.detach()) - E_o) < 1e-12 * abs(E_o)
+    g = p.grad.cpu().numpy()
+    assert np.max(np.abs(g - g_o)) < 1e-12 * np.max(np.abs(g_o))
