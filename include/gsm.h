@@ -209,6 +209,32 @@ gsm_status_t gsm_plan_factors(gsm_plan_t p, int axis, double *host_out, size_t c
 gsm_status_t gsm_fft_lines(int M, int nlines, int sign, gsm_precision_t precision,
                            const double *in_dev, double *out_dev, void *cuda_stream);
 
+/* --- the same FFT without any device allocation ------------------------------
+ * The paper has no counterpart to this entry point; it exists for callers.
+ * gsm_fft_lines obtains its twiddle table with cudaMallocAsync and frees it on
+ * every call.  Some callers cannot do that: code whose device memory is all
+ * held by another allocator (a framework's caching pool), code on a latency-
+ * critical path that must not take the allocator's locks or risk an
+ * out-of-memory failure at call time, or a plug-in that is not allowed to own
+ * device memory.  gsm_fft_lines_noalloc computes exactly what gsm_fft_lines
+ * computes, with the same arguments, but keeps the twiddle table in a fixed
+ * 128 KiB scratch array that the library declares statically in device memory:
+ *   - it calls no cudaMalloc, cudaFree or other allocating routine;
+ *   - M is limited by that scratch to M <= 8192 (16-byte entries); larger M is
+ *     rejected with GSM_ERR_UNSUPPORTED_SIZE;
+ *   - every GPU that loads the library holds the 128 KiB until the process
+ *     exits;
+ *   - the first call on each device looks up the device address of the
+ *     scratch (set-up, once per device, on the current device); make that
+ *     first call before any stream capture;
+ *   - all calls share the one scratch array: calls that can overlap on the GPU
+ *     (different streams, no ordering between them) race and may return wrong
+ *     results; order them on one stream or with events.  Nothing in the
+ *     scratch needs to start at zero: each call writes the whole table it reads.
+ */
+gsm_status_t gsm_fft_lines_noalloc(int M, int nlines, int sign, gsm_precision_t precision,
+                                   const double *in_dev, double *out_dev, void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

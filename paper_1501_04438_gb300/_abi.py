@@ -17,7 +17,8 @@ STATUS = {0: "GSM_OK", 1: "GSM_ERR_INVALID_ARG", 2: "GSM_ERR_UNSUPPORTED_SIZE", 
 # Every function declared in include/gsm.h
 EXPORTS = ["gsm_default_options", "gsm_plan", "gsm_apply", "gsm_apply_pass", "gsm_apply_host", "gsm_apply_batched",
            "gsm_hartree", "gsm_plan_info", "gsm_plan_destroy", "gsm_status_string", "gsm_last_error",
-           "gsm_plan_gs_terms", "gsm_plan_kernel_tensor", "gsm_plan_factors", "gsm_fft_lines"]
+           "gsm_plan_gs_terms", "gsm_plan_kernel_tensor", "gsm_plan_factors", "gsm_fft_lines",
+           "gsm_fft_lines_noalloc"]
 
 
 class Options(ctypes.Structure):
@@ -77,6 +78,7 @@ def load(path: str = LIB_PATH):
         L.gsm_plan_kernel_tensor.argtypes = [_vp, _dp, ctypes.c_size_t]
         L.gsm_plan_factors.argtypes = [_vp, ctypes.c_int, _dp, ctypes.c_size_t]
         L.gsm_fft_lines.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp, _vp, _vp]
+        L.gsm_fft_lines_noalloc.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp, _vp, _vp]
         for name in EXPORTS:
             if name not in ("gsm_default_options", "gsm_status_string", "gsm_last_error"):
                 getattr(L, name).restype = ctypes.c_int

@@ -384,4 +384,17 @@ gsm_status_t gsm_fft_lines(int M, int nlines, int sign, gsm_precision_t precisio
     return launch_fft_lines(M, nlines, sign, precision, in_dev, out_dev, static_cast<cudaStream_t>(cuda_stream));
 }
 
+gsm_status_t gsm_fft_lines_noalloc(int M, int nlines, int sign, gsm_precision_t precision, const double *in_dev,
+                                   double *out_dev, void *cuda_stream)
+{
+    if (!in_dev || !out_dev || nlines < 0 || (sign != 1 && sign != -1) || precision < GSM_FP64 ||
+        precision > GSM_FP32X2) {
+        set_error("bad FFT arguments");
+        return GSM_ERR_INVALID_ARG;
+    }
+    if (nlines == 0) return GSM_OK;
+    return launch_fft_lines_noalloc(M, nlines, sign, precision, in_dev, out_dev,
+                                    static_cast<cudaStream_t>(cuda_stream));
+}
+
 }  // extern "C"

@@ -74,6 +74,8 @@ gsm_status_t launch_hartree(Plan *p, const void *psi, void *u, void *energy, voi
                             cudaStream_t st);
 gsm_status_t launch_fft_lines(int M, int nlines, int sign, gsm_precision_t prec,
                               const double *in, double *out, cudaStream_t st);
+gsm_status_t launch_fft_lines_noalloc(int M, int nlines, int sign, gsm_precision_t prec,
+                                      const double *in, double *out, cudaStream_t st);
 gsm_status_t make_twiddles(Plan *p, int axis, cudaStream_t st);
 gsm_status_t make_pass_multiplier(Plan *p, cudaStream_t st);
 bool make_sched(int M, Sched *s);

@@ -16,6 +16,7 @@
 // or nl (yf, yi) consecutive complex values.  In 2D: xf (one slab), conv on
 // W[kx][y] along y, xi.
 #include <algorithm>
+#include <mutex>
 #include <type_traits>
 
 #include "gsm_internal.h"
@@ -641,6 +642,89 @@ gsm_status_t launch_hartree(Plan *p, const void *psi, void *u, void *energy, voi
     if (p->opt.precision == GSM_FP32)
         return hartree_t<float>(p, (const float *)psi, (float *)u, (float *)energy, (float *)grad, st);
     return hartree_t<double>(p, (const double *)psi, (double *)u, (double *)energy, (double *)grad, st);
+}
+
+// ------------------------------------------------------------------ no-allocation FFT
+// Scratch of gsm_fft_lines_noalloc: the twiddle table of one transform length,
+// up to 8192 entries of 16 bytes (FP64 or double-float pairs).  A file-scope
+// __device__ array, so every GPU that loads this library holds these 128 KiB
+// until the process exits; every call shares it.
+namespace {
+
+constexpr size_t kStaticTwiddleBytes = 8192 * 16;
+__device__ __align__(256) unsigned char g_static_twiddles[kStaticTwiddleBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_static_mutex;
+void *g_static_addr[kMaxDevices] = {};
+
+// The host-side name g_static_twiddles is not a device address; the device
+// address is looked up once per device, with that device current.
+cudaError_t static_twiddle_address(void **out)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_static_mutex);
+    if (!g_static_addr[dev]) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_static_twiddles);
+        if (e != cudaSuccess) return e;
+        g_static_addr[dev] = p;
+    }
+    *out = g_static_addr[dev];
+    return cudaSuccess;
+}
+
+template <class Pol>
+gsm_status_t fft_hook_static_t(int M, int nlines, int sign, const double *in, double *out, cudaStream_t st)
+{
+    Sched sc;
+    if (!make_sched(M, &sc)) {
+        set_error("FFT length must be a product of 2, 3, 5 between 2 and 8192");
+        return GSM_ERR_UNSUPPORTED_SIZE;
+    }
+    if (sizeof(typename Pol::tw_t) * (size_t)M > kStaticTwiddleBytes) {
+        set_error("FFT length exceeds the 128 KiB static twiddle scratch (M <= 8192)");
+        return GSM_ERR_UNSUPPORTED_SIZE;
+    }
+    void *d_tw = nullptr;
+    GSM_CUDA_TRY(static_twiddle_address(&d_tw));
+    // every entry the FFT reads is written here first: nothing needs clearing
+    k_twiddles<<<(M + 255) / 256, 256, 0, st>>>(M, Pol::kId, d_tw);
+    const PassCfg c = choose_cfg<Pol>(M, std::max(1, 2048 / M));
+    const auto *tw = static_cast<const typename Pol::tw_t *>(d_tw);
+    const int blocks = (nlines + c.nl - 1) / c.nl;
+    cudaError_t e = cudaSuccess;
+    with_emax(c, [&](auto E) {
+        if (sign < 0) {
+            e = raise_smem(k_fft_hook<Pol, true, E()>, c.smem);
+            if (e == cudaSuccess)
+                k_fft_hook<Pol, true, E()><<<blocks, c.nthr, c.smem, st>>>((const double2 *)in, (double2 *)out,
+                                                                           nlines, sc, c.nl, tw);
+        } else {
+            e = raise_smem(k_fft_hook<Pol, false, E()>, c.smem);
+            if (e == cudaSuccess)
+                k_fft_hook<Pol, false, E()><<<blocks, c.nthr, c.smem, st>>>((const double2 *)in, (double2 *)out,
+                                                                            nlines, sc, c.nl, tw);
+        }
+    });
+    GSM_CUDA_TRY(e);
+    GSM_CUDA_TRY(cudaGetLastError());
+    return GSM_OK;
+}
+
+}  // namespace
+
+gsm_status_t launch_fft_lines_noalloc(int M, int nlines, int sign, gsm_precision_t prec, const double *in,
+                                      double *out, cudaStream_t st)
+{
+    switch (prec) {
+    case GSM_FP64: return fft_hook_static_t<F64>(M, nlines, sign, in, out, st);
+    case GSM_FP32: return fft_hook_static_t<F32>(M, nlines, sign, in, out, st);
+    default: return fft_hook_static_t<DF64>(M, nlines, sign, in, out, st);
+    }
 }
 
 }  // namespace gsm
