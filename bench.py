@@ -250,6 +250,7 @@ def main():
     u = torch.empty_like(rho)
     stream = torch.cuda.Stream(device=dev)
     plan = gsm.Plan("coulomb3d", L_BOX, n, precision=prec, stream=stream)
+    tune_report = plan.autotune(stream=stream)   # part of the plan: launch shapes by measurement
     info = plan.info()
     npass = info["npasses"]
     flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)   # > L2 (129 MiB)
@@ -318,7 +319,14 @@ def main():
                          "l2": "flushed between steps (512 MiB write, outside the events)"},
               "roofline": roof, "hbm_whole_apply": hbm_whole,
               "passes_ms": {PASS_NAMES_3D[p]: avg_pass[p] for p in range(npass)},
-              "gpu_launches": a.steps * npass, "clocks": clocks, "wall_s_timed": t_wall}
+              "gpu_launches": a.steps * npass, "clocks": clocks, "wall_s_timed": t_wall,
+              "launch_shapes": {PASS_NAMES_3D[p]: {"lines_per_cta": info["launch_nl"][p],
+                                                   "threads_per_line": info["launch_threads"][p],
+                                                   "elems_per_thread": info["launch_emax"][p]}
+                                for p in range(npass)}}
+    if os.environ.get("GSM_BENCH_TUNE_REPORT"):
+        with open(os.environ["GSM_BENCH_TUNE_REPORT"], "w") as f:
+            f.write(tune_report)
 
     if rank == 0:
         # e2e: host buffers through the C interface, copies inside the timed region
@@ -363,6 +371,7 @@ def main():
             for vp in ("fp32x2", "fp32"):
                 vdt = torch.float32 if vp == "fp32" else torch.float64
                 vp_plan = gsm.Plan("coulomb3d", L_BOX, n, precision=vp, stream=stream)
+                vp_plan.autotune(stream=stream)
                 vr = rho.to(vdt)
                 vu = torch.empty_like(vr)
                 time_passes(torch, vp_plan, vr, vu, 2, flush, stream)

@@ -102,6 +102,9 @@ typedef struct {
     size_t bytes_multiplier;    /* device bytes of the stored multiplier */
     size_t bytes_workspace;     /* device bytes of the FFT workspace */
     int npasses;                /* kernel launches of one apply (5 in 3D, 3 in 2D) */
+    int launch_nl[5];           /* per pass: lines per CTA, */
+    int launch_threads[5];      /*   threads per line, */
+    int launch_emax[5];         /*   elements per thread (see gsm_plan_autotune) */
 } gsm_plan_info_t;
 
 void gsm_default_options(gsm_options_t *opt);
@@ -146,6 +149,20 @@ gsm_status_t gsm_apply(gsm_plan_t p, const void *rho, void *u, void *cuda_stream
  * gsm_apply.  Errors as gsm_apply, and GSM_ERR_INVALID_ARG for a bad pass.
  */
 gsm_status_t gsm_apply_pass(gsm_plan_t p, int pass, const void *rho, void *u, void *cuda_stream);
+
+/*
+ * Choose the launch shape of each pass by measurement (no counterpart in the
+ * paper; it changes no result, only speed): for every pass, candidate shapes
+ * (elements per thread, lines per CTA) are timed with CUDA events on the
+ * plan's own workspace and the fastest is kept in the plan.  Temporary input
+ * and output arrays are allocated for the run; the stream is synchronised.
+ * If the environment variable GSM_AUTOTUNE_CACHE names a file, shapes found
+ * there for this device, precision and grid are used without timing, and new
+ * results are appended.  `report` (may be NULL) receives a text table of the
+ * timings, truncated to report_len bytes.  Same plan rules as gsm_apply: no
+ * apply may be in flight on the plan.
+ */
+gsm_status_t gsm_plan_autotune(gsm_plan_t p, void *cuda_stream, char *report, size_t report_len);
 
 /*
  * Same as gsm_apply with HOST arrays: copies rho to the device, applies, copies

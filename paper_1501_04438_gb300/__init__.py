@@ -107,7 +107,10 @@ class Plan:
         _abi.check(_abi.load().gsm_plan_info(self.handle, ctypes.byref(inf)))
         return {"S": inf.S, "nterms": inf.nterms, "gs_err": inf.gs_err, "c0": inf.c0, "c2": inf.c2,
                 "delta": inf.delta, "M": tuple(inf.M[: self.d]), "bytes_multiplier": inf.bytes_multiplier,
-                "bytes_workspace": inf.bytes_workspace, "npasses": inf.npasses}
+                "bytes_workspace": inf.bytes_workspace, "npasses": inf.npasses,
+                "launch_nl": list(inf.launch_nl[: inf.npasses]),
+                "launch_threads": list(inf.launch_threads[: inf.npasses]),
+                "launch_emax": list(inf.launch_emax[: inf.npasses])}
 
     def gs_terms(self):
         nt = self.info()["nterms"]
@@ -148,6 +151,13 @@ class Plan:
         _abi.check(_abi.load().gsm_apply(self.handle, ctypes.c_void_p(rho.data_ptr()),
                                          ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream)))
         return out
+
+    def autotune(self, stream=None) -> str:
+        """Time candidate launch shapes of every pass and keep the fastest
+        (gsm_plan_autotune); returns the timing report."""
+        buf = ctypes.create_string_buffer(1 << 16)
+        _abi.check(_abi.load().gsm_plan_autotune(self.handle, _stream_ptr(stream), buf, len(buf)))
+        return buf.value.decode()
 
     def apply_pass(self, pass_index: int, rho=None, out=None, stream=None):
         """Launch one pass of the apply (see gsm_apply_pass); rho is needed by

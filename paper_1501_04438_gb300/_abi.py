@@ -15,7 +15,7 @@ STATUS = {0: "GSM_OK", 1: "GSM_ERR_INVALID_ARG", 2: "GSM_ERR_UNSUPPORTED_SIZE", 
           4: "GSM_ERR_CUDA", 5: "GSM_ERR_ACCURACY", 6: "GSM_ERR_TIMEOUT", 7: "GSM_ERR_BAD_PLAN"}
 
 # Every function declared in include/gsm.h
-EXPORTS = ["gsm_default_options", "gsm_plan", "gsm_apply", "gsm_apply_pass", "gsm_apply_host", "gsm_apply_batched",
+EXPORTS = ["gsm_default_options", "gsm_plan", "gsm_apply", "gsm_apply_pass", "gsm_plan_autotune", "gsm_apply_host", "gsm_apply_batched",
            "gsm_hartree", "gsm_plan_info", "gsm_plan_destroy", "gsm_status_string", "gsm_last_error",
            "gsm_plan_gs_terms", "gsm_plan_kernel_tensor", "gsm_plan_factors", "gsm_fft_lines",
            "gsm_fft_lines_noalloc"]
@@ -31,7 +31,9 @@ class PlanInfo(ctypes.Structure):
                 ("L", ctypes.c_double), ("delta", ctypes.c_double), ("S", ctypes.c_int), ("nterms", ctypes.c_int),
                 ("gs_err", ctypes.c_double), ("c0", ctypes.c_double), ("c2", ctypes.c_double),
                 ("precision", ctypes.c_int), ("bytes_multiplier", ctypes.c_size_t),
-                ("bytes_workspace", ctypes.c_size_t), ("npasses", ctypes.c_int)]
+                ("bytes_workspace", ctypes.c_size_t), ("npasses", ctypes.c_int),
+                ("launch_nl", ctypes.c_int * 5), ("launch_threads", ctypes.c_int * 5),
+                ("launch_emax", ctypes.c_int * 5)]
 
 
 class GSMError(RuntimeError):
@@ -65,6 +67,7 @@ def load(path: str = LIB_PATH):
         L.gsm_apply.argtypes = [_vp, _vp, _vp, _vp]
         L.gsm_apply_host.argtypes = [_vp, _vp, _vp, _vp]
         L.gsm_apply_pass.argtypes = [_vp, ctypes.c_int, _vp, _vp, _vp]
+        L.gsm_plan_autotune.argtypes = [_vp, _vp, ctypes.c_char_p, ctypes.c_size_t]
         L.gsm_apply_batched.argtypes = [ctypes.c_int, ctypes.POINTER(_vp), ctypes.POINTER(_vp),
                                         ctypes.POINTER(_vp), _vp]
         L.gsm_hartree.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp]

@@ -210,6 +210,23 @@ gsm_status_t gsm_apply_pass(gsm_plan_t h, int pass, const void *rho, void *u, vo
     return launch_pass(p, pass, rho, u, static_cast<cudaStream_t>(cuda_stream));
 }
 
+gsm_status_t gsm_plan_autotune(gsm_plan_t h, void *cuda_stream, char *report, size_t report_len)
+{
+    Plan *p = checked(h);
+    if (!p) {
+        set_error("bad plan handle");
+        return GSM_ERR_BAD_PLAN;
+    }
+    std::string rep;
+    gsm_status_t s = autotune_plan(p, static_cast<cudaStream_t>(cuda_stream), &rep);
+    if (report && report_len > 0) {
+        const size_t n = rep.size() < report_len - 1 ? rep.size() : report_len - 1;
+        memcpy(report, rep.data(), n);
+        report[n] = 0;
+    }
+    return s;
+}
+
 gsm_status_t gsm_apply_host(gsm_plan_t h, const void *rho_host, void *u_host, void *cuda_stream)
 {
     Plan *p = checked(h);
@@ -309,6 +326,14 @@ gsm_status_t gsm_plan_info(gsm_plan_t h, gsm_plan_info_t *info)
     info->bytes_multiplier = p->mult_elems * me;
     info->bytes_workspace = p->work1_bytes + p->work2_bytes;
     info->npasses = p->d == 3 ? 5 : 3;
+    const PassCfg *cf3[5] = {&p->cfg_xf, &p->cfg_yf, &p->cfg_conv, &p->cfg_yi, &p->cfg_xi};
+    const PassCfg *cf2[3] = {&p->cfg_xf, &p->cfg_conv, &p->cfg_xi};
+    for (int i = 0; i < info->npasses; ++i) {
+        const PassCfg *c = p->d == 3 ? cf3[i] : cf2[i];
+        info->launch_nl[i] = c->nl;
+        info->launch_threads[i] = c->gthr;
+        info->launch_emax[i] = c->emax;
+    }
     return GSM_OK;
 }
 

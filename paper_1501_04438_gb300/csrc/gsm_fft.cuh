@@ -2,14 +2,15 @@
 //
 // A CTA holds `nl` lines of length M in shared memory, line l at offset
 // l * LS, element i at pidx(i) (one pad element every 2^kPadShift elements, so
-// that the strided accesses of the early stages spread over the banks).
+// that the strided accesses of the early stages spread over the banks); the
+// FFT of each line is done by its own group of threads (see Group).
 // The transform is a Stockham autosort FFT (self-sorting, no bit reversal):
 // for a stage of radix R after stages whose radices multiply to Ns,
 // butterfly b (0 <= b < M/R) reads x[b + t M/R], t = 0..R-1, multiplies
 // element t by w^(j t) with j = b mod Ns and w = exp(-+2 pi i / (Ns R)),
 // applies the radix-R DFT in registers and writes the outputs to
 // (b - j) R + j + t Ns.  Every thread first loads all its butterflies,
-// the CTA synchronises, then every thread stores: stages run in place.
+// the group synchronises, then every thread stores: stages run in place.
 //
 // Unnormalised: forward uses exp(-2 pi i jk/M), inverse exp(+2 pi i jk/M).
 #pragma once
@@ -139,27 +140,52 @@ __device__ __forceinline__ void bfly(cx<R> *v)
     else bfly8<R, FWD>(v);
 }
 
+// ---------------------------------------------------------------- groups
+// The FFT of one line is done by a group of T threads (a multiple of 32).
+// The group synchronises with __syncwarp (one warp), with __syncthreads
+// (the group is the whole CTA) or with a named barrier of its own, so groups
+// of one CTA never wait for each other between stages.
+struct Group {
+    int t;      // thread index in the group
+    int T;      // threads in the group
+    int bar;    // -1: one warp; 0: whole CTA; > 0: named barrier id
+};
+
+__device__ __forceinline__ void group_sync(const Group &g)
+{
+    if (g.bar < 0) __syncwarp();
+    else if (g.bar == 0) __syncthreads();
+    else asm volatile("bar.sync %0, %1;" ::"r"(g.bar), "r"(g.T) : "memory");
+}
+
+// Group of the calling thread when the CTA holds nl groups of T threads each.
+__device__ __forceinline__ Group make_group(int T, int nl)
+{
+    Group g;
+    g.t = threadIdx.x % T;
+    g.T = T;
+    g.bar = (T == 32) ? -1 : (nl == 1 ? 0 : 1 + (int)(threadIdx.x / T));
+    return g;
+}
+
 // ---------------------------------------------------------------- one stage
-// NB = upper bound of butterflies per thread (compile time).
+// One Stockham stage on one line s[pidx(0..M-1)] by the group.  NB = upper
+// bound of butterflies per thread (compile time); every thread first loads
+// its butterflies, the group synchronises, then every thread stores.
 template <class Pol, int RAD, bool FWD, int NB>
-__device__ __forceinline__ void fft_stage(typename Pol::scplx *s, int LS, int M, int nl, int Ns,
-                                          const typename Pol::tw_t *__restrict__ tw, int tid,
-                                          int nthr)
+__device__ __forceinline__ void fft_stage(typename Pol::scplx *s, int M, int Ns,
+                                          const typename Pol::tw_t *__restrict__ tw, const Group &g)
 {
     using R = typename Pol::real;
     const int nb = M / RAD;
-    const int total = nl * nb;
     const int step = M / (Ns * RAD);   // twiddle-table stride of this stage
     cx<R> v[NB][RAD];
 #pragma unroll
     for (int i = 0; i < NB; ++i) {
-        const int bf = tid + i * nthr;
-        if (bf < total) {
-            const int line = bf / nb;
-            const int b = bf - line * nb;
-            const typename Pol::scplx *base = s + line * LS;
+        const int b = g.t + i * g.T;
+        if (b < nb) {
 #pragma unroll
-            for (int t = 0; t < RAD; ++t) v[i][t] = Pol::ld(base[pidx<Pol>(b + t * nb)]);
+            for (int t = 0; t < RAD; ++t) v[i][t] = Pol::ld(s[pidx<Pol>(b + t * nb)]);
             if (Ns > 1) {
                 const int j = b % Ns;
 #pragma unroll
@@ -171,45 +197,41 @@ __device__ __forceinline__ void fft_stage(typename Pol::scplx *s, int LS, int M,
             bfly<R, RAD, FWD>(v[i]);
         }
     }
-    __syncthreads();
+    group_sync(g);
 #pragma unroll
     for (int i = 0; i < NB; ++i) {
-        const int bf = tid + i * nthr;
-        if (bf < total) {
-            const int line = bf / nb;
-            const int b = bf - line * nb;
+        const int b = g.t + i * g.T;
+        if (b < nb) {
             const int j = b % Ns;
             const int d0 = (b - j) * RAD + j;
-            typename Pol::scplx *base = s + line * LS;
 #pragma unroll
-            for (int t = 0; t < RAD; ++t) base[pidx<Pol>(d0 + t * Ns)] = Pol::st(v[i][t]);
+            for (int t = 0; t < RAD; ++t) s[pidx<Pol>(d0 + t * Ns)] = Pol::st(v[i][t]);
         }
     }
-    __syncthreads();
+    group_sync(g);
 }
 
-// All stages of one FFT over the nl lines held by the CTA.  EMAX bounds the
-// number of elements per thread (nl * M / nthr <= EMAX).  The caller must
-// synchronise before (data written) and may read right after (the last stage
-// ends with a barrier).
+// All stages of the FFT of one line by one group.  EMAX bounds the elements
+// per thread (M <= EMAX * T).  The caller synchronises the group (or CTA)
+// after writing the line; the last stage ends with a group barrier, so the
+// group may read the result right away.  The schedule lists radices in the
+// order 8, 4, 2, 5, 3 (make_sched): each radix gets one loop of its own.
 template <class Pol, bool FWD, int EMAX>
-__device__ __forceinline__ void fft_lines(typename Pol::scplx *s, int LS, const Sched &sc, int nl,
-                                          const typename Pol::tw_t *__restrict__ tw, int tid, int nthr)
+__device__ __forceinline__ void fft_line(typename Pol::scplx *s, const Sched &sc,
+                                         const typename Pol::tw_t *__restrict__ tw, const Group &g)
 {
-    // The schedule lists radices in the order 8, 4, 2, 5, 3 (make_sched), so
-    // each radix gets one loop of its own.
     int Ns = 1, st = 0;
     const int M = sc.M;
     for (; st < sc.nst && sc.r[st] == 8; ++st, Ns *= 8)
-        fft_stage<Pol, 8, FWD, (EMAX + 7) / 8>(s, LS, M, nl, Ns, tw, tid, nthr);
+        fft_stage<Pol, 8, FWD, (EMAX + 7) / 8>(s, M, Ns, tw, g);
     for (; st < sc.nst && sc.r[st] == 4; ++st, Ns *= 4)
-        fft_stage<Pol, 4, FWD, (EMAX + 3) / 4>(s, LS, M, nl, Ns, tw, tid, nthr);
+        fft_stage<Pol, 4, FWD, (EMAX + 3) / 4>(s, M, Ns, tw, g);
     for (; st < sc.nst && sc.r[st] == 2; ++st, Ns *= 2)
-        fft_stage<Pol, 2, FWD, (EMAX + 1) / 2>(s, LS, M, nl, Ns, tw, tid, nthr);
+        fft_stage<Pol, 2, FWD, (EMAX + 1) / 2>(s, M, Ns, tw, g);
     for (; st < sc.nst && sc.r[st] == 5; ++st, Ns *= 5)
-        fft_stage<Pol, 5, FWD, (EMAX + 4) / 5>(s, LS, M, nl, Ns, tw, tid, nthr);
+        fft_stage<Pol, 5, FWD, (EMAX + 4) / 5>(s, M, Ns, tw, g);
     for (; st < sc.nst && sc.r[st] == 3; ++st, Ns *= 3)
-        fft_stage<Pol, 3, FWD, (EMAX + 2) / 3>(s, LS, M, nl, Ns, tw, tid, nthr);
+        fft_stage<Pol, 3, FWD, (EMAX + 2) / 3>(s, M, Ns, tw, g);
 }
 
 }  // namespace gsm

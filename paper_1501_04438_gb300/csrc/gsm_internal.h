@@ -18,9 +18,11 @@ constexpr int kMinN = 8;
 constexpr int kSmax = 500;          // largest sinc parameter S scanned by the plan
 constexpr int kGsCap = 2 * kSmax + 2;
 
-// Launch shape of one pass: nl lines of length M per CTA, nthr threads.
+// Launch shape of one pass: nl lines of length M per CTA, each transformed
+// by a group of gthr threads holding up to emax elements each; nthr = nl * gthr.
 struct PassCfg {
     int nl = 1;
+    int gthr = 256;
     int nthr = 256;
     int emax = 8;      // complex elements per thread (template instance)
     size_t smem = 0;
@@ -70,6 +72,7 @@ gsm_status_t build_plan_data(Plan *p, cudaStream_t st);
 gsm_status_t configure_passes(Plan *p);
 gsm_status_t launch_apply(const Plan *p, const void *rho, void *u, cudaStream_t st);
 gsm_status_t launch_pass(const Plan *p, int pass, const void *rho, void *u, cudaStream_t st);
+gsm_status_t autotune_plan(Plan *p, cudaStream_t st, std::string *report);
 gsm_status_t launch_hartree(Plan *p, const void *psi, void *u, void *energy, void *grad,
                             cudaStream_t st);
 gsm_status_t launch_fft_lines(int M, int nlines, int sign, gsm_precision_t prec,

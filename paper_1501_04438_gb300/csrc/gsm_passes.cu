@@ -15,8 +15,13 @@
 // in shared memory; the other side of each pass moves chunks of 2nl (xf, xi)
 // or nl (yf, yi) consecutive complex values.  In 2D: xf (one slab), conv on
 // W[kx][y] along y, xi.
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
 #include <algorithm>
 #include <mutex>
+#include <string>
 #include <type_traits>
 
 #include "gsm_internal.h"
@@ -30,71 +35,84 @@ constexpr int kMaxThreads = 512;   // CTA size cap: leaves 128 registers per thr
 template <class Pol>
 using S_t = typename Pol::scplx;
 
+// Launch shape (see PassCfg): a CTA holds nl lines; line l is transformed by
+// group l of gthr threads (blockDim.x = nl * gthr).  Loads and stores that
+// touch one line are done by its group; the transposed side of a pass is
+// done by the whole CTA, with one __syncthreads between it and the FFTs.
+
 // ------------------------------------------------------------------ pass xf
 template <class Pol, int EMAX>
 __global__ void __launch_bounds__(kMaxThreads) k_xf(const typename Pol::io_t *__restrict__ rho,
-                                             S_t<Pol> *__restrict__ W1, int nx, int ny, int hx,
-                                             Sched sc, int nl, const typename Pol::tw_t *__restrict__ tw)
+                                                    S_t<Pol> *__restrict__ W1, int nx, int ny, int hx,
+                                                    Sched sc, int nl, int gthr,
+                                                    const typename Pol::tw_t *__restrict__ tw)
 {
     using R = typename Pol::real;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    S_t<Pol> *s = reinterpret_cast<S_t<Pol> *>(smem_raw);
     const int M = sc.M, LS = line_stride<Pol>(M);
+    const Group g = make_group(gthr, nl);
+    const int l = threadIdx.x / gthr;
+    S_t<Pol> *s = reinterpret_cast<S_t<Pol> *>(smem_raw) + l * LS;
     const int z = blockIdx.y;
     const int y0 = blockIdx.x * 2 * nl;
+    const int ya = y0 + 2 * l;
     const typename Pol::io_t *slab = rho + (size_t)z * ny * nx;
-    for (int i = threadIdx.x; i < nl * M; i += blockDim.x) {
-        const int l = i / M, x = i - l * M;
-        const int ya = y0 + 2 * l;
+    for (int x = g.t; x < M; x += g.T) {
         R a = Pol::zero(), b = Pol::zero();
         if (x < nx) {
             if (ya < ny) a = Pol::from_io(slab[(size_t)ya * nx + x]);
             if (ya + 1 < ny) b = Pol::from_io(slab[(size_t)(ya + 1) * nx + x]);
         }
-        s[l * LS + pidx<Pol>(x)] = Pol::st(cx<R>{a, b});
+        s[pidx<Pol>(x)] = Pol::st(cx<R>{a, b});
     }
+    group_sync(g);
+    fft_line<Pol, true, EMAX>(s, sc, tw, g);
     __syncthreads();
-    fft_lines<Pol, true, EMAX>(s, LS, sc, nl, tw, threadIdx.x, blockDim.x);
     // Z = A + iB with A, B the transforms of the two real rows:
     // 2A[k] = Z[k] + conj Z[-k], 2B[k] = -i (Z[k] - conj Z[-k]); the factor 2
     // is removed by the multiplier.
+    const S_t<Pol> *s0 = reinterpret_cast<const S_t<Pol> *>(smem_raw);
     S_t<Pol> *out = W1 + (size_t)z * hx * ny;
     for (int i = threadIdx.x; i < hx * nl; i += blockDim.x) {
-        const int k = i / nl, l = i - k * nl;
-        const cx<R> zk = Pol::ld(s[l * LS + pidx<Pol>(k)]);
-        const cx<R> zm = cconj(Pol::ld(s[l * LS + pidx<Pol>(k == 0 ? 0 : M - k)]));
-        const int ya = y0 + 2 * l;
-        if (ya < ny) out[(size_t)k * ny + ya] = Pol::st(cadd(zk, zm));
-        if (ya + 1 < ny) out[(size_t)k * ny + ya + 1] = Pol::st(cmul_negi(csub(zk, zm)));
+        const int k = i / nl, ll = i - k * nl;
+        const cx<R> zk = Pol::ld(s0[ll * LS + pidx<Pol>(k)]);
+        const cx<R> zm = cconj(Pol::ld(s0[ll * LS + pidx<Pol>(k == 0 ? 0 : M - k)]));
+        const int yy = y0 + 2 * ll;
+        if (yy < ny) out[(size_t)k * ny + yy] = Pol::st(cadd(zk, zm));
+        if (yy + 1 < ny) out[(size_t)k * ny + yy + 1] = Pol::st(cmul_negi(csub(zk, zm)));
     }
 }
 
 // ------------------------------------------------------------------ pass yf
 template <class Pol, int EMAX>
 __global__ void __launch_bounds__(kMaxThreads) k_yf(const S_t<Pol> *__restrict__ W1, S_t<Pol> *__restrict__ W2,
-                                             int ny, int nz, int hx, Sched sc, int nl,
-                                             const typename Pol::tw_t *__restrict__ tw)
+                                                    int ny, int nz, int hx, Sched sc, int nl, int gthr,
+                                                    const typename Pol::tw_t *__restrict__ tw)
 {
     using R = typename Pol::real;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    S_t<Pol> *s = reinterpret_cast<S_t<Pol> *>(smem_raw);
     const int M = sc.M, LS = line_stride<Pol>(M);
+    const Group g = make_group(gthr, nl);
+    const int l = threadIdx.x / gthr;
+    S_t<Pol> *s = reinterpret_cast<S_t<Pol> *>(smem_raw) + l * LS;
     const int kx = blockIdx.y;
     const int z0 = blockIdx.x * nl;
-    for (int i = threadIdx.x; i < nl * M; i += blockDim.x) {
-        const int l = i / M, y = i - l * M;
-        const int z = z0 + l;
+    const int z = z0 + l;
+    const S_t<Pol> *in = W1 + ((size_t)z * hx + kx) * ny;
+    for (int y = g.t; y < M; y += g.T) {
         S_t<Pol> v = Pol::st(cx<R>{Pol::zero(), Pol::zero()});
-        if (y < ny && z < nz) v = W1[((size_t)z * hx + kx) * ny + y];
-        s[l * LS + pidx<Pol>(y)] = v;
+        if (y < ny && z < nz) v = in[y];
+        s[pidx<Pol>(y)] = v;
     }
+    group_sync(g);
+    fft_line<Pol, true, EMAX>(s, sc, tw, g);
     __syncthreads();
-    fft_lines<Pol, true, EMAX>(s, LS, sc, nl, tw, threadIdx.x, blockDim.x);
+    const S_t<Pol> *s0 = reinterpret_cast<const S_t<Pol> *>(smem_raw);
     S_t<Pol> *out = W2 + (size_t)kx * M * nz;
     for (int i = threadIdx.x; i < M * nl; i += blockDim.x) {
-        const int ky = i / nl, l = i - ky * nl;
-        const int z = z0 + l;
-        if (z < nz) out[(size_t)ky * nz + z] = s[l * LS + pidx<Pol>(ky)];
+        const int ky = i / nl, ll = i - ky * nl;
+        const int zz = z0 + ll;
+        if (zz < nz) out[(size_t)ky * nz + zz] = s0[ll * LS + pidx<Pol>(ky)];
     }
 }
 
@@ -102,114 +120,112 @@ __global__ void __launch_bounds__(kMaxThreads) k_yf(const S_t<Pol> *__restrict__
 // Lines of length n (stored) padded to M: forward, multiply by the real
 // multiplier mult[row + min(k, M - k)], inverse, keep the first n.
 // 3D: line = kx * My + ky, row = (kx * (ny + 1) + min(ky, My - ky)) * (nz + 1).
-// 2D: line = kx, row = kx * (ny + 1).
+// 2D: line = kx, row = kx * (ny + 1).  Entirely group-local: no CTA barrier.
 template <class Pol, int EMAX>
 __global__ void __launch_bounds__(kMaxThreads) k_conv(S_t<Pol> *__restrict__ W, const typename Pol::mult_t *__restrict__ mult,
-                                               int nlines, int n, int is3d, int My, int ny1, Sched sc,
-                                               int nl, const typename Pol::tw_t *__restrict__ tw)
+                                                      int nlines, int n, int is3d, int My, int ny1, Sched sc,
+                                                      int nl, int gthr, const typename Pol::tw_t *__restrict__ tw)
 {
     using R = typename Pol::real;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    S_t<Pol> *s = reinterpret_cast<S_t<Pol> *>(smem_raw);
     const int M = sc.M, LS = line_stride<Pol>(M);
-    const int line0 = blockIdx.x * nl;
-    for (int i = threadIdx.x; i < nl * M; i += blockDim.x) {
-        const int l = i / M, z = i - l * M;
-        const int line = line0 + l;
+    const Group g = make_group(gthr, nl);
+    const int l = threadIdx.x / gthr;
+    S_t<Pol> *s = reinterpret_cast<S_t<Pol> *>(smem_raw) + l * LS;
+    const int line = blockIdx.x * nl + l;
+    if (line >= nlines) return;   // the whole group leaves; no CTA barrier follows
+    S_t<Pol> *w = W + (size_t)line * n;
+    for (int z = g.t; z < M; z += g.T) {
         S_t<Pol> v = Pol::st(cx<R>{Pol::zero(), Pol::zero()});
-        if (z < n && line < nlines) v = W[(size_t)line * n + z];
-        s[l * LS + pidx<Pol>(z)] = v;
+        if (z < n) v = w[z];
+        s[pidx<Pol>(z)] = v;
     }
-    __syncthreads();
-    fft_lines<Pol, true, EMAX>(s, LS, sc, nl, tw, threadIdx.x, blockDim.x);
-    const int h = n + 1;
-    for (int i = threadIdx.x; i < nl * M; i += blockDim.x) {
-        const int l = i / M, k = i - l * M;
-        const int line = line0 + l;
-        if (line >= nlines) continue;
-        size_t row;
-        if (is3d) {
-            const int kx = line / My, ky = line - kx * My;
-            const int fky = min(ky, My - ky);
-            row = ((size_t)kx * ny1 + fky) * h;
-        } else {
-            row = (size_t)line * h;
-        }
-        const int fk = min(k, M - k);
-        const R m = Pol::mult(mult[row + fk]);
-        const int p = l * LS + pidx<Pol>(k);
+    group_sync(g);
+    fft_line<Pol, true, EMAX>(s, sc, tw, g);
+    size_t row;
+    if (is3d) {
+        const int kx = line / My, ky = line - kx * My;
+        row = ((size_t)kx * ny1 + min(ky, My - ky)) * (n + 1);
+    } else {
+        row = (size_t)line * (n + 1);
+    }
+    const typename Pol::mult_t *mrow = mult + row;
+    for (int k = g.t; k < M; k += g.T) {
+        const R m = Pol::mult(mrow[min(k, M - k)]);
+        const int p = pidx<Pol>(k);
         s[p] = Pol::st(cscale(Pol::ld(s[p]), m));
     }
-    __syncthreads();
-    fft_lines<Pol, false, EMAX>(s, LS, sc, nl, tw, threadIdx.x, blockDim.x);
-    for (int i = threadIdx.x; i < nl * n; i += blockDim.x) {
-        const int l = i / n, z = i - l * n;
-        const int line = line0 + l;
-        if (line < nlines) W[(size_t)line * n + z] = s[l * LS + pidx<Pol>(z)];
-    }
+    group_sync(g);
+    fft_line<Pol, false, EMAX>(s, sc, tw, g);
+    for (int z = g.t; z < n; z += g.T) w[z] = s[pidx<Pol>(z)];
 }
 
 // ------------------------------------------------------------------ pass yi
 template <class Pol, int EMAX>
 __global__ void __launch_bounds__(kMaxThreads) k_yi(const S_t<Pol> *__restrict__ W2, S_t<Pol> *__restrict__ W1,
-                                             int ny, int nz, int hx, Sched sc, int nl,
-                                             const typename Pol::tw_t *__restrict__ tw)
+                                                    int ny, int nz, int hx, Sched sc, int nl, int gthr,
+                                                    const typename Pol::tw_t *__restrict__ tw)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    S_t<Pol> *s = reinterpret_cast<S_t<Pol> *>(smem_raw);
     const int M = sc.M, LS = line_stride<Pol>(M);
+    const Group g = make_group(gthr, nl);
+    const int l = threadIdx.x / gthr;
+    S_t<Pol> *s0 = reinterpret_cast<S_t<Pol> *>(smem_raw);
+    S_t<Pol> *s = s0 + l * LS;
     const int kx = blockIdx.y;
     const int z0 = blockIdx.x * nl;
     const S_t<Pol> *in = W2 + (size_t)kx * M * nz;
     for (int i = threadIdx.x; i < M * nl; i += blockDim.x) {
-        const int ky = i / nl, l = i - ky * nl;
-        const int z = z0 + l;
-        if (z < nz) s[l * LS + pidx<Pol>(ky)] = in[(size_t)ky * nz + z];
+        const int ky = i / nl, ll = i - ky * nl;
+        const int zz = z0 + ll;
+        if (zz < nz) s0[ll * LS + pidx<Pol>(ky)] = in[(size_t)ky * nz + zz];
     }
     __syncthreads();
-    fft_lines<Pol, false, EMAX>(s, LS, sc, nl, tw, threadIdx.x, blockDim.x);
-    for (int i = threadIdx.x; i < nl * ny; i += blockDim.x) {
-        const int l = i / ny, y = i - l * ny;
-        const int z = z0 + l;
-        if (z < nz) W1[((size_t)z * hx + kx) * ny + y] = s[l * LS + pidx<Pol>(y)];
+    const int z = z0 + l;
+    fft_line<Pol, false, EMAX>(s, sc, tw, g);
+    if (z < nz) {
+        S_t<Pol> *out = W1 + ((size_t)z * hx + kx) * ny;
+        for (int y = g.t; y < ny; y += g.T) out[y] = s[pidx<Pol>(y)];
     }
 }
 
 // ------------------------------------------------------------------ pass xi
 template <class Pol, int EMAX>
 __global__ void __launch_bounds__(kMaxThreads) k_xi(const S_t<Pol> *__restrict__ W1, typename Pol::io_t *__restrict__ u,
-                                             int nx, int ny, int hx, Sched sc, int nl,
-                                             const typename Pol::tw_t *__restrict__ tw)
+                                                    int nx, int ny, int hx, Sched sc, int nl, int gthr,
+                                                    const typename Pol::tw_t *__restrict__ tw)
 {
     using R = typename Pol::real;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    S_t<Pol> *s = reinterpret_cast<S_t<Pol> *>(smem_raw);
     const int M = sc.M, LS = line_stride<Pol>(M);
+    const Group g = make_group(gthr, nl);
+    const int l = threadIdx.x / gthr;
+    S_t<Pol> *s0 = reinterpret_cast<S_t<Pol> *>(smem_raw);
+    S_t<Pol> *s = s0 + l * LS;
     const int z = blockIdx.y;
     const int y0 = blockIdx.x * 2 * nl;
     const S_t<Pol> *in = W1 + (size_t)z * hx * ny;
     // Z[k] = A[k] + i B[k] (k = 0..nx), Z[M-k] = conj A[k] + i conj B[k];
     // A, B real at k = 0 and k = nx (DC and Nyquist of real rows)
     for (int i = threadIdx.x; i < hx * nl; i += blockDim.x) {
-        const int k = i / nl, l = i - k * nl;
-        const int ya = y0 + 2 * l;
+        const int k = i / nl, ll = i - k * nl;
+        const int yy = y0 + 2 * ll;
         cx<R> A = {Pol::zero(), Pol::zero()}, B = {Pol::zero(), Pol::zero()};
-        if (ya < ny) A = Pol::ld(in[(size_t)k * ny + ya]);
-        if (ya + 1 < ny) B = Pol::ld(in[(size_t)k * ny + ya + 1]);
+        if (yy < ny) A = Pol::ld(in[(size_t)k * ny + yy]);
+        if (yy + 1 < ny) B = Pol::ld(in[(size_t)k * ny + yy + 1]);
         if (k == 0 || k == nx) {
             A.im = Pol::zero();
             B.im = Pol::zero();
         }
-        s[l * LS + pidx<Pol>(k)] = Pol::st(cadd(A, cmul_posi(B)));
-        if (k > 0 && k < nx) s[l * LS + pidx<Pol>(M - k)] = Pol::st(cadd(cconj(A), cmul_posi(cconj(B))));
+        s0[ll * LS + pidx<Pol>(k)] = Pol::st(cadd(A, cmul_posi(B)));
+        if (k > 0 && k < nx) s0[ll * LS + pidx<Pol>(M - k)] = Pol::st(cadd(cconj(A), cmul_posi(cconj(B))));
     }
     __syncthreads();
-    fft_lines<Pol, false, EMAX>(s, LS, sc, nl, tw, threadIdx.x, blockDim.x);
+    fft_line<Pol, false, EMAX>(s, sc, tw, g);
+    const int ya = y0 + 2 * l;
     typename Pol::io_t *slab = u + (size_t)z * ny * nx;
-    for (int i = threadIdx.x; i < nl * nx; i += blockDim.x) {
-        const int l = i / nx, x = i - l * nx;
-        const int ya = y0 + 2 * l;
-        const cx<R> c = Pol::ld(s[l * LS + pidx<Pol>(x)]);
+    for (int x = g.t; x < nx; x += g.T) {
+        const cx<R> c = Pol::ld(s[pidx<Pol>(x)]);
         if (ya < ny) slab[(size_t)ya * nx + x] = Pol::to_io(c.re);
         if (ya + 1 < ny) slab[(size_t)(ya + 1) * nx + x] = Pol::to_io(c.im);
     }
@@ -218,29 +234,26 @@ __global__ void __launch_bounds__(kMaxThreads) k_xi(const S_t<Pol> *__restrict__
 // ------------------------------------------------------------------ FFT test hook
 template <class Pol, bool FWD, int EMAX>
 __global__ void __launch_bounds__(kMaxThreads) k_fft_hook(const double2 *__restrict__ in, double2 *__restrict__ out,
-                                                   int nlines, Sched sc, int nl,
-                                                   const typename Pol::tw_t *__restrict__ tw)
+                                                          int nlines, Sched sc, int nl, int gthr,
+                                                          const typename Pol::tw_t *__restrict__ tw)
 {
     using R = typename Pol::real;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    S_t<Pol> *s = reinterpret_cast<S_t<Pol> *>(smem_raw);
     const int M = sc.M, LS = line_stride<Pol>(M);
-    const int line0 = blockIdx.x * nl;
-    for (int i = threadIdx.x; i < nl * M; i += blockDim.x) {
-        const int l = i / M, k = i - l * M;
-        double2 v = make_double2(0.0, 0.0);
-        if (line0 + l < nlines) v = in[(size_t)(line0 + l) * M + k];
-        s[l * LS + pidx<Pol>(k)] =
-            Pol::st(cx<R>{Pol::from_io((typename Pol::io_t)v.x), Pol::from_io((typename Pol::io_t)v.y)});
+    const Group g = make_group(gthr, nl);
+    const int l = threadIdx.x / gthr;
+    S_t<Pol> *s = reinterpret_cast<S_t<Pol> *>(smem_raw) + l * LS;
+    const int line = blockIdx.x * nl + l;
+    if (line >= nlines) return;
+    for (int k = g.t; k < M; k += g.T) {
+        const double2 v = in[(size_t)line * M + k];
+        s[pidx<Pol>(k)] = Pol::st(cx<R>{Pol::from_io((typename Pol::io_t)v.x), Pol::from_io((typename Pol::io_t)v.y)});
     }
-    __syncthreads();
-    fft_lines<Pol, FWD, EMAX>(s, LS, sc, nl, tw, threadIdx.x, blockDim.x);
-    for (int i = threadIdx.x; i < nl * M; i += blockDim.x) {
-        const int l = i / M, k = i - l * M;
-        if (line0 + l < nlines) {
-            const cx<R> c = Pol::ld(s[l * LS + pidx<Pol>(k)]);
-            out[(size_t)(line0 + l) * M + k] = make_double2((double)Pol::to_io(c.re), (double)Pol::to_io(c.im));
-        }
+    group_sync(g);
+    fft_line<Pol, FWD, EMAX>(s, sc, tw, g);
+    for (int k = g.t; k < M; k += g.T) {
+        const cx<R> c = Pol::ld(s[pidx<Pol>(k)]);
+        out[(size_t)line * M + k] = make_double2((double)Pol::to_io(c.re), (double)Pol::to_io(c.im));
     }
 }
 
@@ -345,23 +358,37 @@ cudaError_t raise_smem(K kernel, size_t smem)
 template <class Pol>
 size_t pass_smem(int M, int nl) { return (size_t)nl * line_stride<Pol>(M) * sizeof(S_t<Pol>); }
 
-// nl lines of length M per CTA, nthr threads, emax = elements per thread
-// (8 or 16); nthr * emax >= nl * M.
+// Launch shape for lines of length M: emax elements per thread (8 or 16),
+// gthr = threads per line (a multiple of 32 with gthr * emax >= M), nl lines
+// (groups) per CTA, nthr = nl * gthr <= kMaxThreads.  Groups larger than a
+// warp in a CTA of several groups use named barriers 1..nl (nl <= 15).
+inline int round32(int x) { return ((x + 31) / 32) * 32; }
+
+template <class Pol>
+bool make_cfg(int M, int nl, int emax, PassCfg *c)
+{
+    const int gthr = std::max(32, round32((M + emax - 1) / emax));
+    if (gthr > kMaxThreads || nl < 1 || nl * gthr > kMaxThreads) return false;
+    if (gthr > 32 && nl > 1 && nl > 15) return false;
+    if (pass_smem<Pol>(M, nl) > 200 * 1024) return false;
+    c->nl = nl;
+    c->gthr = gthr;
+    c->nthr = nl * gthr;
+    c->emax = emax;
+    c->smem = pass_smem<Pol>(M, nl);
+    return true;
+}
+
+// Default shape before any tuning: 8 elements per thread when a line fits
+// 512 threads that way, else 16; as many lines as requested that fit.
 template <class Pol>
 PassCfg choose_cfg(int M, int nl_want)
 {
     PassCfg c;
-    int nl = std::max(1, nl_want);
-    const size_t smem_cap = 200 * 1024;
-    while (nl > 1 && (pass_smem<Pol>(M, nl) > smem_cap || (long)nl * M / 16 > kMaxThreads)) nl /= 2;
-    int emax = ((long)nl * M / 8 <= kMaxThreads) ? 8 : 16;
-    int nthr = (nl * M + emax - 1) / emax;
-    nthr = ((nthr + 31) / 32) * 32;
-    nthr = std::max(32, std::min(kMaxThreads, nthr));
-    c.nl = nl;
-    c.nthr = nthr;
-    c.emax = emax;
-    c.smem = pass_smem<Pol>(M, nl);
+    const int emax = (M <= 8 * kMaxThreads) ? 8 : 16;
+    for (int nl = std::max(1, nl_want); nl >= 1; nl /= 2)
+        if (make_cfg<Pol>(M, nl, emax, &c)) return c;
+    make_cfg<Pol>(M, 1, 16, &c);
     return c;
 }
 
@@ -432,19 +459,19 @@ void launch_pass_t(const Plan *p, int pass, const void *rho_v, void *u_v, cudaSt
         const PassCfg &c = p->cfg_xf;
         dim3 g((ny + 2 * c.nl - 1) / (2 * c.nl), nz);
         with_emax(c, [&](auto E) {
-            k_xf<Pol, E()><<<g, c.nthr, c.smem, st>>>(rho, W1, nx, ny, hx, p->sched[0], c.nl, twx);
+            k_xf<Pol, E()><<<g, c.nthr, c.smem, st>>>(rho, W1, nx, ny, hx, p->sched[0], c.nl, c.gthr, twx);
         });
     } else if (pass == last) {
         const PassCfg &c = p->cfg_xi;
         dim3 g((ny + 2 * c.nl - 1) / (2 * c.nl), nz);
         with_emax(c, [&](auto E) {
-            k_xi<Pol, E()><<<g, c.nthr, c.smem, st>>>(W1, u, nx, ny, hx, p->sched[0], c.nl, twx);
+            k_xi<Pol, E()><<<g, c.nthr, c.smem, st>>>(W1, u, nx, ny, hx, p->sched[0], c.nl, c.gthr, twx);
         });
     } else if (p->d == 2) {
         const PassCfg &c = p->cfg_conv;
         with_emax(c, [&](auto E) {
             k_conv<Pol, E()><<<(hx + c.nl - 1) / c.nl, c.nthr, c.smem, st>>>(W1, mult, hx, ny, 0, 1, ny + 1,
-                                                                          p->sched[1], c.nl, twy);
+                                                                          p->sched[1], c.nl, c.gthr, twy);
         });
     } else {
         const tw *twz = static_cast<const tw *>(p->d_tw[2]);
@@ -453,20 +480,20 @@ void launch_pass_t(const Plan *p, int pass, const void *rho_v, void *u_v, cudaSt
             const PassCfg &c = p->cfg_yf;
             dim3 g((nz + c.nl - 1) / c.nl, hx);
             with_emax(c, [&](auto E) {
-                k_yf<Pol, E()><<<g, c.nthr, c.smem, st>>>(W1, W2, ny, nz, hx, p->sched[1], c.nl, twy);
+                k_yf<Pol, E()><<<g, c.nthr, c.smem, st>>>(W1, W2, ny, nz, hx, p->sched[1], c.nl, c.gthr, twy);
             });
         } else if (pass == 2) {
             const PassCfg &c = p->cfg_conv;
             const int nlines = hx * My;
             with_emax(c, [&](auto E) {
                 k_conv<Pol, E()><<<(nlines + c.nl - 1) / c.nl, c.nthr, c.smem, st>>>(
-                    W2, mult, nlines, nz, 1, My, ny + 1, p->sched[2], c.nl, twz);
+                    W2, mult, nlines, nz, 1, My, ny + 1, p->sched[2], c.nl, c.gthr, twz);
             });
         } else {
             const PassCfg &c = p->cfg_yi;
             dim3 g((nz + c.nl - 1) / c.nl, hx);
             with_emax(c, [&](auto E) {
-                k_yi<Pol, E()><<<g, c.nthr, c.smem, st>>>(W2, W1, ny, nz, hx, p->sched[1], c.nl, twy);
+                k_yi<Pol, E()><<<g, c.nthr, c.smem, st>>>(W2, W1, ny, nz, hx, p->sched[1], c.nl, c.gthr, twy);
             });
         }
     }
@@ -485,6 +512,166 @@ template <class Pol>
 gsm_status_t pass_t(const Plan *p, int pass, const void *rho, void *u, cudaStream_t st)
 {
     launch_pass_t<Pol>(p, pass, rho, u, st);
+    GSM_CUDA_TRY(cudaGetLastError());
+    return GSM_OK;
+}
+
+// ------------------------------------------------------------------ autotuning
+// Each pass has its own launch shape; the tuner times candidate shapes of
+// one pass at a time (the others keep theirs) and keeps the fastest.
+template <class Pol>
+cudaError_t raise_pass_smem(const Plan *p, int pass, const PassCfg &c)
+{
+    const int last = p->d == 3 ? 4 : 2;
+    cudaError_t e = cudaSuccess;
+    with_emax(c, [&](auto E) {
+        if (pass == 0) e = raise_smem(k_xf<Pol, E()>, c.smem);
+        else if (pass == last) e = raise_smem(k_xi<Pol, E()>, c.smem);
+        else if (p->d == 2 || pass == 2) e = raise_smem(k_conv<Pol, E()>, c.smem);
+        else if (pass == 1) e = raise_smem(k_yf<Pol, E()>, c.smem);
+        else e = raise_smem(k_yi<Pol, E()>, c.smem);
+    });
+    return e;
+}
+
+PassCfg *pass_cfg(Plan *p, int pass)
+{
+    if (p->d == 3) {
+        PassCfg *c[5] = {&p->cfg_xf, &p->cfg_yf, &p->cfg_conv, &p->cfg_yi, &p->cfg_xi};
+        return c[pass];
+    }
+    PassCfg *c[3] = {&p->cfg_xf, &p->cfg_conv, &p->cfg_xi};
+    return c[pass];
+}
+
+int pass_len(const Plan *p, int pass)
+{
+    if (p->d == 3) {
+        const int m[5] = {p->M[0], p->M[1], p->M[2], p->M[1], p->M[0]};
+        return m[pass];
+    }
+    const int m[3] = {p->M[0], p->M[1], p->M[0]};
+    return m[pass];
+}
+
+std::mutex g_tune_mutex;
+
+std::string tune_key(const Plan *p, int pass)
+{
+    cudaDeviceProp prop;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::string name = "gpu";
+    if (cudaGetDeviceProperties(&prop, dev) == cudaSuccess) name = prop.name;
+    for (char &ch : name)
+        if (ch == ' ') ch = '_';
+    char buf[256];
+    snprintf(buf, sizeof(buf), "v2 %s p%d d%d n%d,%d,%d pass%d", name.c_str(), (int)p->opt.precision, p->d, p->n[0],
+             p->n[1], p->d == 3 ? p->n[2] : 1, pass);
+    return buf;
+}
+
+bool cache_lookup(const char *path, const std::string &key, int *nl, int *emax)
+{
+    FILE *f = fopen(path, "r");
+    if (!f) return false;
+    char line[512];
+    bool hit = false;
+    while (fgets(line, sizeof(line), f)) {
+        const size_t kl = key.size();
+        if (strncmp(line, key.c_str(), kl) == 0 && line[kl] == ' ') {
+            int a = 0, b = 0;
+            if (sscanf(line + kl, " nl=%d emax=%d", &a, &b) == 2) {
+                *nl = a;
+                *emax = b;
+                hit = true;
+            }
+        }
+    }
+    fclose(f);
+    return hit;
+}
+
+template <class Pol>
+gsm_status_t autotune_t(Plan *p, cudaStream_t st, std::string *report)
+{
+    using io = typename Pol::io_t;
+    size_t N = 1;
+    for (int a = 0; a < p->d; ++a) N *= (size_t)p->n[a];
+    void *rho = nullptr, *u = nullptr;
+    GSM_CUDA_TRY(cudaMalloc(&rho, N * sizeof(io)));
+    cudaError_t e = cudaMalloc(&u, N * sizeof(io));
+    if (e != cudaSuccess) {
+        cudaFree(rho);
+        GSM_CUDA_TRY(e);
+    }
+    cudaMemsetAsync(rho, 0, N * sizeof(io), st);
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    const char *cache = getenv("GSM_AUTOTUNE_CACHE");
+    const int np = p->d == 3 ? 5 : 3;
+    char buf[256];
+    for (int pass = 0; pass < np; ++pass) launch_pass_t<Pol>(p, pass, rho, u, st);
+    for (int pass = 0; pass < np && e == cudaSuccess; ++pass) {
+        PassCfg *cfg = pass_cfg(p, pass);
+        const int M = pass_len(p, pass);
+        const std::string key = tune_key(p, pass);
+        int cnl = 0, cem = 0;
+        if (cache) {
+            std::lock_guard<std::mutex> lock(g_tune_mutex);
+            PassCfg c;
+            if (cache_lookup(cache, key, &cnl, &cem) && make_cfg<Pol>(M, cnl, cem, &c) &&
+                raise_pass_smem<Pol>(p, pass, c) == cudaSuccess) {
+                *cfg = c;
+                snprintf(buf, sizeof(buf), "pass %d M=%d cached nl=%d gthr=%d emax=%d\n", pass, M, c.nl, c.gthr,
+                         c.emax);
+                *report += buf;
+                continue;
+            }
+        }
+        PassCfg best = *cfg;
+        float best_ms = 1e30f;
+        const int nls[] = {1, 2, 3, 4, 6, 8, 12, 16};
+        for (int emax : {8, 16}) {
+            for (int nl : nls) {
+                PassCfg c;
+                if (!make_cfg<Pol>(M, nl, emax, &c)) continue;
+                if (raise_pass_smem<Pol>(p, pass, c) != cudaSuccess) continue;
+                *cfg = c;
+                launch_pass_t<Pol>(p, pass, rho, u, st);
+                cudaEventRecord(e0, st);
+                for (int r = 0; r < 3; ++r) launch_pass_t<Pol>(p, pass, rho, u, st);
+                cudaEventRecord(e1, st);
+                e = cudaEventSynchronize(e1);
+                if (e != cudaSuccess) break;
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                ms /= 3.f;
+                snprintf(buf, sizeof(buf), "pass %d M=%d nl=%d gthr=%d emax=%d smem=%zu: %.4f ms\n", pass, M, c.nl,
+                         c.gthr, c.emax, c.smem, ms);
+                *report += buf;
+                if (ms < best_ms) {
+                    best_ms = ms;
+                    best = c;
+                }
+            }
+        }
+        *cfg = best;
+        if (cache && e == cudaSuccess) {
+            std::lock_guard<std::mutex> lock(g_tune_mutex);
+            FILE *f = fopen(cache, "a");
+            if (f) {
+                fprintf(f, "%s nl=%d emax=%d\n", key.c_str(), best.nl, best.emax);
+                fclose(f);
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(rho);
+    cudaFree(u);
+    GSM_CUDA_TRY(e);
     GSM_CUDA_TRY(cudaGetLastError());
     return GSM_OK;
 }
@@ -509,12 +696,12 @@ gsm_status_t fft_hook_t(int M, int nlines, int sign, const double *in, double *o
             e = raise_smem(k_fft_hook<Pol, true, E()>, c.smem);
             if (e == cudaSuccess)
                 k_fft_hook<Pol, true, E()><<<blocks, c.nthr, c.smem, st>>>((const double2 *)in, (double2 *)out,
-                                                                           nlines, sc, c.nl, tw);
+                                                                           nlines, sc, c.nl, c.gthr, tw);
         } else {
             e = raise_smem(k_fft_hook<Pol, false, E()>, c.smem);
             if (e == cudaSuccess)
                 k_fft_hook<Pol, false, E()><<<blocks, c.nthr, c.smem, st>>>((const double2 *)in, (double2 *)out,
-                                                                            nlines, sc, c.nl, tw);
+                                                                            nlines, sc, c.nl, c.gthr, tw);
         }
     });
     GSM_CUDA_TRY(e);
@@ -602,6 +789,15 @@ gsm_status_t launch_pass(const Plan *p, int pass, const void *rho, void *u, cuda
     case GSM_FP64: return pass_t<F64>(p, pass, rho, u, st);
     case GSM_FP32: return pass_t<F32>(p, pass, rho, u, st);
     default: return pass_t<DF64>(p, pass, rho, u, st);
+    }
+}
+
+gsm_status_t autotune_plan(Plan *p, cudaStream_t st, std::string *report)
+{
+    switch (p->opt.precision) {
+    case GSM_FP64: return autotune_t<F64>(p, st, report);
+    case GSM_FP32: return autotune_t<F32>(p, st, report);
+    default: return autotune_t<DF64>(p, st, report);
     }
 }
 
@@ -702,12 +898,12 @@ gsm_status_t fft_hook_static_t(int M, int nlines, int sign, const double *in, do
             e = raise_smem(k_fft_hook<Pol, true, E()>, c.smem);
             if (e == cudaSuccess)
                 k_fft_hook<Pol, true, E()><<<blocks, c.nthr, c.smem, st>>>((const double2 *)in, (double2 *)out,
-                                                                           nlines, sc, c.nl, tw);
+                                                                           nlines, sc, c.nl, c.gthr, tw);
         } else {
             e = raise_smem(k_fft_hook<Pol, false, E()>, c.smem);
             if (e == cudaSuccess)
                 k_fft_hook<Pol, false, E()><<<blocks, c.nthr, c.smem, st>>>((const double2 *)in, (double2 *)out,
-                                                                            nlines, sc, c.nl, tw);
+                                                                            nlines, sc, c.nl, c.gthr, tw);
         }
     });
     GSM_CUDA_TRY(e);

@@ -252,3 +252,20 @@ def test_hartree_energy_and_gradient(gsm, kernel):
     assert abs(float(E.detach()) - E_o) < 1e-12 * abs(E_o)
     g = p.grad.cpu().numpy()
     assert np.max(np.abs(g - g_o)) < 1e-12 * np.max(np.abs(g_o))
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32x2", "fp32"])
+def test_autotune_changes_no_bits(gsm, precision):
+    torch = _torch()
+    dt = torch.float32 if precision == "fp32" else torch.float64
+    for kernel, n in (("coulomb3d", (24, 20, 16)), ("poisson2d", (120, 96))):
+        d = len(n)
+        rho = np.random.default_rng(14).standard_normal(tuple(reversed(n)))
+        plan = gsm.Plan(kernel, 3.0, n, precision=precision)
+        r = torch.tensor(rho, dtype=dt, device="cuda")
+        u0 = plan.apply(r).clone()
+        report = plan.autotune()
+        assert "pass" in report
+        u1 = plan.apply(r)
+        torch.cuda.synchronize()
+        assert torch.equal(u0, u1)
