@@ -50,6 +50,8 @@ def args_parse():
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-n", type=int, default=128, help="grid of the reference arm's bounded sample")
+    ap.add_argument("--suite", action="store_true",
+                    help="measure every config (one JSON line each) instead of the headline line")
     return ap.parse_args()
 
 
@@ -391,5 +393,181 @@ def main():
         dist.destroy_process_group()
 
 
+# ------------------------------------------------------------------ config suite
+def _time_apply(torch, fn, steps, flush, stream):
+    """Mean ms of fn() over `steps` runs, CUDA events on `stream`, L2 flushed
+    between runs outside the events."""
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    with torch.cuda.stream(stream):
+        fn()
+        for e0, e1 in ev:
+            flush.zero_()
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+    torch.cuda.synchronize()
+    return float(np.mean([a.elapsed_time(b) for a, b in ev]))
+
+
+def run_suite(a):
+    import torch
+
+    import oracle
+    import paper_1501_04438_gb300 as gsm
+    from paper_1501_04438_gb300 import workloads as wl
+
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    from closed_forms import coulomb2d_gaussian, poisson2d_gaussian
+
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.Stream(device=dev)
+    flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)
+    steps = max(3, a.steps)
+
+    def emit(d):
+        d["gpu"] = torch.cuda.get_device_name(0)
+        print(json.dumps(d), flush=True)
+
+    def precisions_line(cfg, kernel, rho_h, L, n_tuple, u_ref, extra=None):
+        out = {"config": cfg, "kernel": kernel, "grid": list(n_tuple), "L": L, "forms": {}}
+        for prec in ("fp64", "fp32x2", "fp32"):
+            dt = torch.float32 if prec == "fp32" else torch.float64
+            plan = gsm.Plan(kernel, L, n_tuple, precision=prec, stream=stream)
+            plan.autotune(stream=stream)
+            r = torch.tensor(rho_h, dtype=dt, device=dev)
+            u = torch.empty_like(r)
+            ms = _time_apply(torch, lambda: plan.apply(r, u, stream=stream), steps, flush, stream)
+            uh = u.double().cpu().numpy()
+            npts = int(np.prod(n_tuple))
+            out["forms"][prec] = {"ms": ms, "Mpts_s": npts / (ms / 1e3) / 1e6,
+                                  "rel_err_vs_oracle": relmax(uh, u_ref), "S": plan.info()["S"]}
+            if extra is not None:
+                out["forms"][prec]["rel_err_vs_closed_form"] = relmax(uh, extra)
+            plan.destroy()
+        return out
+
+    # config 1: 3D Coulomb 32^3 on [-8,8]^3, exp(-|x|^2) vs erf closed form
+    from closed_forms import coulomb3d_gaussian
+    rho = wl.coulomb3d_gaussian(32, 8.0, 1.0)
+    X, Y, Z = wl.mesh((32, 32, 32), 8.0)
+    ue = coulomb3d_gaussian(np.sqrt(X * X + Y * Y + Z * Z), 1.0)
+    uo = oracle.apply("coulomb3d", rho, 8.0)[0]
+    line = precisions_line("1", "coulomb3d", rho, 8.0, (32, 32, 32), uo, ue)
+    line["oracle_rel_err_vs_closed_form"] = relmax(uo, ue)
+    emit(line)
+
+    # config 2: 3D Coulomb on [-12,12]^3, anisotropic and 8-Gaussian mixture, 128^3 and 256^3
+    for n in (128, 256):
+        for name, rho in (("2a anisotropic", wl.coulomb3d_anisotropic(n, 12.0, 4.0)),
+                          ("2b mixture8", wl.coulomb3d_mixture(n, 12.0))):
+            t0 = time.perf_counter()
+            uo = oracle.Prepared("coulomb3d", n, 12.0).run(rho)
+            line = precisions_line(name, "coulomb3d", rho, 12.0, (n, n, n), uo)
+            line["oracle_s"] = time.perf_counter() - t0
+            emit(line)
+
+    # config 3: 2D Poisson and Coulomb on [-16,16]^2, 1024^2 and 4096^2, 6 isotropic Gaussians
+    params = wl.mixture2d_params()
+    for n in (1024, 4096):
+        rho = wl.mixture((n, n), 16.0, params)
+        X, Y = wl.mesh((n, n), 16.0)
+        for kernel in ("poisson2d", "coulomb2d"):
+            closed = np.zeros_like(rho)
+            for c, sw, amp in params:
+                r = np.sqrt((X - c[0]) ** 2 + (Y - c[1]) ** 2)
+                f = poisson2d_gaussian if kernel == "poisson2d" else coulomb2d_gaussian
+                closed += amp * f(r, sw[0])
+            t0 = time.perf_counter()
+            uo = oracle.Prepared(kernel, n, 16.0).run(rho)
+            line = precisions_line("3", kernel, rho, 16.0, (n, n), uo, closed)
+            line["oracle_s"] = time.perf_counter() - t0
+            line["oracle_rel_err_vs_closed_form"] = relmax(uo, closed)
+            emit(line)
+
+    # config 4: 48 densities, n in {48,64,96,128,160}, [-10,10]^3, 4 Gaussians each
+    specs = wl.batch_specs()
+    for prec in ("fp64", "fp32"):
+        dt = torch.float32 if prec == "fp32" else torch.float64
+        plans = [gsm.Plan("coulomb3d", 10.0, n, precision=prec, stream=stream) for n, _ in specs]
+        for p in plans:
+            p.autotune(stream=stream)
+        rhos = [torch.tensor(wl.mixture((n, n, n), 10.0, prm), dtype=dt, device=dev) for n, prm in specs]
+        outs = [torch.empty_like(r) for r in rhos]
+        npts = sum(n ** 3 for n, _ in specs)
+        ms_loop = _time_apply(torch, lambda: [p.apply(r, o, stream=stream) for p, r, o in zip(plans, rhos, outs)],
+                              steps, flush, stream)
+        loop_out = [o.clone() for o in outs]
+        ms_grouped = _time_apply(torch, lambda: gsm.apply_batched(plans, rhos, outs, stream=stream), steps, flush,
+                                 stream)
+        same = all(torch.equal(x, y) for x, y in zip(outs, loop_out))
+        batch = gsm.Batch(plans, rhos, outs, stream=stream)
+        ms_graph = _time_apply(torch, lambda: batch.launch(stream=stream), steps, flush, stream)
+        same_graph = all(torch.equal(x, y) for x, y in zip(outs, loop_out))
+        # oracle spot check on three instances
+        errs = []
+        for i in (0, len(specs) // 2, len(specs) - 1):
+            n, prm = specs[i]
+            uo = oracle.Prepared("coulomb3d", n, 10.0, S=plans[i].info()["S"], taylor_mode=1).run(
+                wl.mixture((n, n, n), 10.0, prm))
+            errs.append(relmax(outs[i].double().cpu().numpy(), uo))
+        emit({"config": "4 batch48", "precision": prec, "instances": len(specs),
+              "sizes": [n for n, _ in specs], "points": npts,
+              "loop": {"ms": ms_loop, "Mpts_s": npts / ms_loop / 1e3},
+              "grouped": {"ms": ms_grouped, "Mpts_s": npts / ms_grouped / 1e3, "bitwise_equal_loop": same},
+              "graph": {"ms": ms_graph, "Mpts_s": npts / ms_graph / 1e3, "bitwise_equal_loop": same_graph},
+              "rel_err_vs_oracle_sampled": errs})
+        batch.destroy()
+        for p in plans:
+            p.destroy()
+        del rhos, outs, loop_out
+
+    # config 5: 192^3 on [-12,12]^3, Hartree energy and gradient, Coulomb and dipolar (n = m = e_z)
+    from paper_1501_04438_gb300.autograd import hartree_energy
+    n, L = 192, 12.0
+    psi_h = wl.psi3d(n, L)
+    for kernel in ("coulomb3d", "dipolar3d"):
+        plan = gsm.Plan(kernel, L, n, stream=stream)
+        plan.autotune(stream=stream)
+        psi = torch.tensor(psi_h, device=dev)
+
+        def fwd_bwd():
+            p = psi.detach().requires_grad_(True)
+            E = hartree_energy(p, plan)
+            E.backward()
+            return E, p.grad
+
+        with torch.cuda.stream(stream):
+            E, g = fwd_bwd()
+        torch.cuda.synchronize()
+        ms = _time_apply(torch, fwd_bwd, steps, flush, stream)
+        E_o, g_o, _ = oracle.hartree(kernel, psi_h, L, taylor_mode=1, S=plan.info()["S"])
+        gh = g.cpu().numpy()
+        # central differences of the GPU energy, h = 1e-6, real and imaginary parts
+        rng = np.random.default_rng(5)
+        fd_err = 0.0
+        idxs = [tuple(int(v) for v in rng.integers(n // 4, 3 * n // 4, 3)) for _ in range(16)]
+        for idx in idxs:
+            for unit in (1.0, 1j):
+                vals = []
+                for sgn in (1, -1):
+                    with torch.cuda.stream(stream):
+                        p2 = psi.clone()
+                        p2[idx] += sgn * 1e-6 * unit
+                        e2, _, _ = plan.hartree(p2, stream=stream)
+                    vals.append(float(e2))
+                fd = (vals[0] - vals[1]) / 2e-6
+                an = gh[idx].real if unit == 1.0 else gh[idx].imag
+                fd_err = max(fd_err, abs(fd - an))
+        emit({"config": "5 hartree", "kernel": kernel, "grid": [n] * 3, "L": L,
+              "ms_energy_and_gradient": ms, "Mpts_s": n ** 3 / ms / 1e3,
+              "energy": float(E.detach()), "rel_err_energy_vs_oracle": abs(float(E.detach()) - E_o) / abs(E_o),
+              "rel_err_grad_vs_oracle": float(np.max(np.abs(gh - g_o)) / np.max(np.abs(g_o))),
+              "fd_max_abs_err_over_max_grad": fd_err / float(np.max(np.abs(g_o))), "fd_points": 2 * len(idxs)})
+        plan.destroy()
+
+
 if __name__ == "__main__":
-    main()
+    if "--suite" in sys.argv:
+        run_suite(args_parse())
+    else:
+        main()

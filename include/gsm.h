@@ -46,6 +46,7 @@ extern "C" {
 #endif
 
 typedef struct gsm_plan_s *gsm_plan_t;
+typedef struct gsm_batch_s *gsm_batch_t;
 
 /* Kernels of Eq. kernelPhy plus the dipolar kernel of Eq. dipkerneld. */
 typedef enum {
@@ -174,12 +175,29 @@ gsm_status_t gsm_apply_host(gsm_plan_t p, const void *rho_host, void *u_host, vo
 /*
  * Apply `count` plans to their densities in one call: u[i] = U_i * rho[i].
  * Plans may differ in size, kernel and precision (each uses its own I/O type)
- * but must be distinct handles.  Plans of equal kernel/precision are grouped so
- * that each pass is one launch over all instances of the group.  Errors as in
- * gsm_apply; nothing is launched if any argument is invalid.
+ * but must be distinct handles.  Plans whose padded lengths are all <= 512
+ * are grouped by precision and dimension: each pass is ONE launch over up to
+ * 48 instances of different sizes (one warp per FFT line, one CTA shape for
+ * all sizes); other plans are applied one by one.  The results are the same
+ * bits as gsm_apply's.  Errors as in gsm_apply; nothing is launched if any
+ * argument is invalid.  (No counterpart in the paper, which treats one
+ * density at a time.)
  */
 gsm_status_t gsm_apply_batched(int count, const gsm_plan_t *plans, const void *const *rho,
                                void *const *u, void *cuda_stream);
+
+/*
+ * The same batched apply recorded once into a CUDA graph, so that every later
+ * run is a single cudaGraphLaunch.  The graph holds the given rho[i] and u[i]
+ * pointers and each plan's workspace: refill the same rho arrays between
+ * launches; the plans must outlive the batch, and no other apply may be in
+ * flight on them while the batch runs.  gsm_batch_create synchronises
+ * `cuda_stream`; gsm_batch_launch is asynchronous on its stream.
+ */
+gsm_status_t gsm_batch_create(gsm_batch_t *out, int count, const gsm_plan_t *plans,
+                              const void *const *rho, void *const *u, void *cuda_stream);
+gsm_status_t gsm_batch_launch(gsm_batch_t b, void *cuda_stream);
+gsm_status_t gsm_batch_destroy(gsm_batch_t b);
 
 /*
  * Hartree-type energy and its gradient (3D kernels), all on the device:

@@ -22,7 +22,7 @@ import numpy as np
 from . import _abi
 from ._abi import GSMError, KERNEL_DIM, KERNELS, PRECISIONS
 
-__all__ = ["Plan", "apply", "apply_batched", "GSMApply", "hartree_energy", "fft_lines", "GSMError",
+__all__ = ["Plan", "Batch", "apply", "apply_batched", "GSMApply", "hartree_energy", "fft_lines", "GSMError",
            "KERNELS", "PRECISIONS", "library_path"]
 
 
@@ -228,6 +228,42 @@ def apply_batched(plans, rhos, outs=None, stream=None):
     U = (ctypes.c_void_p * count)(*[o.data_ptr() for o in outs])
     _abi.check(_abi.load().gsm_apply_batched(count, H, R, U, _stream_ptr(stream)))
     return outs
+
+
+class Batch:
+    """gsm_batch_create: the batched apply of `plans` on fixed arrays `rhos`
+    -> `outs`, captured once into a CUDA graph; launch() replays it."""
+
+    def __init__(self, plans, rhos, outs=None, stream=None):
+        torch = _torch()
+        count = len(plans)
+        if outs is None:
+            outs = [torch.empty_like(r) for r in rhos]
+        for p, r, o in zip(plans, rhos, outs):
+            p._check_field(r, "rho")
+            p._check_field(o, "out")
+        self.plans, self.rhos, self.outs = list(plans), list(rhos), list(outs)
+        H = (ctypes.c_void_p * count)(*[p.handle.value for p in plans])
+        R = (ctypes.c_void_p * count)(*[r.data_ptr() for r in rhos])
+        U = (ctypes.c_void_p * count)(*[o.data_ptr() for o in outs])
+        h = ctypes.c_void_p()
+        _abi.check(_abi.load().gsm_batch_create(ctypes.byref(h), count, H, R, U, _stream_ptr(stream)))
+        self._h = h
+
+    def launch(self, stream=None):
+        _abi.check(_abi.load().gsm_batch_launch(self._h, _stream_ptr(stream)))
+        return self.outs
+
+    def destroy(self):
+        if getattr(self, "_h", None) is not None:
+            _abi.load().gsm_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
 
 
 def fft_lines(x, sign: int = -1, precision: str = "fp64", stream=None):

@@ -18,7 +18,7 @@ STATUS = {0: "GSM_OK", 1: "GSM_ERR_INVALID_ARG", 2: "GSM_ERR_UNSUPPORTED_SIZE", 
 EXPORTS = ["gsm_default_options", "gsm_plan", "gsm_apply", "gsm_apply_pass", "gsm_plan_autotune", "gsm_apply_host", "gsm_apply_batched",
            "gsm_hartree", "gsm_plan_info", "gsm_plan_destroy", "gsm_status_string", "gsm_last_error",
            "gsm_plan_gs_terms", "gsm_plan_kernel_tensor", "gsm_plan_factors", "gsm_fft_lines",
-           "gsm_fft_lines_noalloc"]
+           "gsm_fft_lines_noalloc", "gsm_batch_create", "gsm_batch_launch", "gsm_batch_destroy"]
 
 
 class Options(ctypes.Structure):
@@ -70,6 +70,10 @@ def load(path: str = LIB_PATH):
         L.gsm_plan_autotune.argtypes = [_vp, _vp, ctypes.c_char_p, ctypes.c_size_t]
         L.gsm_apply_batched.argtypes = [ctypes.c_int, ctypes.POINTER(_vp), ctypes.POINTER(_vp),
                                         ctypes.POINTER(_vp), _vp]
+        L.gsm_batch_create.argtypes = [ctypes.POINTER(_vp), ctypes.c_int, ctypes.POINTER(_vp), ctypes.POINTER(_vp),
+                                       ctypes.POINTER(_vp), _vp]
+        L.gsm_batch_launch.argtypes = [_vp, _vp]
+        L.gsm_batch_destroy.argtypes = [_vp]
         L.gsm_hartree.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp]
         L.gsm_plan_info.argtypes = [_vp, ctypes.POINTER(PlanInfo)]
         L.gsm_plan_destroy.argtypes = [_vp]

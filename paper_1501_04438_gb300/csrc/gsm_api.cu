@@ -252,15 +252,16 @@ gsm_status_t gsm_apply_host(gsm_plan_t h, const void *rho_host, void *u_host, vo
     return GSM_OK;
 }
 
-gsm_status_t gsm_apply_batched(int count, const gsm_plan_t *plans, const void *const *rho, void *const *u,
-                               void *cuda_stream)
+static gsm_status_t check_batch_args(int count, const gsm_plan_t *plans, const void *const *rho, void *const *u,
+                                     std::vector<const Plan *> *out)
 {
     if (count < 0 || (count > 0 && (!plans || !rho || !u))) {
         set_error("bad batch arguments");
         return GSM_ERR_INVALID_ARG;
     }
     for (int i = 0; i < count; ++i) {
-        if (!checked(plans[i])) {
+        const Plan *p = checked(plans[i]);
+        if (!p) {
             set_error("bad plan handle in batch");
             return GSM_ERR_BAD_PLAN;
         }
@@ -273,12 +274,117 @@ gsm_status_t gsm_apply_batched(int count, const gsm_plan_t *plans, const void *c
                 set_error("a plan appears twice in one batch (its workspace is shared)");
                 return GSM_ERR_INVALID_ARG;
             }
+        out->push_back(p);
     }
-    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
-    for (int i = 0; i < count; ++i) {
-        gsm_status_t s = launch_apply(checked(plans[i]), rho[i], u[i], st);
-        if (s != GSM_OK) return s;
+    return GSM_OK;
+}
+
+gsm_status_t gsm_apply_batched(int count, const gsm_plan_t *plans, const void *const *rho, void *const *u,
+                               void *cuda_stream)
+{
+    std::vector<const Plan *> ps;
+    gsm_status_t s = check_batch_args(count, plans, rho, u, &ps);
+    if (s != GSM_OK || count == 0) return s;
+    return launch_batched(count, ps.data(), rho, u, kBatchLines, static_cast<cudaStream_t>(cuda_stream), false);
+}
+
+}  // extern "C"
+
+namespace gsm {
+constexpr uint64_t kBatchMagic = 0x47534d4241544348ull;   // "GSMBATCH"
+struct Batch {
+    uint64_t magic = 0;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int count = 0;
+};
+}  // namespace gsm
+
+extern "C" {
+
+gsm_status_t gsm_batch_create(gsm_batch_t *out, int count, const gsm_plan_t *plans, const void *const *rho,
+                              void *const *u, void *cuda_stream)
+{
+    if (!out) {
+        set_error("out is NULL");
+        return GSM_ERR_INVALID_ARG;
     }
+    *out = nullptr;
+    std::vector<const Plan *> ps;
+    gsm_status_t s = check_batch_args(count, plans, rho, u, &ps);
+    if (s != GSM_OK) return s;
+    if (count == 0) {
+        set_error("empty batch");
+        return GSM_ERR_INVALID_ARG;
+    }
+    // kernels are prepared outside the capture; the capture records the launches only
+    s = launch_batched(count, ps.data(), rho, u, kBatchLines, nullptr, true);
+    if (s != GSM_OK) return s;
+    GSM_CUDA_TRY(cudaStreamSynchronize(static_cast<cudaStream_t>(cuda_stream)));
+    cudaStream_t cs;
+    GSM_CUDA_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    Batch *b = new (std::nothrow) Batch();
+    if (!b) {
+        cudaStreamDestroy(cs);
+        set_error("host allocation failed");
+        return GSM_ERR_OOM;
+    }
+    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        s = launch_batched(count, ps.data(), rho, u, kBatchLines, cs, false);
+        cudaGraph_t g = nullptr;
+        cudaError_t e2 = cudaStreamEndCapture(cs, &g);
+        if (s == GSM_OK && e2 != cudaSuccess) e = e2;
+        b->graph = g;
+        if (s == GSM_OK && e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, g, 0);
+    }
+    cudaStreamDestroy(cs);
+    if (s == GSM_OK && e != cudaSuccess) {
+        set_error(std::string("batch graph: ") + cudaGetErrorString(e));
+        s = e == cudaErrorMemoryAllocation ? GSM_ERR_OOM : GSM_ERR_CUDA;
+    }
+    if (s != GSM_OK) {
+        if (b->exec) cudaGraphExecDestroy(b->exec);
+        if (b->graph) cudaGraphDestroy(b->graph);
+        delete b;
+        return s;
+    }
+    b->count = count;
+    b->magic = kBatchMagic;
+    *out = reinterpret_cast<gsm_batch_t>(b);
+    return GSM_OK;
+}
+
+static Batch *checked_batch(gsm_batch_t h)
+{
+    Batch *b = reinterpret_cast<Batch *>(h);
+    if (!b || b->magic != kBatchMagic) return nullptr;
+    return b;
+}
+
+gsm_status_t gsm_batch_launch(gsm_batch_t h, void *cuda_stream)
+{
+    Batch *b = checked_batch(h);
+    if (!b) {
+        set_error("bad batch handle");
+        return GSM_ERR_BAD_PLAN;
+    }
+    GSM_CUDA_TRY(cudaGraphLaunch(b->exec, static_cast<cudaStream_t>(cuda_stream)));
+    return GSM_OK;
+}
+
+gsm_status_t gsm_batch_destroy(gsm_batch_t h)
+{
+    Batch *b = checked_batch(h);
+    if (!b) {
+        set_error("bad batch handle");
+        return GSM_ERR_BAD_PLAN;
+    }
+    cudaDeviceSynchronize();
+    cudaGraphExecDestroy(b->exec);
+    cudaGraphDestroy(b->graph);
+    b->magic = 0;
+    delete b;
     return GSM_OK;
 }
 

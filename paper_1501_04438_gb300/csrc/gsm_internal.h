@@ -73,6 +73,9 @@ gsm_status_t configure_passes(Plan *p);
 gsm_status_t launch_apply(const Plan *p, const void *rho, void *u, cudaStream_t st);
 gsm_status_t launch_pass(const Plan *p, int pass, const void *rho, void *u, cudaStream_t st);
 gsm_status_t autotune_plan(Plan *p, cudaStream_t st, std::string *report);
+gsm_status_t launch_batched(int count, const Plan *const *plans, const void *const *rho, void *const *u,
+                            int nl, cudaStream_t st, bool dry);
+constexpr int kBatchLines = 8;   // lines (warps) per CTA of the grouped batch kernels
 gsm_status_t launch_hartree(Plan *p, const void *psi, void *u, void *energy, void *grad,
                             cudaStream_t st);
 gsm_status_t launch_fft_lines(int M, int nlines, int sign, gsm_precision_t prec,

@@ -21,7 +21,9 @@
 
 #include <algorithm>
 #include <mutex>
+#include <new>
 #include <string>
+#include <vector>
 #include <type_traits>
 
 #include "gsm_internal.h"
@@ -41,20 +43,21 @@ using S_t = typename Pol::scplx;
 // done by the whole CTA, with one __syncthreads between it and the FFTs.
 
 // ------------------------------------------------------------------ pass xf
+// Each pass is a __device__ body taking its tile (bx, by) explicitly, so that
+// the single-plan kernels and the grouped batch kernels share it.
 template <class Pol, int EMAX>
-__global__ void __launch_bounds__(kMaxThreads) k_xf(const typename Pol::io_t *__restrict__ rho,
-                                                    S_t<Pol> *__restrict__ W1, int nx, int ny, int hx,
-                                                    Sched sc, int nl, int gthr,
-                                                    const typename Pol::tw_t *__restrict__ tw)
+__device__ __forceinline__ void body_xf(const typename Pol::io_t *__restrict__ rho, S_t<Pol> *__restrict__ W1,
+                                        int nx, int ny, int hx, const Sched &sc, int nl, int gthr,
+                                        const typename Pol::tw_t *__restrict__ tw, int bx, int by,
+                                        unsigned char *smem_raw)
 {
     using R = typename Pol::real;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
     const int M = sc.M, LS = line_stride<Pol>(M);
     const Group g = make_group(gthr, nl);
     const int l = threadIdx.x / gthr;
     S_t<Pol> *s = reinterpret_cast<S_t<Pol> *>(smem_raw) + l * LS;
-    const int z = blockIdx.y;
-    const int y0 = blockIdx.x * 2 * nl;
+    const int z = by;
+    const int y0 = bx * 2 * nl;
     const int ya = y0 + 2 * l;
     const typename Pol::io_t *slab = rho + (size_t)z * ny * nx;
     for (int x = g.t; x < M; x += g.T) {
@@ -83,20 +86,30 @@ __global__ void __launch_bounds__(kMaxThreads) k_xf(const typename Pol::io_t *__
     }
 }
 
-// ------------------------------------------------------------------ pass yf
 template <class Pol, int EMAX>
-__global__ void __launch_bounds__(kMaxThreads) k_yf(const S_t<Pol> *__restrict__ W1, S_t<Pol> *__restrict__ W2,
-                                                    int ny, int nz, int hx, Sched sc, int nl, int gthr,
+__global__ void __launch_bounds__(kMaxThreads) k_xf(const typename Pol::io_t *__restrict__ rho,
+                                                    S_t<Pol> *__restrict__ W1, int nx, int ny, int hx,
+                                                    Sched sc, int nl, int gthr,
                                                     const typename Pol::tw_t *__restrict__ tw)
 {
-    using R = typename Pol::real;
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    body_xf<Pol, EMAX>(rho, W1, nx, ny, hx, sc, nl, gthr, tw, blockIdx.x, blockIdx.y, smem_raw);
+}
+
+// ------------------------------------------------------------------ pass yf
+template <class Pol, int EMAX>
+__device__ __forceinline__ void body_yf(const S_t<Pol> *__restrict__ W1, S_t<Pol> *__restrict__ W2, int ny,
+                                        int nz, int hx, const Sched &sc, int nl, int gthr,
+                                        const typename Pol::tw_t *__restrict__ tw, int bx, int by,
+                                        unsigned char *smem_raw)
+{
+    using R = typename Pol::real;
     const int M = sc.M, LS = line_stride<Pol>(M);
     const Group g = make_group(gthr, nl);
     const int l = threadIdx.x / gthr;
     S_t<Pol> *s = reinterpret_cast<S_t<Pol> *>(smem_raw) + l * LS;
-    const int kx = blockIdx.y;
-    const int z0 = blockIdx.x * nl;
+    const int kx = by;
+    const int z0 = bx * nl;
     const int z = z0 + l;
     const S_t<Pol> *in = W1 + ((size_t)z * hx + kx) * ny;
     for (int y = g.t; y < M; y += g.T) {
@@ -116,23 +129,32 @@ __global__ void __launch_bounds__(kMaxThreads) k_yf(const S_t<Pol> *__restrict__
     }
 }
 
+template <class Pol, int EMAX>
+__global__ void __launch_bounds__(kMaxThreads) k_yf(const S_t<Pol> *__restrict__ W1, S_t<Pol> *__restrict__ W2,
+                                                    int ny, int nz, int hx, Sched sc, int nl, int gthr,
+                                                    const typename Pol::tw_t *__restrict__ tw)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    body_yf<Pol, EMAX>(W1, W2, ny, nz, hx, sc, nl, gthr, tw, blockIdx.x, blockIdx.y, smem_raw);
+}
+
 // ------------------------------------------------------------------ pass conv
 // Lines of length n (stored) padded to M: forward, multiply by the real
 // multiplier mult[row + min(k, M - k)], inverse, keep the first n.
 // 3D: line = kx * My + ky, row = (kx * (ny + 1) + min(ky, My - ky)) * (nz + 1).
 // 2D: line = kx, row = kx * (ny + 1).  Entirely group-local: no CTA barrier.
 template <class Pol, int EMAX>
-__global__ void __launch_bounds__(kMaxThreads) k_conv(S_t<Pol> *__restrict__ W, const typename Pol::mult_t *__restrict__ mult,
-                                                      int nlines, int n, int is3d, int My, int ny1, Sched sc,
-                                                      int nl, int gthr, const typename Pol::tw_t *__restrict__ tw)
+__device__ __forceinline__ void body_conv(S_t<Pol> *__restrict__ W, const typename Pol::mult_t *__restrict__ mult,
+                                          int nlines, int n, int is3d, int My, int ny1, const Sched &sc, int nl,
+                                          int gthr, const typename Pol::tw_t *__restrict__ tw, int bx,
+                                          unsigned char *smem_raw)
 {
     using R = typename Pol::real;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
     const int M = sc.M, LS = line_stride<Pol>(M);
     const Group g = make_group(gthr, nl);
     const int l = threadIdx.x / gthr;
     S_t<Pol> *s = reinterpret_cast<S_t<Pol> *>(smem_raw) + l * LS;
-    const int line = blockIdx.x * nl + l;
+    const int line = bx * nl + l;
     if (line >= nlines) return;   // the whole group leaves; no CTA barrier follows
     S_t<Pol> *w = W + (size_t)line * n;
     for (int z = g.t; z < M; z += g.T) {
@@ -160,20 +182,29 @@ __global__ void __launch_bounds__(kMaxThreads) k_conv(S_t<Pol> *__restrict__ W, 
     for (int z = g.t; z < n; z += g.T) w[z] = s[pidx<Pol>(z)];
 }
 
-// ------------------------------------------------------------------ pass yi
 template <class Pol, int EMAX>
-__global__ void __launch_bounds__(kMaxThreads) k_yi(const S_t<Pol> *__restrict__ W2, S_t<Pol> *__restrict__ W1,
-                                                    int ny, int nz, int hx, Sched sc, int nl, int gthr,
-                                                    const typename Pol::tw_t *__restrict__ tw)
+__global__ void __launch_bounds__(kMaxThreads) k_conv(S_t<Pol> *__restrict__ W, const typename Pol::mult_t *__restrict__ mult,
+                                                      int nlines, int n, int is3d, int My, int ny1, Sched sc,
+                                                      int nl, int gthr, const typename Pol::tw_t *__restrict__ tw)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    body_conv<Pol, EMAX>(W, mult, nlines, n, is3d, My, ny1, sc, nl, gthr, tw, blockIdx.x, smem_raw);
+}
+
+// ------------------------------------------------------------------ pass yi
+template <class Pol, int EMAX>
+__device__ __forceinline__ void body_yi(const S_t<Pol> *__restrict__ W2, S_t<Pol> *__restrict__ W1, int ny,
+                                        int nz, int hx, const Sched &sc, int nl, int gthr,
+                                        const typename Pol::tw_t *__restrict__ tw, int bx, int by,
+                                        unsigned char *smem_raw)
+{
     const int M = sc.M, LS = line_stride<Pol>(M);
     const Group g = make_group(gthr, nl);
     const int l = threadIdx.x / gthr;
     S_t<Pol> *s0 = reinterpret_cast<S_t<Pol> *>(smem_raw);
     S_t<Pol> *s = s0 + l * LS;
-    const int kx = blockIdx.y;
-    const int z0 = blockIdx.x * nl;
+    const int kx = by;
+    const int z0 = bx * nl;
     const S_t<Pol> *in = W2 + (size_t)kx * M * nz;
     for (int i = threadIdx.x; i < M * nl; i += blockDim.x) {
         const int ky = i / nl, ll = i - ky * nl;
@@ -189,21 +220,30 @@ __global__ void __launch_bounds__(kMaxThreads) k_yi(const S_t<Pol> *__restrict__
     }
 }
 
-// ------------------------------------------------------------------ pass xi
 template <class Pol, int EMAX>
-__global__ void __launch_bounds__(kMaxThreads) k_xi(const S_t<Pol> *__restrict__ W1, typename Pol::io_t *__restrict__ u,
-                                                    int nx, int ny, int hx, Sched sc, int nl, int gthr,
+__global__ void __launch_bounds__(kMaxThreads) k_yi(const S_t<Pol> *__restrict__ W2, S_t<Pol> *__restrict__ W1,
+                                                    int ny, int nz, int hx, Sched sc, int nl, int gthr,
                                                     const typename Pol::tw_t *__restrict__ tw)
 {
-    using R = typename Pol::real;
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    body_yi<Pol, EMAX>(W2, W1, ny, nz, hx, sc, nl, gthr, tw, blockIdx.x, blockIdx.y, smem_raw);
+}
+
+// ------------------------------------------------------------------ pass xi
+template <class Pol, int EMAX>
+__device__ __forceinline__ void body_xi(const S_t<Pol> *__restrict__ W1, typename Pol::io_t *__restrict__ u, int nx,
+                                        int ny, int hx, const Sched &sc, int nl, int gthr,
+                                        const typename Pol::tw_t *__restrict__ tw, int bx, int by,
+                                        unsigned char *smem_raw)
+{
+    using R = typename Pol::real;
     const int M = sc.M, LS = line_stride<Pol>(M);
     const Group g = make_group(gthr, nl);
     const int l = threadIdx.x / gthr;
     S_t<Pol> *s0 = reinterpret_cast<S_t<Pol> *>(smem_raw);
     S_t<Pol> *s = s0 + l * LS;
-    const int z = blockIdx.y;
-    const int y0 = blockIdx.x * 2 * nl;
+    const int z = by;
+    const int y0 = bx * 2 * nl;
     const S_t<Pol> *in = W1 + (size_t)z * hx * ny;
     // Z[k] = A[k] + i B[k] (k = 0..nx), Z[M-k] = conj A[k] + i conj B[k];
     // A, B real at k = 0 and k = nx (DC and Nyquist of real rows)
@@ -231,6 +271,15 @@ __global__ void __launch_bounds__(kMaxThreads) k_xi(const S_t<Pol> *__restrict__
     }
 }
 
+template <class Pol, int EMAX>
+__global__ void __launch_bounds__(kMaxThreads) k_xi(const S_t<Pol> *__restrict__ W1, typename Pol::io_t *__restrict__ u,
+                                                    int nx, int ny, int hx, Sched sc, int nl, int gthr,
+                                                    const typename Pol::tw_t *__restrict__ tw)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    body_xi<Pol, EMAX>(W1, u, nx, ny, hx, sc, nl, gthr, tw, blockIdx.x, blockIdx.y, smem_raw);
+}
+
 // ------------------------------------------------------------------ FFT test hook
 template <class Pol, bool FWD, int EMAX>
 __global__ void __launch_bounds__(kMaxThreads) k_fft_hook(const double2 *__restrict__ in, double2 *__restrict__ out,
@@ -254,6 +303,70 @@ __global__ void __launch_bounds__(kMaxThreads) k_fft_hook(const double2 *__restr
     for (int k = g.t; k < M; k += g.T) {
         const cx<R> c = Pol::ld(s[pidx<Pol>(k)]);
         out[(size_t)line * M + k] = make_double2((double)Pol::to_io(c.re), (double)Pol::to_io(c.im));
+    }
+}
+
+// ------------------------------------------------------------------ grouped batch
+// One launch per pass covers up to kBatchMax instances of different sizes:
+// CTA b belongs to instance i with prefix[i] <= b < prefix[i+1] and handles
+// tile b - prefix[i] of that instance's pass grid.  Every line is done by one
+// warp holding up to 16 elements per thread (M <= 512), nl lines per CTA, so
+// one CTA shape serves all sizes.
+constexpr int kBatchMax = 48;
+constexpr int kBatchEmax = 16;
+constexpr int kBatchMaxM = 32 * kBatchEmax;
+
+struct InstDesc {
+    const void *rho;
+    void *u;
+    void *W1, *W2;
+    const void *mult;
+    const void *tw[3];
+    int n[3], M[3];
+    Sched sc[3];
+    int gx[5];   // x extent of each pass's tile grid
+};
+
+struct BatchArgs {
+    int count, d, nl;
+    int prefix[kBatchMax + 1];
+    InstDesc inst[kBatchMax];
+};
+
+template <class Pol, int PASS>
+__global__ void __launch_bounds__(kMaxThreads) k_batch(const __grid_constant__ BatchArgs a)
+{
+    using io = typename Pol::io_t;
+    using tw = typename Pol::tw_t;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int b = blockIdx.x;
+    int i = 0;
+    while (i + 1 < a.count && a.prefix[i + 1] <= b) ++i;
+    const InstDesc &d = a.inst[i];
+    const int t = b - a.prefix[i];
+    const int gx = d.gx[PASS];
+    const int bx = t % gx, by = t / gx;
+    const int nx = d.n[0], ny = d.n[1], nz = a.d == 3 ? d.n[2] : 1, hx = nx + 1;
+    S_t<Pol> *W1 = static_cast<S_t<Pol> *>(d.W1);
+    S_t<Pol> *W2 = static_cast<S_t<Pol> *>(d.W2);
+    const auto *mult = static_cast<const typename Pol::mult_t *>(d.mult);
+    const tw *tw0 = static_cast<const tw *>(d.tw[0]);
+    const tw *tw1 = static_cast<const tw *>(d.tw[1]);
+    const tw *tw2 = static_cast<const tw *>(d.tw[2]);
+    const int nl = a.nl;
+    const int last = a.d == 3 ? 4 : 2;
+    if (PASS == 0) {
+        body_xf<Pol, kBatchEmax>(static_cast<const io *>(d.rho), W1, nx, ny, hx, d.sc[0], nl, 32, tw0, bx, by, smem_raw);
+    } else if (PASS == last) {
+        body_xi<Pol, kBatchEmax>(W1, static_cast<io *>(d.u), nx, ny, hx, d.sc[0], nl, 32, tw0, bx, by, smem_raw);
+    } else if (a.d == 2) {
+        body_conv<Pol, kBatchEmax>(W1, mult, hx, ny, 0, 1, ny + 1, d.sc[1], nl, 32, tw1, bx, smem_raw);
+    } else if (PASS == 1) {
+        body_yf<Pol, kBatchEmax>(W1, W2, ny, nz, hx, d.sc[1], nl, 32, tw1, bx, by, smem_raw);
+    } else if (PASS == 2) {
+        body_conv<Pol, kBatchEmax>(W2, mult, hx * d.M[1], nz, 1, d.M[1], ny + 1, d.sc[2], nl, 32, tw2, bx, smem_raw);
+    } else {
+        body_yi<Pol, kBatchEmax>(W2, W1, ny, nz, hx, d.sc[1], nl, 32, tw1, bx, by, smem_raw);
     }
 }
 
@@ -921,6 +1034,136 @@ gsm_status_t launch_fft_lines_noalloc(int M, int nlines, int sign, gsm_precision
     case GSM_FP32: return fft_hook_static_t<F32>(M, nlines, sign, in, out, st);
     default: return fft_hook_static_t<DF64>(M, nlines, sign, in, out, st);
     }
+}
+
+
+// ------------------------------------------------------------------ grouped batch, host side
+namespace {
+
+bool batch_eligible(const Plan *p)
+{
+    for (int a = 0; a < p->d; ++a)
+        if (p->M[a] > kBatchMaxM) return false;
+    return true;
+}
+
+// Tile grid of pass `pass` of plan p for lines-per-CTA nl: (gx, gy).
+void pass_grid(const Plan *p, int pass, int nl, int *gx, int *gy)
+{
+    const int nx = p->n[0], ny = p->n[1], nz = p->d == 3 ? p->n[2] : 1, hx = nx + 1;
+    const int last = p->d == 3 ? 4 : 2;
+    if (pass == 0 || pass == last) {
+        *gx = (ny + 2 * nl - 1) / (2 * nl);
+        *gy = nz;
+    } else if (p->d == 2) {
+        *gx = (hx + nl - 1) / nl;
+        *gy = 1;
+    } else if (pass == 2) {
+        *gx = (hx * p->M[1] + nl - 1) / nl;
+        *gy = 1;
+    } else {
+        *gx = (nz + nl - 1) / nl;
+        *gy = hx;
+    }
+}
+
+template <class Pol>
+gsm_status_t launch_batch_t(BatchArgs &a, const std::vector<const Plan *> &plans, const void *const *rho,
+                            void *const *u, cudaStream_t st, bool dry)
+{
+    const int np = a.d == 3 ? 5 : 3;
+    size_t smem = 0;
+    for (size_t i = 0; i < plans.size(); ++i) {
+        const Plan *p = plans[i];
+        InstDesc &d = a.inst[i];
+        d.rho = rho[i];
+        d.u = u[i];
+        d.W1 = p->d_work1;
+        d.W2 = p->d_work2;
+        d.mult = p->d_mult;
+        for (int ax = 0; ax < 3; ++ax) {
+            d.n[ax] = ax < p->d ? p->n[ax] : 1;
+            d.M[ax] = ax < p->d ? p->M[ax] : 1;
+            d.tw[ax] = ax < p->d ? p->d_tw[ax] : nullptr;
+            if (ax < p->d) d.sc[ax] = p->sched[ax];
+            if (ax < p->d) smem = std::max(smem, pass_smem<Pol>(p->M[ax], a.nl));
+        }
+        for (int pass = 0; pass < np; ++pass) {
+            int gx, gy;
+            pass_grid(p, pass, a.nl, &gx, &gy);
+            d.gx[pass] = gx;
+        }
+    }
+    cudaError_t e = cudaSuccess;
+    auto run = [&](auto kernel, int pass) {
+        a.prefix[0] = 0;
+        for (int i = 0; i < a.count; ++i) {
+            int gx, gy;
+            pass_grid(plans[i], pass, a.nl, &gx, &gy);
+            a.prefix[i + 1] = a.prefix[i] + gx * gy;
+        }
+        if (e == cudaSuccess) e = raise_smem(kernel, smem);
+        if (e == cudaSuccess && !dry) kernel<<<a.prefix[a.count], a.nl * 32, smem, st>>>(a);
+    };
+    run(k_batch<Pol, 0>, 0);
+    run(k_batch<Pol, 1>, 1);
+    run(k_batch<Pol, 2>, 2);
+    if (np == 5) {
+        run(k_batch<Pol, 3>, 3);
+        run(k_batch<Pol, 4>, 4);
+    }
+    GSM_CUDA_TRY(e);
+    GSM_CUDA_TRY(cudaGetLastError());
+    return GSM_OK;
+}
+
+}  // namespace
+
+// Launch u[i] = U_i * rho[i]: plans with all padded lengths <= 512 are grouped
+// by (precision, dimension) into launches of up to kBatchMax instances per
+// pass; the others are applied one by one.  dry: only prepare the kernels
+// (shared-memory limits), launch nothing.
+gsm_status_t launch_batched(int count, const Plan *const *plans, const void *const *rho, void *const *u,
+                            int nl, cudaStream_t st, bool dry)
+{
+    std::vector<int> done(count, 0);
+    for (int i = 0; i < count; ++i) {
+        if (done[i]) continue;
+        if (!batch_eligible(plans[i])) {
+            gsm_status_t s = dry ? GSM_OK : launch_apply(plans[i], rho[i], u[i], st);
+            if (s != GSM_OK) return s;
+            done[i] = 1;
+            continue;
+        }
+        std::vector<const Plan *> grp;
+        std::vector<const void *> r;
+        std::vector<void *> w;
+        for (int j = i; j < count && (int)grp.size() < kBatchMax; ++j) {
+            if (done[j] || !batch_eligible(plans[j])) continue;
+            if (plans[j]->opt.precision != plans[i]->opt.precision || plans[j]->d != plans[i]->d) continue;
+            grp.push_back(plans[j]);
+            r.push_back(rho[j]);
+            w.push_back(u[j]);
+            done[j] = 1;
+        }
+        BatchArgs *a = new (std::nothrow) BatchArgs();
+        if (!a) {
+            set_error("host allocation failed");
+            return GSM_ERR_OOM;
+        }
+        a->count = (int)grp.size();
+        a->d = plans[i]->d;
+        a->nl = nl;
+        gsm_status_t s;
+        switch (plans[i]->opt.precision) {
+        case GSM_FP64: s = launch_batch_t<F64>(*a, grp, r.data(), w.data(), st, dry); break;
+        case GSM_FP32: s = launch_batch_t<F32>(*a, grp, r.data(), w.data(), st, dry); break;
+        default: s = launch_batch_t<DF64>(*a, grp, r.data(), w.data(), st, dry); break;
+        }
+        delete a;
+        if (s != GSM_OK) return s;
+    }
+    return GSM_OK;
 }
 
 }  // namespace gsm

@@ -214,12 +214,39 @@ def test_apply_host_equals_device(gsm):
 
 
 def test_batched_equals_single(gsm):
+    """Grouped launches and the graph-captured batch give the bits of gsm_apply,
+    for uneven sizes, a ragged tail and a size outside the grouped path."""
     torch = _torch()
-    specs = wl.batch_specs(count=6, sizes=(24, 32, 40))
+    specs = wl.batch_specs(count=7, sizes=(24, 32, 40, 48))
+    specs.append((270, specs[0][1]))    # M = 540 > 512: applied on its own
     plans, rhos = [], []
     for n, params in specs:
         plans.append(gsm.Plan("coulomb3d", 10.0, n))
         rhos.append(torch.tensor(wl.mixture((n, n, n), 10.0, params), device="cuda"))
+    outs = gsm.apply_batched(plans, rhos)
+    singles = [p.apply(r) for p, r in zip(plans, rhos)]
+    for o, s1 in zip(outs, singles):
+        assert torch.equal(o, s1)
+    batch = gsm.Batch(plans, rhos)
+    for _ in range(2):
+        gouts = batch.launch()
+        torch.cuda.synchronize()
+        for o, s1 in zip(gouts, singles):
+            assert torch.equal(o, s1)
+    batch.destroy()
+
+
+@pytest.mark.parametrize("precision", ["fp32x2", "fp32"])
+def test_batched_other_precisions_and_2d(gsm, precision):
+    torch = _torch()
+    dt = torch.float32 if precision == "fp32" else torch.float64
+    plans, rhos = [], []
+    for n in (16, 20, 24):
+        plans.append(gsm.Plan("coulomb3d", 4.0, n, precision=precision))
+        rhos.append(torch.tensor(np.random.default_rng(n).standard_normal((n, n, n)), dtype=dt, device="cuda"))
+    for n in (64, 100):
+        plans.append(gsm.Plan("poisson2d", 6.0, n, precision=precision))
+        rhos.append(torch.tensor(np.random.default_rng(n).standard_normal((n, n)), dtype=dt, device="cuda"))
     outs = gsm.apply_batched(plans, rhos)
     for p, r, o in zip(plans, rhos, outs):
         assert torch.equal(p.apply(r), o)
@@ -269,3 +296,39 @@ def test_autotune_changes_no_bits(gsm, precision):
         u1 = plan.apply(r)
         torch.cuda.synchronize()
         assert torch.equal(u0, u1)
+
+
+# ------------------------------------------------------------------ full sizes
+@pytest.mark.parametrize("precision", ["fp64", "fp32x2"])
+def test_full_size_256_cube_parity(gsm, precision):
+    """The benchmark workload (3D Coulomb, 256^3, 8-Gaussian mixture) in the
+    benchmark's launch configuration (autotuned), against the full oracle."""
+    torch = _torch()
+    rho = wl.coulomb3d_mixture(256, 12.0)
+    plan = gsm.Plan("coulomb3d", 12.0, 256, precision=precision)
+    plan.autotune()
+    u = plan.apply(torch.tensor(rho, device="cuda")).cpu().numpy()
+    uo = oracle.Prepared("coulomb3d", 256, 12.0, S=plan.info()["S"]).run(rho)
+    assert relmax(u, uo) < 1e-12
+
+
+@pytest.mark.parametrize("kernel", ["poisson2d", "coulomb2d"])
+def test_full_size_4096_square_parity(gsm, kernel):
+    """2D at 4096^2 (M = 8192 lines, one per CTA) against the oracle and the
+    closed forms of Examples 2 and 3 summed over the mixture."""
+    import sys, os
+    sys.path.insert(0, os.path.dirname(__file__))
+    from closed_forms import coulomb2d_gaussian, poisson2d_gaussian
+    torch = _torch()
+    params = wl.mixture2d_params()
+    n, L = 4096, 16.0
+    rho = wl.mixture((n, n), L, params)
+    plan = gsm.Plan(kernel, L, n)
+    plan.autotune()
+    u = plan.apply(torch.tensor(rho, device="cuda")).cpu().numpy()
+    uo = oracle.Prepared(kernel, n, L, S=plan.info()["S"]).run(rho)
+    assert relmax(u, uo) < 1e-12
+    X, Y = wl.mesh((n, n), L)
+    f = poisson2d_gaussian if kernel == "poisson2d" else coulomb2d_gaussian
+    closed = sum(a * f(np.sqrt((X - c[0]) ** 2 + (Y - c[1]) ** 2), s[0]) for c, s, a in params)
+    assert relmax(u, closed) < (1e-13 if kernel == "poisson2d" else 1e-12)
