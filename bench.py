@@ -554,6 +554,7 @@ def run_suite(a):
                         p2 = psi.clone()
                         p2[idx] += sgn * 1e-6 * unit
                         e2, _, _ = plan.hartree(p2, stream=stream)
+                        e2 = e2.cpu()     # copied on the stream that computed it
                     vals.append(float(e2))
                 fd = (vals[0] - vals[1]) / 2e-6
                 an = gh[idx].real if unit == 1.0 else gh[idx].imag

@@ -48,12 +48,15 @@ extern "C" {
 typedef struct gsm_plan_s *gsm_plan_t;
 typedef struct gsm_batch_s *gsm_batch_t;
 
-/* Kernels of Eq. kernelPhy plus the dipolar kernel of Eq. dipkerneld. */
+/* Kernels of Eq. kernelPhy, the dipolar kernel of Eq. dipkerneld, and the
+ * Davey-Stewartson potential of Example 5, u = -(1/2 pi) ln|x| * (d_xx rho)
+ * (the Poisson potential of d_xx rho, end of Sec. 2.4). */
 typedef enum {
     GSM_COULOMB_3D = 0,
     GSM_COULOMB_2D = 1,
     GSM_POISSON_2D = 2,
-    GSM_DIPOLAR_3D = 3
+    GSM_DIPOLAR_3D = 3,
+    GSM_DAVEY_STEWARTSON_2D = 4
 } gsm_kernel_t;
 
 /* Arithmetic of the FFT passes and of the multiplier product.
@@ -87,8 +90,9 @@ typedef struct {
     int S;                      /* > 0: use this sinc-quadrature S; 0: the smallest
                                    S whose GS error on [delta, 2 sqrt(d)] is <= gs_eps */
     gsm_precision_t precision;  /* default GSM_FP64 */
-    double dip_n[3];            /* dipolar unit vectors n, m (default e_z, e_z) */
-    double dip_m[3];
+    double dip_n[3];            /* dipolar unit vectors n, m (default e_z, e_z); any */
+    double dip_m[3];            /* directions (both along one axis: octant multiplier,
+                                   otherwise a half-spectrum multiplier table) */
     int debug;                  /* reserved, 0 */
 } gsm_options_t;
 
@@ -119,11 +123,13 @@ void gsm_default_options(gsm_options_t *opt);
  * synchronises that stream before it returns.
  *   out    : receives the handle (set to NULL on failure).
  *   kind   : kernel; d must be 3 for GSM_COULOMB_3D and GSM_DIPOLAR_3D, 2 otherwise.
+ *            GSM_DAVEY_STEWARTSON_2D uses the Gaussian sum of ln r.
  *   L      : half-width of the box [-L, L]^d, > 0.
  *   n      : d points per axis (x first), each even, >= 8, with 2n a product of
  *            2, 3 and 5 and 2n <= 8192.
  *   gs_eps : target accuracy of the Gaussian sum; <= 0 selects the default
- *            (1e-15 relative for 1/r, 1e-13 absolute for ln r).
+ *            (1e-15 relative for 1/r, 1e-13 absolute for ln r).  The ln r sum
+ *            built in double has a floor near 5e-14.
  *   opt    : NULL for defaults.
  * Errors: GSM_ERR_INVALID_ARG, GSM_ERR_UNSUPPORTED_SIZE, GSM_ERR_ACCURACY,
  *         GSM_ERR_OOM, GSM_ERR_CUDA.
@@ -191,8 +197,10 @@ gsm_status_t gsm_apply_batched(int count, const gsm_plan_t *plans, const void *c
  * run is a single cudaGraphLaunch.  The graph holds the given rho[i] and u[i]
  * pointers and each plan's workspace: refill the same rho arrays between
  * launches; the plans must outlive the batch, and no other apply may be in
- * flight on them while the batch runs.  gsm_batch_create synchronises
- * `cuda_stream`; gsm_batch_launch is asynchronous on its stream.
+ * flight on them while the batch runs.  gsm_batch_create first runs the batch
+ * on `cuda_stream` with 4 and with 8 lines per CTA, keeps the faster shape
+ * (so u is written), then records the graph; it synchronises the stream.
+ * gsm_batch_launch is asynchronous on its stream.
  */
 gsm_status_t gsm_batch_create(gsm_batch_t *out, int count, const gsm_plan_t *plans,
                               const void *const *rho, void *const *u, void *cuda_stream);

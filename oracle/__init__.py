@@ -23,13 +23,13 @@ _LIB = os.path.join(_HERE, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
 
-KERNELS = {"coulomb3d": 0, "coulomb2d": 1, "poisson2d": 2, "dipolar3d": 3}
-KERNEL_DIM = {"coulomb3d": 3, "coulomb2d": 2, "poisson2d": 2, "dipolar3d": 3}
+KERNELS = {"coulomb3d": 0, "coulomb2d": 1, "poisson2d": 2, "dipolar3d": 3, "ds2d": 4}
+KERNEL_DIM = {"coulomb3d": 3, "coulomb2d": 2, "poisson2d": 2, "dipolar3d": 3, "ds2d": 2}
 GS_CAP = 1024
 
 # Default accuracy targets of the Gaussian sums (Sec. 3.2-3.3): relative error
 # of 1/r and absolute error of ln r over [delta, 2 sqrt(d)].
-DEFAULT_EPS = {"coulomb3d": 1e-15, "coulomb2d": 1e-15, "dipolar3d": 1e-15, "poisson2d": 1e-13}
+DEFAULT_EPS = {"coulomb3d": 1e-15, "coulomb2d": 1e-15, "dipolar3d": 1e-15, "poisson2d": 1e-13, "ds2d": 1e-13}
 
 
 def build(force: bool = False) -> str:
@@ -125,7 +125,7 @@ def gs(kernel: str, delta: float = 1e-3, eps: float | None = None, S: int = 0, r
     """Gaussian sum (w_q, tau_q) of 1/r (Coulomb kernels) or ln r (Poisson).
 
     Returns (w, tau, S, err), err being E_rel or E_abs on [delta, rmax]."""
-    base = "coulomb3d" if kernel == "dipolar3d" else kernel
+    base = {"dipolar3d": "coulomb3d", "ds2d": "poisson2d"}.get(kernel, kernel)
     d = KERNEL_DIM[kernel]
     if rmax is None:
         rmax = 2.0 * np.sqrt(d)
@@ -151,7 +151,7 @@ def gs_eval(w, tau, r):
 
 
 def gs_error(kernel, w, tau, delta, rmax, ns=4000):
-    base = "coulomb3d" if kernel == "dipolar3d" else kernel
+    base = {"dipolar3d": "coulomb3d", "ds2d": "poisson2d"}.get(kernel, kernel)
     w = np.ascontiguousarray(w, dtype=np.float64)
     tau = np.ascontiguousarray(tau, dtype=np.float64)
     return lib().orc_gs_error(KERNELS[base], len(w), _ptr(w), _ptr(tau), delta, rmax, ns)
@@ -172,7 +172,7 @@ def fftn(a: np.ndarray, sign: int = -1) -> np.ndarray:
 
 
 def taylor_coeffs(kernel: str, w, tau, delta: float):
-    base = "coulomb3d" if kernel == "dipolar3d" else kernel
+    base = {"dipolar3d": "coulomb3d", "ds2d": "poisson2d"}.get(kernel, kernel)
     d = KERNEL_DIM[kernel]
     w = np.ascontiguousarray(w, dtype=np.float64)
     tau = np.ascontiguousarray(tau, dtype=np.float64)

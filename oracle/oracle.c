@@ -394,8 +394,12 @@ int orc_taylor_coeffs(int kernel, int d, int nterms, const double *w, const doub
 /* ------------------------------------------------------------------------ */
 static int base_kernel(int kernel)
 {
-    /* The dipolar potential is a 3D Coulomb potential of d_nm rho (Sec. 2.4). */
-    return kernel == ORC_DIPOLAR_3D ? ORC_COULOMB_3D : kernel;
+    /* The dipolar potential is a 3D Coulomb potential of d_nm rho (Sec. 2.4); */
+    /* the Davey-Stewartson potential a 2D Poisson potential of d_xx rho       */
+    /* (end of Sec. 2.4, Example 5).                                          */
+    if (kernel == ORC_DIPOLAR_3D) return ORC_COULOMB_3D;
+    if (kernel == ORC_DS_2D) return ORC_POISSON_2D;
+    return kernel;
 }
 
 static int kernel_dim(int kernel)
@@ -640,7 +644,7 @@ static int run_scalar(const struct orc_prepared_s *h, const double *rho, double 
     else if (kernel == ORC_COULOMB_2D) s = L / (2.0 * PI);
     else s = -L * L / (2.0 * PI);              /* ln kernel, -1/(2 pi) ln|x| */
     double extra = 0.0;
-    if (kernel == ORC_POISSON_2D) {
+    if (kernel == ORC_POISSON_2D && !dn) {   /* a derivative source has zero mass */
         /* trapezoidal int rho~, summed pairwise (a sequential sum over n^2    */
         /* points drifts by ~1e-12 relative at n = 4096)                       */
         double hu = 2.0 / n[0], hv = 2.0 / n[1];
@@ -703,6 +707,18 @@ int orc_run(const orc_prepared_t *h, const double *rho, double *u, double *i1, d
 #ifdef _OPENMP
     if (p->threads > 0) omp_set_num_threads(p->threads);
 #endif
+    if (p->kernel == ORC_DS_2D) {
+        /* Example 5: u = -(1/2 pi) ln|x| * (d_xx rho), d_xx rho from the Fourier */
+        /* interpolant of the n-grid (taylor_mode 0) or the padded grid (1)       */
+        static const double ex[3] = {1.0, 0.0, 0.0};
+        if (p->taylor_mode == 1) return run_scalar(h, rho, u, i1, i2, ex, ex);
+        size_t N = prod(2, p->n);
+        double *src = malloc(sizeof(double) * N);
+        spectral_derivative(2, p->n, p->L, 1, ex, ex, rho, src);
+        int rc = run_scalar(h, src, u, i1, i2, NULL, NULL);
+        free(src);
+        return rc;
+    }
     if (p->kernel != ORC_DIPOLAR_3D) return run_scalar(h, rho, u, i1, i2, NULL, NULL);
     size_t N = prod(3, p->n);
     double *src = malloc(sizeof(double) * N), *uc = malloc(sizeof(double) * N);

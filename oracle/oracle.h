@@ -9,7 +9,7 @@
 extern "C" {
 #endif
 
-enum { ORC_COULOMB_3D = 0, ORC_COULOMB_2D = 1, ORC_POISSON_2D = 2, ORC_DIPOLAR_3D = 3 };
+enum { ORC_COULOMB_3D = 0, ORC_COULOMB_2D = 1, ORC_POISSON_2D = 2, ORC_DIPOLAR_3D = 3, ORC_DS_2D = 4 };
 enum { ORC_OK = 0, ORC_ERR = 1 };
 
 #define ORC_GS_CAP 1024      /* max number of Gaussian terms */

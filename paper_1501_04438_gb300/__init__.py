@@ -50,7 +50,8 @@ def _io_dtype(precision: str):
 class Plan:
     """A plan (Algorithm 1, "Precomputation") for one kernel, box and grid.
 
-    kernel    : "coulomb3d", "coulomb2d", "poisson2d" or "dipolar3d"
+    kernel    : "coulomb3d", "coulomb2d", "poisson2d", "dipolar3d" or "ds2d"
+                (Davey-Stewartson, the Poisson potential of d_xx rho)
     L         : the box is [-L, L]^d
     n         : points per axis (int, or a tuple x-first)
     gs_eps    : Gaussian-sum accuracy (<= 0: library default)

@@ -8,8 +8,8 @@ import threading
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libgsm.so")
 
-KERNELS = {"coulomb3d": 0, "coulomb2d": 1, "poisson2d": 2, "dipolar3d": 3}
-KERNEL_DIM = {"coulomb3d": 3, "coulomb2d": 2, "poisson2d": 2, "dipolar3d": 3}
+KERNELS = {"coulomb3d": 0, "coulomb2d": 1, "poisson2d": 2, "dipolar3d": 3, "ds2d": 4}
+KERNEL_DIM = {"coulomb3d": 3, "coulomb2d": 2, "poisson2d": 2, "dipolar3d": 3, "ds2d": 2}
 PRECISIONS = {"fp64": 0, "fp32": 1, "fp32x2": 2}
 STATUS = {0: "GSM_OK", 1: "GSM_ERR_INVALID_ARG", 2: "GSM_ERR_UNSUPPORTED_SIZE", 3: "GSM_ERR_OOM",
           4: "GSM_ERR_CUDA", 5: "GSM_ERR_ACCURACY", 6: "GSM_ERR_TIMEOUT", 7: "GSM_ERR_BAD_PLAN"}

@@ -100,7 +100,7 @@ gsm_status_t gsm_plan(gsm_plan_t *out, gsm_kernel_t kind, int d, double L, const
         return GSM_ERR_INVALID_ARG;
     }
     *out = nullptr;
-    if (kind < GSM_COULOMB_3D || kind > GSM_DIPOLAR_3D) {
+    if (kind < GSM_COULOMB_3D || kind > GSM_DAVEY_STEWARTSON_2D) {
         set_error("unknown kernel");
         return GSM_ERR_INVALID_ARG;
     }
@@ -142,12 +142,10 @@ gsm_status_t gsm_plan(gsm_plan_t *out, gsm_kernel_t kind, int d, double L, const
             set_error("dipolar n and m must be unit vectors");
             return GSM_ERR_INVALID_ARG;
         }
+        // n and m along one axis: the multiplier folds onto the octant;
+        // otherwise a half-spectrum table is built (dip_axis = -1)
         for (int a = 0; a < 3; ++a)
             if (fabs(fabs(o.dip_n[a]) - 1.0) == 0.0 && fabs(fabs(o.dip_m[a]) - 1.0) == 0.0) dip_axis = a;
-        if (dip_axis < 0) {
-            set_error("dipolar n and m must both lie along one coordinate axis");
-            return GSM_ERR_UNSUPPORTED_SIZE;
-        }
     }
     Plan *p = new (std::nothrow) Plan();
     if (!p) {
@@ -163,7 +161,8 @@ gsm_status_t gsm_plan(gsm_plan_t *out, gsm_kernel_t kind, int d, double L, const
     p->L = L;
     p->opt = o;
     p->dip_axis = dip_axis;
-    p->eps = gs_eps > 0.0 ? gs_eps : (kind == GSM_POISSON_2D ? 1e-13 : 1e-15);
+    const bool log_kernel = kind == GSM_POISSON_2D || kind == GSM_DAVEY_STEWARTSON_2D;
+    p->eps = gs_eps > 0.0 ? gs_eps : (log_kernel ? 1e-13 : 1e-15);
     cudaGetDevice(&p->device);
     p->magic = kPlanMagic;
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
@@ -297,6 +296,7 @@ struct Batch {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     int count = 0;
+    int nl = 0;   // lines (warps) per CTA chosen by timing
 };
 }  // namespace gsm
 
@@ -317,10 +317,41 @@ gsm_status_t gsm_batch_create(gsm_batch_t *out, int count, const gsm_plan_t *pla
         set_error("empty batch");
         return GSM_ERR_INVALID_ARG;
     }
-    // kernels are prepared outside the capture; the capture records the launches only
-    s = launch_batched(count, ps.data(), rho, u, kBatchLines, nullptr, true);
-    if (s != GSM_OK) return s;
-    GSM_CUDA_TRY(cudaStreamSynchronize(static_cast<cudaStream_t>(cuda_stream)));
+    // kernels are prepared outside the capture, and the lines per CTA of the
+    // grouped launches (4 or 8 warps) are chosen by timing both on the stream
+    cudaStream_t ts = static_cast<cudaStream_t>(cuda_stream);
+    int best_nl = kBatchLines;
+    {
+        float best_ms = 1e30f;
+        cudaEvent_t e0, e1;
+        GSM_CUDA_TRY(cudaEventCreate(&e0));
+        GSM_CUDA_TRY(cudaEventCreate(&e1));
+        for (int nl : {4, 8}) {
+            s = launch_batched(count, ps.data(), rho, u, nl, ts, true);
+            if (s == GSM_OK) s = launch_batched(count, ps.data(), rho, u, nl, ts, false);
+            cudaEventRecord(e0, ts);
+            if (s == GSM_OK) s = launch_batched(count, ps.data(), rho, u, nl, ts, false);
+            cudaEventRecord(e1, ts);
+            cudaError_t e = cudaEventSynchronize(e1);
+            if (s != GSM_OK || e != cudaSuccess) {
+                cudaEventDestroy(e0);
+                cudaEventDestroy(e1);
+                if (s == GSM_OK) {
+                    set_error(std::string("batch timing: ") + cudaGetErrorString(e));
+                    s = GSM_ERR_CUDA;
+                }
+                return s;
+            }
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (ms < best_ms) {
+                best_ms = ms;
+                best_nl = nl;
+            }
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+    }
     cudaStream_t cs;
     GSM_CUDA_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
     Batch *b = new (std::nothrow) Batch();
@@ -331,7 +362,7 @@ gsm_status_t gsm_batch_create(gsm_batch_t *out, int count, const gsm_plan_t *pla
     }
     cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
-        s = launch_batched(count, ps.data(), rho, u, kBatchLines, cs, false);
+        s = launch_batched(count, ps.data(), rho, u, best_nl, cs, false);
         cudaGraph_t g = nullptr;
         cudaError_t e2 = cudaStreamEndCapture(cs, &g);
         if (s == GSM_OK && e2 != cudaSuccess) e = e2;
@@ -350,6 +381,7 @@ gsm_status_t gsm_batch_create(gsm_batch_t *out, int count, const gsm_plan_t *pla
         return s;
     }
     b->count = count;
+    b->nl = best_nl;
     b->magic = kBatchMagic;
     *out = reinterpret_cast<gsm_batch_t>(b);
     return GSM_OK;
@@ -429,7 +461,7 @@ gsm_status_t gsm_plan_info(gsm_plan_t h, gsm_plan_info_t *info)
     info->c2 = p->c2;
     info->precision = p->opt.precision;
     const size_t me = p->opt.precision == GSM_FP64 ? 8 : (p->opt.precision == GSM_FP32 ? 4 : 8);
-    info->bytes_multiplier = p->mult_elems * me;
+    info->bytes_multiplier = p->mult_elems_pass * me;
     info->bytes_workspace = p->work1_bytes + p->work2_bytes;
     info->npasses = p->d == 3 ? 5 : 3;
     const PassCfg *cf3[5] = {&p->cfg_xf, &p->cfg_yf, &p->cfg_conv, &p->cfg_yi, &p->cfg_xi};

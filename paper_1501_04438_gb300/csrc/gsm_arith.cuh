@@ -146,6 +146,7 @@ struct F64 {
     using io_t = double;
     static constexpr int kId = 0;
     static constexpr int kPadShift = 3;   // one pad element per 8 (128 bytes)
+    static constexpr bool kPrune = true;  // FP64-pipe bound: prune padded/cropped stages
     __device__ static __forceinline__ cx<real> ld(const scplx &v) { return {v.x, v.y}; }
     __device__ static __forceinline__ scplx st(cx<real> a) { return make_double2(a.re, a.im); }
     __device__ static __forceinline__ cx<real> tw(const tw_t &v) { return {v.x, v.y}; }
@@ -163,6 +164,7 @@ struct F32 {
     using io_t = float;
     static constexpr int kId = 1;
     static constexpr int kPadShift = 4;   // one pad element per 16 (128 bytes)
+    static constexpr bool kPrune = false;
     __device__ static __forceinline__ cx<real> ld(const scplx &v) { return {v.x, v.y}; }
     __device__ static __forceinline__ scplx st(cx<real> a) { return make_float2(a.re, a.im); }
     __device__ static __forceinline__ cx<real> tw(const tw_t &v) { return {v.x, v.y}; }
@@ -180,6 +182,7 @@ struct DF64 {
     using io_t = double;
     static constexpr int kId = 2;
     static constexpr int kPadShift = 3;
+    static constexpr bool kPrune = false;
     __device__ static __forceinline__ cx<real> ld(const scplx &v) { return {df{v.x, v.y}, df{v.z, v.w}}; }
     __device__ static __forceinline__ scplx st(cx<real> a) { return make_float4(a.re.hi, a.re.lo, a.im.hi, a.im.lo); }
     __device__ static __forceinline__ cx<real> tw(const tw_t &v) { return {df{v.x, v.y}, df{v.z, v.w}}; }

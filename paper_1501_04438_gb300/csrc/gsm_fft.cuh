@@ -15,6 +15,8 @@
 // Unnormalised: forward uses exp(-2 pi i jk/M), inverse exp(+2 pi i jk/M).
 #pragma once
 
+#include <type_traits>
+
 #include "gsm_arith.cuh"
 
 namespace gsm {
@@ -70,8 +72,10 @@ __device__ __forceinline__ void bfly4(cx<R> *v)
     v[3] = csub(a1, a3);
 }
 
+// Radix 8, plain form: the rotations by w8 and w8^3 are formed first (used
+// for FP32 and double-float, whose passes are not limited by arithmetic).
 template <class R, bool FWD>
-__device__ __forceinline__ void bfly8(cx<R> *v)
+__device__ __forceinline__ void bfly8_plain(cx<R> *v)
 {
     cx<R> a[4], b[4];
 #pragma unroll
@@ -79,7 +83,6 @@ __device__ __forceinline__ void bfly8(cx<R> *v)
         a[t] = cadd(v[t], v[t + 4]);
         b[t] = csub(v[t], v[t + 4]);
     }
-    // b_t *= w8^t, w8 = exp(-+ i pi/4)
     {
         cx<R> z = b[1];
         if (FWD) b[1] = {rmulk(radd(z.re, z.im), kSqrtHalf), rmulk(rsub(z.im, z.re), kSqrtHalf)};
@@ -99,6 +102,113 @@ __device__ __forceinline__ void bfly8(cx<R> *v)
         v[2 * k + 1] = b[k];
     }
 }
+
+// Radix 8 as two radix-4 transforms of a_t = x_t + x_{t+4} (even outputs)
+// and of b_t = (x_t - x_{t+4}) w8^t (odd outputs).  The 1/sqrt(2) of w8 and
+// w8^3 is applied in the last additions (x + c s contracts to one FMA; used
+// for FP64, whose passes are limited by the FP64 pipe):
+//   u1 = b1 w8 sqrt2, u3 = b3 w8^3 sqrt2 (additions only),
+//   B0,2 = (b0 + b2') +- c (u1 + u3),  B1,3 = (b0 - b2') +- c rot(u1 - u3).
+template <class R, bool FWD>
+__device__ __forceinline__ void bfly8_odd(const cx<R> &b0, const cx<R> &b1, const cx<R> &b2, const cx<R> &b3,
+                                          cx<R> *B, bool half)
+{
+    cx<R> u1, u3;
+    if (FWD) {   // w8 = (1 - i)/sqrt2, w8^3 = (-1 - i)/sqrt2
+        u1 = {radd(b1.re, b1.im), rsub(b1.im, b1.re)};
+        u3 = {rsub(b3.im, b3.re), rneg(radd(b3.re, b3.im))};
+    } else {     // conjugates
+        u1 = {rsub(b1.re, b1.im), radd(b1.re, b1.im)};
+        u3 = {rneg(radd(b3.re, b3.im)), rsub(b3.re, b3.im)};
+    }
+    const cx<R> b2r = rot_quarter<R, FWD>(b2);
+    const cx<R> p = cadd(b0, b2r), q = csub(b0, b2r);
+    const cx<R> s = cadd(u1, u3), d = rot_quarter<R, FWD>(csub(u1, u3));
+    B[0] = {radd(p.re, rmulk(s.re, kSqrtHalf)), radd(p.im, rmulk(s.im, kSqrtHalf))};
+    B[1] = {radd(q.re, rmulk(d.re, kSqrtHalf)), radd(q.im, rmulk(d.im, kSqrtHalf))};
+    if (half) return;
+    B[2] = {rsub(p.re, rmulk(s.re, kSqrtHalf)), rsub(p.im, rmulk(s.im, kSqrtHalf))};
+    B[3] = {rsub(q.re, rmulk(d.re, kSqrtHalf)), rsub(q.im, rmulk(d.im, kSqrtHalf))};
+}
+
+template <class R, bool FWD>
+__device__ __forceinline__ void bfly8(cx<R> *v)
+{
+    cx<R> a[4], b[4], B[4];
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+        a[t] = cadd(v[t], v[t + 4]);
+        b[t] = csub(v[t], v[t + 4]);
+    }
+    bfly4<R, FWD>(a);
+    bfly8_odd<R, FWD>(b[0], b[1], b[2], b[3], B, false);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        v[2 * k] = a[k];
+        v[2 * k + 1] = B[k];
+    }
+}
+
+// --- pruned butterflies -------------------------------------------------------
+// First stage of a transform whose inputs x_t, t >= R/2, are zero (zero
+// padding): a_t = b_t = x_t.  Last stage of a transform of which only the
+// outputs t < R/2 are kept (the crop): the other outputs are not formed.
+template <class R, bool FWD>
+__device__ __forceinline__ void bfly8_half_in(cx<R> *v)
+{
+    cx<R> a[4] = {v[0], v[1], v[2], v[3]}, B[4];
+    bfly4<R, FWD>(a);
+    bfly8_odd<R, FWD>(v[0], v[1], v[2], v[3], B, false);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        v[2 * k] = a[k];
+        v[2 * k + 1] = B[k];
+    }
+}
+
+template <class R, bool FWD>
+__device__ __forceinline__ void bfly8_half_out(cx<R> *v)
+{
+    cx<R> a[4], b[4], B[4];
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+        a[t] = cadd(v[t], v[t + 4]);
+        b[t] = csub(v[t], v[t + 4]);
+    }
+    // outputs 0 and 1 of the radix-4 transform of a
+    const cx<R> p = cadd(a[0], a[2]), q = csub(a[0], a[2]);
+    const cx<R> s = cadd(a[1], a[3]), d = rot_quarter<R, FWD>(csub(a[1], a[3]));
+    bfly8_odd<R, FWD>(b[0], b[1], b[2], b[3], B, true);
+    v[0] = cadd(p, s);
+    v[1] = B[0];
+    v[2] = cadd(q, d);
+    v[3] = B[1];
+}
+
+template <class R, bool FWD>
+__device__ __forceinline__ void bfly4_half_in(cx<R> *v)
+{
+    const cx<R> x0 = v[0], x1 = v[1], r1 = rot_quarter<R, FWD>(v[1]);
+    v[0] = cadd(x0, x1);
+    v[1] = cadd(x0, r1);
+    v[2] = csub(x0, x1);
+    v[3] = csub(x0, r1);
+}
+
+template <class R, bool FWD>
+__device__ __forceinline__ void bfly4_half_out(cx<R> *v)
+{
+    const cx<R> p = cadd(v[0], v[2]), q = csub(v[0], v[2]);
+    const cx<R> s = cadd(v[1], v[3]), d = rot_quarter<R, FWD>(csub(v[1], v[3]));
+    v[0] = cadd(p, s);
+    v[1] = cadd(q, d);
+}
+
+template <class R, bool FWD>
+__device__ __forceinline__ void bfly2_half_in(cx<R> *v) { v[1] = v[0]; }
+
+template <class R, bool FWD>
+__device__ __forceinline__ void bfly2_half_out(cx<R> *v) { v[0] = cadd(v[0], v[1]); }
 
 template <class R, bool FWD>
 __device__ __forceinline__ void bfly3(cx<R> *v)
@@ -130,14 +240,29 @@ __device__ __forceinline__ void bfly5(cx<R> *v)
     v[3] = csub(p2, q2);
 }
 
-template <class R, int RAD, bool FWD>
+// HALF = 0: full radix-RAD DFT; 1: inputs t >= RAD/2 are zero; 2: only the
+// outputs t < RAD/2 are formed (even RAD only).
+template <class R, int RAD, bool FWD, int HALF>
 __device__ __forceinline__ void bfly(cx<R> *v)
 {
-    if constexpr (RAD == 2) bfly2<R, FWD>(v);
-    else if constexpr (RAD == 3) bfly3<R, FWD>(v);
-    else if constexpr (RAD == 4) bfly4<R, FWD>(v);
-    else if constexpr (RAD == 5) bfly5<R, FWD>(v);
-    else bfly8<R, FWD>(v);
+    if constexpr (RAD == 2) {
+        if constexpr (HALF == 1) bfly2_half_in<R, FWD>(v);
+        else if constexpr (HALF == 2) bfly2_half_out<R, FWD>(v);
+        else bfly2<R, FWD>(v);
+    } else if constexpr (RAD == 3) {
+        bfly3<R, FWD>(v);
+    } else if constexpr (RAD == 4) {
+        if constexpr (HALF == 1) bfly4_half_in<R, FWD>(v);
+        else if constexpr (HALF == 2) bfly4_half_out<R, FWD>(v);
+        else bfly4<R, FWD>(v);
+    } else if constexpr (RAD == 5) {
+        bfly5<R, FWD>(v);
+    } else {
+        if constexpr (HALF == 1) bfly8_half_in<R, FWD>(v);
+        else if constexpr (HALF == 2) bfly8_half_out<R, FWD>(v);
+        else if constexpr (std::is_same<R, double>::value) bfly8<R, FWD>(v);
+        else bfly8_plain<R, FWD>(v);
+    }
 }
 
 // ---------------------------------------------------------------- groups
@@ -172,11 +297,16 @@ __device__ __forceinline__ Group make_group(int T, int nl)
 // One Stockham stage on one line s[pidx(0..M-1)] by the group.  NB = upper
 // bound of butterflies per thread (compile time); every thread first loads
 // its butterflies, the group synchronises, then every thread stores.
-template <class Pol, int RAD, bool FWD, int NB>
+// HALF = 1 (first stage of a zero-padded transform): only the inputs t < RAD/2
+// are read; HALF = 2 (last stage of a cropped transform): only the outputs
+// t < RAD/2, which land in the first half of the line, are formed and stored.
+template <class Pol, int RAD, bool FWD, int NB, int HALF>
 __device__ __forceinline__ void fft_stage(typename Pol::scplx *s, int M, int Ns,
                                           const typename Pol::tw_t *__restrict__ tw, const Group &g)
 {
     using R = typename Pol::real;
+    constexpr int NIN = HALF == 1 ? RAD / 2 : RAD;
+    constexpr int NOUT = HALF == 2 ? RAD / 2 : RAD;
     const int nb = M / RAD;
     const int step = M / (Ns * RAD);   // twiddle-table stride of this stage
     cx<R> v[NB][RAD];
@@ -185,16 +315,16 @@ __device__ __forceinline__ void fft_stage(typename Pol::scplx *s, int M, int Ns,
         const int b = g.t + i * g.T;
         if (b < nb) {
 #pragma unroll
-            for (int t = 0; t < RAD; ++t) v[i][t] = Pol::ld(s[pidx<Pol>(b + t * nb)]);
+            for (int t = 0; t < NIN; ++t) v[i][t] = Pol::ld(s[pidx<Pol>(b + t * nb)]);
             if (Ns > 1) {
                 const int j = b % Ns;
 #pragma unroll
-                for (int t = 1; t < RAD; ++t) {
+                for (int t = 1; t < NIN; ++t) {
                     cx<R> w = Pol::tw(tw[j * t * step]);
                     v[i][t] = FWD ? cmul(v[i][t], w) : cmulc(v[i][t], w);
                 }
             }
-            bfly<R, RAD, FWD>(v[i]);
+            bfly<R, RAD, FWD, HALF>(v[i]);
         }
     }
     group_sync(g);
@@ -205,7 +335,7 @@ __device__ __forceinline__ void fft_stage(typename Pol::scplx *s, int M, int Ns,
             const int j = b % Ns;
             const int d0 = (b - j) * RAD + j;
 #pragma unroll
-            for (int t = 0; t < RAD; ++t) s[pidx<Pol>(d0 + t * Ns)] = Pol::st(v[i][t]);
+            for (int t = 0; t < NOUT; ++t) s[pidx<Pol>(d0 + t * Ns)] = Pol::st(v[i][t]);
         }
     }
     group_sync(g);
@@ -215,23 +345,37 @@ __device__ __forceinline__ void fft_stage(typename Pol::scplx *s, int M, int Ns,
 // per thread (M <= EMAX * T).  The caller synchronises the group (or CTA)
 // after writing the line; the last stage ends with a group barrier, so the
 // group may read the result right away.  The schedule lists radices in the
-// order 8, 4, 2, 5, 3 (make_sched): each radix gets one loop of its own.
-template <class Pol, bool FWD, int EMAX>
+// order 8, 4, 2, 5, 3 (make_sched): each radix gets one loop of its own, so the
+// first stage has an even radix whenever M is even.
+// ZPAD: the second half of the input is zero and is not read (the first stage
+// is pruned); the caller need not write it.  CROP: only the first half of the
+// output is needed (the last stage is pruned when its radix is even; the
+// second half of the line is then left undefined).  Both apply to policies
+// with kPrune only; for the others the full stages run.
+template <class Pol, bool FWD, int EMAX, bool ZPAD_ = false, bool CROP_ = false>
 __device__ __forceinline__ void fft_line(typename Pol::scplx *s, const Sched &sc,
                                          const typename Pol::tw_t *__restrict__ tw, const Group &g)
 {
+    // pruning pays where the arithmetic pipe is the limit: FP64 only
+    constexpr bool ZPAD = ZPAD_ && Pol::kPrune, CROP = CROP_ && Pol::kPrune;
     int Ns = 1, st = 0;
-    const int M = sc.M;
-    for (; st < sc.nst && sc.r[st] == 8; ++st, Ns *= 8)
-        fft_stage<Pol, 8, FWD, (EMAX + 7) / 8>(s, M, Ns, tw, g);
-    for (; st < sc.nst && sc.r[st] == 4; ++st, Ns *= 4)
-        fft_stage<Pol, 4, FWD, (EMAX + 3) / 4>(s, M, Ns, tw, g);
-    for (; st < sc.nst && sc.r[st] == 2; ++st, Ns *= 2)
-        fft_stage<Pol, 2, FWD, (EMAX + 1) / 2>(s, M, Ns, tw, g);
-    for (; st < sc.nst && sc.r[st] == 5; ++st, Ns *= 5)
-        fft_stage<Pol, 5, FWD, (EMAX + 4) / 5>(s, M, Ns, tw, g);
-    for (; st < sc.nst && sc.r[st] == 3; ++st, Ns *= 3)
-        fft_stage<Pol, 3, FWD, (EMAX + 2) / 3>(s, M, Ns, tw, g);
+    const int M = sc.M, last = sc.nst - 1;
+#define GSM_STAGE(RAD)                                                                         \
+    do {                                                                                       \
+        constexpr int NB = (EMAX + RAD - 1) / RAD;                                             \
+        if (ZPAD && st == 0 && (RAD % 2) == 0)                                                 \
+            fft_stage<Pol, RAD, FWD, NB, (RAD % 2 == 0) ? 1 : 0>(s, M, Ns, tw, g);             \
+        else if (CROP && st == last && st > 0 && (RAD % 2) == 0)                               \
+            fft_stage<Pol, RAD, FWD, NB, (RAD % 2 == 0) ? 2 : 0>(s, M, Ns, tw, g);             \
+        else                                                                                   \
+            fft_stage<Pol, RAD, FWD, NB, 0>(s, M, Ns, tw, g);                                  \
+    } while (0)
+    for (; st < sc.nst && sc.r[st] == 8; ++st, Ns *= 8) GSM_STAGE(8);
+    for (; st < sc.nst && sc.r[st] == 4; ++st, Ns *= 4) GSM_STAGE(4);
+    for (; st < sc.nst && sc.r[st] == 2; ++st, Ns *= 2) GSM_STAGE(2);
+    for (; st < sc.nst && sc.r[st] == 5; ++st, Ns *= 5) GSM_STAGE(5);
+    for (; st < sc.nst && sc.r[st] == 3; ++st, Ns *= 3) GSM_STAGE(3);
+#undef GSM_STAGE
 }
 
 }  // namespace gsm

@@ -53,7 +53,9 @@ struct Plan {
     void *d_tw[3] = {nullptr, nullptr, nullptr};  // twiddle tables per axis
     void *d_work1 = nullptr, *d_work2 = nullptr;  // FFT workspace
     size_t work1_bytes = 0, work2_bytes = 0;
-    size_t mult_elems = 0;
+    size_t mult_elems = 0;         // octant entries (FP64 tables)
+    size_t mult_elems_pass = 0;    // entries of the pass-precision table
+    bool mult_full = false;        // pass table covers the half spectrum (general dipolar)
     void *d_stage_in = nullptr, *d_stage_out = nullptr;   // gsm_apply_host staging
     double *d_scratch = nullptr;                           // energy partial sums
     size_t scratch_elems = 0;
@@ -75,7 +77,8 @@ gsm_status_t launch_pass(const Plan *p, int pass, const void *rho, void *u, cuda
 gsm_status_t autotune_plan(Plan *p, cudaStream_t st, std::string *report);
 gsm_status_t launch_batched(int count, const Plan *const *plans, const void *const *rho, void *const *u,
                             int nl, cudaStream_t st, bool dry);
-constexpr int kBatchLines = 8;   // lines (warps) per CTA of the grouped batch kernels
+constexpr int kBatchLines = 4;      // default lines (warps) per CTA of the grouped batch kernels
+constexpr int kBatchMaxLines = 8;   // largest shape tried (bounds the CTA size)
 gsm_status_t launch_hartree(Plan *p, const void *psi, void *u, void *energy, void *grad,
                             cudaStream_t st);
 gsm_status_t launch_fft_lines(int M, int nlines, int sign, gsm_precision_t prec,

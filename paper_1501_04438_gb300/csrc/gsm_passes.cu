@@ -60,7 +60,8 @@ __device__ __forceinline__ void body_xf(const typename Pol::io_t *__restrict__ r
     const int y0 = bx * 2 * nl;
     const int ya = y0 + 2 * l;
     const typename Pol::io_t *slab = rho + (size_t)z * ny * nx;
-    for (int x = g.t; x < M; x += g.T) {
+    // x >= nx is zero padding: written only when the first stage reads it
+    for (int x = g.t; x < (Pol::kPrune ? nx : M); x += g.T) {
         R a = Pol::zero(), b = Pol::zero();
         if (x < nx) {
             if (ya < ny) a = Pol::from_io(slab[(size_t)ya * nx + x]);
@@ -69,7 +70,7 @@ __device__ __forceinline__ void body_xf(const typename Pol::io_t *__restrict__ r
         s[pidx<Pol>(x)] = Pol::st(cx<R>{a, b});
     }
     group_sync(g);
-    fft_line<Pol, true, EMAX>(s, sc, tw, g);
+    fft_line<Pol, true, EMAX, true, false>(s, sc, tw, g);
     __syncthreads();
     // Z = A + iB with A, B the transforms of the two real rows:
     // 2A[k] = Z[k] + conj Z[-k], 2B[k] = -i (Z[k] - conj Z[-k]); the factor 2
@@ -112,13 +113,13 @@ __device__ __forceinline__ void body_yf(const S_t<Pol> *__restrict__ W1, S_t<Pol
     const int z0 = bx * nl;
     const int z = z0 + l;
     const S_t<Pol> *in = W1 + ((size_t)z * hx + kx) * ny;
-    for (int y = g.t; y < M; y += g.T) {
+    for (int y = g.t; y < (Pol::kPrune ? ny : M); y += g.T) {   // y >= ny: zero padding
         S_t<Pol> v = Pol::st(cx<R>{Pol::zero(), Pol::zero()});
         if (y < ny && z < nz) v = in[y];
         s[pidx<Pol>(y)] = v;
     }
     group_sync(g);
-    fft_line<Pol, true, EMAX>(s, sc, tw, g);
+    fft_line<Pol, true, EMAX, true, false>(s, sc, tw, g);
     __syncthreads();
     const S_t<Pol> *s0 = reinterpret_cast<const S_t<Pol> *>(smem_raw);
     S_t<Pol> *out = W2 + (size_t)kx * M * nz;
@@ -143,11 +144,12 @@ __global__ void __launch_bounds__(kMaxThreads) k_yf(const S_t<Pol> *__restrict__
 // multiplier mult[row + min(k, M - k)], inverse, keep the first n.
 // 3D: line = kx * My + ky, row = (kx * (ny + 1) + min(ky, My - ky)) * (nz + 1).
 // 2D: line = kx, row = kx * (ny + 1).  Entirely group-local: no CTA barrier.
+// full: the multiplier is stored for the whole half spectrum, row line * M.
 template <class Pol, int EMAX>
 __device__ __forceinline__ void body_conv(S_t<Pol> *__restrict__ W, const typename Pol::mult_t *__restrict__ mult,
                                           int nlines, int n, int is3d, int My, int ny1, const Sched &sc, int nl,
                                           int gthr, const typename Pol::tw_t *__restrict__ tw, int bx,
-                                          unsigned char *smem_raw)
+                                          unsigned char *smem_raw, bool full = false)
 {
     using R = typename Pol::real;
     const int M = sc.M, LS = line_stride<Pol>(M);
@@ -157,38 +159,47 @@ __device__ __forceinline__ void body_conv(S_t<Pol> *__restrict__ W, const typena
     const int line = bx * nl + l;
     if (line >= nlines) return;   // the whole group leaves; no CTA barrier follows
     S_t<Pol> *w = W + (size_t)line * n;
-    for (int z = g.t; z < M; z += g.T) {
+    for (int z = g.t; z < (Pol::kPrune ? n : M); z += g.T) {   // z >= n: zero padding
         S_t<Pol> v = Pol::st(cx<R>{Pol::zero(), Pol::zero()});
         if (z < n) v = w[z];
         s[pidx<Pol>(z)] = v;
     }
     group_sync(g);
-    fft_line<Pol, true, EMAX>(s, sc, tw, g);
-    size_t row;
-    if (is3d) {
-        const int kx = line / My, ky = line - kx * My;
-        row = ((size_t)kx * ny1 + min(ky, My - ky)) * (n + 1);
+    fft_line<Pol, true, EMAX, true, false>(s, sc, tw, g);
+    if (full) {
+        const typename Pol::mult_t *mrow = mult + (size_t)line * M;
+        for (int k = g.t; k < M; k += g.T) {
+            const int p = pidx<Pol>(k);
+            s[p] = Pol::st(cscale(Pol::ld(s[p]), Pol::mult(mrow[k])));
+        }
     } else {
-        row = (size_t)line * (n + 1);
-    }
-    const typename Pol::mult_t *mrow = mult + row;
-    for (int k = g.t; k < M; k += g.T) {
-        const R m = Pol::mult(mrow[min(k, M - k)]);
-        const int p = pidx<Pol>(k);
-        s[p] = Pol::st(cscale(Pol::ld(s[p]), m));
+        size_t row;
+        if (is3d) {
+            const int kx = line / My, ky = line - kx * My;
+            row = ((size_t)kx * ny1 + min(ky, My - ky)) * (n + 1);
+        } else {
+            row = (size_t)line * (n + 1);
+        }
+        const typename Pol::mult_t *mrow = mult + row;
+        for (int k = g.t; k < M; k += g.T) {
+            const R m = Pol::mult(mrow[min(k, M - k)]);
+            const int p = pidx<Pol>(k);
+            s[p] = Pol::st(cscale(Pol::ld(s[p]), m));
+        }
     }
     group_sync(g);
-    fft_line<Pol, false, EMAX>(s, sc, tw, g);
+    fft_line<Pol, false, EMAX, false, true>(s, sc, tw, g);
     for (int z = g.t; z < n; z += g.T) w[z] = s[pidx<Pol>(z)];
 }
 
 template <class Pol, int EMAX>
 __global__ void __launch_bounds__(kMaxThreads) k_conv(S_t<Pol> *__restrict__ W, const typename Pol::mult_t *__restrict__ mult,
                                                       int nlines, int n, int is3d, int My, int ny1, Sched sc,
-                                                      int nl, int gthr, const typename Pol::tw_t *__restrict__ tw)
+                                                      int nl, int gthr, const typename Pol::tw_t *__restrict__ tw,
+                                                      int full)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    body_conv<Pol, EMAX>(W, mult, nlines, n, is3d, My, ny1, sc, nl, gthr, tw, blockIdx.x, smem_raw);
+    body_conv<Pol, EMAX>(W, mult, nlines, n, is3d, My, ny1, sc, nl, gthr, tw, blockIdx.x, smem_raw, full != 0);
 }
 
 // ------------------------------------------------------------------ pass yi
@@ -213,7 +224,7 @@ __device__ __forceinline__ void body_yi(const S_t<Pol> *__restrict__ W2, S_t<Pol
     }
     __syncthreads();
     const int z = z0 + l;
-    fft_line<Pol, false, EMAX>(s, sc, tw, g);
+    fft_line<Pol, false, EMAX, false, true>(s, sc, tw, g);
     if (z < nz) {
         S_t<Pol> *out = W1 + ((size_t)z * hx + kx) * ny;
         for (int y = g.t; y < ny; y += g.T) out[y] = s[pidx<Pol>(y)];
@@ -261,7 +272,7 @@ __device__ __forceinline__ void body_xi(const S_t<Pol> *__restrict__ W1, typenam
         if (k > 0 && k < nx) s0[ll * LS + pidx<Pol>(M - k)] = Pol::st(cadd(cconj(A), cmul_posi(cconj(B))));
     }
     __syncthreads();
-    fft_line<Pol, false, EMAX>(s, sc, tw, g);
+    fft_line<Pol, false, EMAX, false, true>(s, sc, tw, g);
     const int ya = y0 + 2 * l;
     typename Pol::io_t *slab = u + (size_t)z * ny * nx;
     for (int x = g.t; x < nx; x += g.T) {
@@ -325,6 +336,7 @@ struct InstDesc {
     int n[3], M[3];
     Sched sc[3];
     int gx[5];   // x extent of each pass's tile grid
+    int full;    // multiplier over the whole half spectrum
 };
 
 struct BatchArgs {
@@ -333,8 +345,8 @@ struct BatchArgs {
     InstDesc inst[kBatchMax];
 };
 
-template <class Pol, int PASS>
-__global__ void __launch_bounds__(kMaxThreads) k_batch(const __grid_constant__ BatchArgs a)
+template <class Pol, int PASS, int D>
+__global__ void __launch_bounds__(32 * kBatchMaxLines) k_batch(const __grid_constant__ BatchArgs a)
 {
     using io = typename Pol::io_t;
     using tw = typename Pol::tw_t;
@@ -346,7 +358,7 @@ __global__ void __launch_bounds__(kMaxThreads) k_batch(const __grid_constant__ B
     const int t = b - a.prefix[i];
     const int gx = d.gx[PASS];
     const int bx = t % gx, by = t / gx;
-    const int nx = d.n[0], ny = d.n[1], nz = a.d == 3 ? d.n[2] : 1, hx = nx + 1;
+    const int nx = d.n[0], ny = d.n[1], nz = D == 3 ? d.n[2] : 1, hx = nx + 1;
     S_t<Pol> *W1 = static_cast<S_t<Pol> *>(d.W1);
     S_t<Pol> *W2 = static_cast<S_t<Pol> *>(d.W2);
     const auto *mult = static_cast<const typename Pol::mult_t *>(d.mult);
@@ -354,17 +366,18 @@ __global__ void __launch_bounds__(kMaxThreads) k_batch(const __grid_constant__ B
     const tw *tw1 = static_cast<const tw *>(d.tw[1]);
     const tw *tw2 = static_cast<const tw *>(d.tw[2]);
     const int nl = a.nl;
-    const int last = a.d == 3 ? 4 : 2;
-    if (PASS == 0) {
+    constexpr int last = D == 3 ? 4 : 2;
+    if constexpr (PASS == 0) {
         body_xf<Pol, kBatchEmax>(static_cast<const io *>(d.rho), W1, nx, ny, hx, d.sc[0], nl, 32, tw0, bx, by, smem_raw);
-    } else if (PASS == last) {
+    } else if constexpr (PASS == last) {
         body_xi<Pol, kBatchEmax>(W1, static_cast<io *>(d.u), nx, ny, hx, d.sc[0], nl, 32, tw0, bx, by, smem_raw);
-    } else if (a.d == 2) {
-        body_conv<Pol, kBatchEmax>(W1, mult, hx, ny, 0, 1, ny + 1, d.sc[1], nl, 32, tw1, bx, smem_raw);
-    } else if (PASS == 1) {
+    } else if constexpr (D == 2) {
+        body_conv<Pol, kBatchEmax>(W1, mult, hx, ny, 0, 1, ny + 1, d.sc[1], nl, 32, tw1, bx, smem_raw, d.full != 0);
+    } else if constexpr (PASS == 1) {
         body_yf<Pol, kBatchEmax>(W1, W2, ny, nz, hx, d.sc[1], nl, 32, tw1, bx, by, smem_raw);
-    } else if (PASS == 2) {
-        body_conv<Pol, kBatchEmax>(W2, mult, hx * d.M[1], nz, 1, d.M[1], ny + 1, d.sc[2], nl, 32, tw2, bx, smem_raw);
+    } else if constexpr (PASS == 2) {
+        body_conv<Pol, kBatchEmax>(W2, mult, hx * d.M[1], nz, 1, d.M[1], ny + 1, d.sc[2], nl, 32, tw2, bx, smem_raw,
+                                   d.full != 0);
     } else {
         body_yi<Pol, kBatchEmax>(W2, W1, ny, nz, hx, d.sc[1], nl, 32, tw1, bx, by, smem_raw);
     }
@@ -584,7 +597,8 @@ void launch_pass_t(const Plan *p, int pass, const void *rho_v, void *u_v, cudaSt
         const PassCfg &c = p->cfg_conv;
         with_emax(c, [&](auto E) {
             k_conv<Pol, E()><<<(hx + c.nl - 1) / c.nl, c.nthr, c.smem, st>>>(W1, mult, hx, ny, 0, 1, ny + 1,
-                                                                          p->sched[1], c.nl, c.gthr, twy);
+                                                                          p->sched[1], c.nl, c.gthr, twy,
+                                                                          p->mult_full ? 1 : 0);
         });
     } else {
         const tw *twz = static_cast<const tw *>(p->d_tw[2]);
@@ -600,7 +614,7 @@ void launch_pass_t(const Plan *p, int pass, const void *rho_v, void *u_v, cudaSt
             const int nlines = hx * My;
             with_emax(c, [&](auto E) {
                 k_conv<Pol, E()><<<(nlines + c.nl - 1) / c.nl, c.nthr, c.smem, st>>>(
-                    W2, mult, nlines, nz, 1, My, ny + 1, p->sched[2], c.nl, c.gthr, twz);
+                    W2, mult, nlines, nz, 1, My, ny + 1, p->sched[2], c.nl, c.gthr, twz, p->mult_full ? 1 : 0);
             });
         } else {
             const PassCfg &c = p->cfg_yi;
@@ -1081,6 +1095,7 @@ gsm_status_t launch_batch_t(BatchArgs &a, const std::vector<const Plan *> &plans
         d.W1 = p->d_work1;
         d.W2 = p->d_work2;
         d.mult = p->d_mult;
+        d.full = p->mult_full ? 1 : 0;
         for (int ax = 0; ax < 3; ++ax) {
             d.n[ax] = ax < p->d ? p->n[ax] : 1;
             d.M[ax] = ax < p->d ? p->M[ax] : 1;
@@ -1105,12 +1120,16 @@ gsm_status_t launch_batch_t(BatchArgs &a, const std::vector<const Plan *> &plans
         if (e == cudaSuccess) e = raise_smem(kernel, smem);
         if (e == cudaSuccess && !dry) kernel<<<a.prefix[a.count], a.nl * 32, smem, st>>>(a);
     };
-    run(k_batch<Pol, 0>, 0);
-    run(k_batch<Pol, 1>, 1);
-    run(k_batch<Pol, 2>, 2);
     if (np == 5) {
-        run(k_batch<Pol, 3>, 3);
-        run(k_batch<Pol, 4>, 4);
+        run(k_batch<Pol, 0, 3>, 0);
+        run(k_batch<Pol, 1, 3>, 1);
+        run(k_batch<Pol, 2, 3>, 2);
+        run(k_batch<Pol, 3, 3>, 3);
+        run(k_batch<Pol, 4, 3>, 4);
+    } else {
+        run(k_batch<Pol, 0, 2>, 0);
+        run(k_batch<Pol, 1, 2>, 1);
+        run(k_batch<Pol, 2, 2>, 2);
     }
     GSM_CUDA_TRY(e);
     GSM_CUDA_TRY(cudaGetLastError());

@@ -27,7 +27,10 @@ constexpr int kTaylorJ = 44;     // terms of the small-tau series of g
 constexpr double kTauSeries = 1.0;   // g by series below, by w(z) above
 constexpr double kTauGauss = 4.0;    // g by the Gaussian transform at and above
 
-__device__ __forceinline__ bool is_log_kernel(int kind) { return kind == GSM_POISSON_2D; }
+__device__ __forceinline__ bool is_log_kernel(int kind)
+{
+    return kind == GSM_POISSON_2D || kind == GSM_DAVEY_STEWARTSON_2D;
+}
 
 // ---------------------------------------------------------------- Sec. 3: GS terms
 // Coulomb (Sec. 3.2): 1/r = (1/sqrt(pi)) int_R exp(-r^2 sinh^2 t) cosh t dt,
@@ -368,6 +371,12 @@ __global__ void k_multiplier(MultParams mp, const double *khat, double *mult)
     }
     double v = mp.scale * (khat[idx] + mp.c0 - mp.c2 * kap2);
     if (mp.kind == GSM_POISSON_2D && idx == 0) v += mp.extra0;
+    if (mp.kind == GSM_DAVEY_STEWARTSON_2D) {
+        // source d_xx rho: symbol -kappa_x^2 in physical units; its k = 0 mode
+        // vanishes, and with it the ln L term of the rescaling
+        const double kx = 0.5 * kPi * k[0];
+        v *= -kx * kx / (mp.L * mp.L);
+    }
     if (mp.kind == GSM_DIPOLAR_3D) {
         const double ka = 0.5 * kPi * k[mp.dip_axis];
         v = -mp.dip_nm + 3.0 * mp.dip_nm * ka * ka / (mp.L * mp.L) * v;
@@ -375,6 +384,54 @@ __global__ void k_multiplier(MultParams mp, const double *khat, double *mult)
     mult[idx] = v * mp.norm;
 }
 
+
+// General dipolar directions (Sec. 2.4, Example 4): the multiplier
+//   norm (-(n.m)) + 3 (n.kappa')(m.kappa')' / L^2 * mC(|k|),
+// mC the normalised Coulomb multiplier on the octant.  (n.k)(m.k) is even under
+// k -> -k but not per axis, so it is stored for every (kx >= 0, ky, kz) of the
+// half spectrum, row (kx * My + ky) of Mz entries.  First derivatives vanish at
+// the Nyquist index: sum_ij n_i m_j k_i k_j drops the terms i != j in which
+// k_i or k_j is the Nyquist frequency.
+struct DipFull {
+    int n[3], M[3];
+    double nv[3], mv[3];
+    double L, norm;
+    int prec;
+};
+
+__global__ void k_multiplier_dip_full(DipFull dp, const double *__restrict__ mC, void *out)
+{
+    const int hx = dp.n[0] + 1, My = dp.M[1], Mz = dp.M[2];
+    const long tot = (long)hx * My * Mz;
+    const long idx = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    if (idx >= tot) return;
+    const int kz = idx % Mz, ky = (idx / Mz) % My, kx = idx / ((long)Mz * My);
+    const int kk[3] = {kx, ky < My - ky ? ky : ky - My, kz < Mz - kz ? kz : kz - Mz};
+    double kap[3];
+    bool nyq[3];
+    for (int j = 0; j < 3; ++j) {
+        kap[j] = 0.5 * kPi * kk[j];
+        nyq[j] = 2 * (kk[j] < 0 ? -kk[j] : kk[j]) == dp.M[j];
+    }
+    double sym = 0.0;
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            if (i != j && (nyq[i] || nyq[j])) continue;
+            sym += dp.nv[i] * dp.mv[j] * kap[i] * kap[j];
+        }
+    const int fy = ky < My - ky ? ky : My - ky, fz = kz < Mz - kz ? kz : Mz - kz;
+    const double c = mC[((size_t)kx * (dp.n[1] + 1) + fy) * (dp.n[2] + 1) + fz];
+    const double nm = dp.nv[0] * dp.mv[0] + dp.nv[1] * dp.mv[1] + dp.nv[2] * dp.mv[2];
+    const double v = -nm * dp.norm + 3.0 * sym / (dp.L * dp.L) * c;
+    if (dp.prec == GSM_FP64) {
+        reinterpret_cast<double *>(out)[idx] = v;
+    } else if (dp.prec == GSM_FP32) {
+        reinterpret_cast<float *>(out)[idx] = (float)v;
+    } else {
+        const df a = df_from_double(v);
+        reinterpret_cast<float2 *>(out)[idx] = make_float2(a.hi, a.lo);
+    }
+}
 }  // namespace
 
 // ---------------------------------------------------------------- host side
@@ -383,7 +440,9 @@ gsm_status_t build_plan_data(Plan *p, cudaStream_t st)
     const int d = p->d;
     const double delta = p->opt.delta;
     const double rmax = 2.0 * sqrt((double)d);
-    const int kind_gs = p->kind == GSM_DIPOLAR_3D ? GSM_COULOMB_3D : p->kind;
+    // the dipolar potential is built on the Coulomb sum, Davey-Stewartson on ln r
+    const int kind_gs = p->kind == GSM_DIPOLAR_3D ? GSM_COULOMB_3D
+                        : (p->kind == GSM_DAVEY_STEWARTSON_2D ? GSM_POISSON_2D : p->kind);
 
     GSM_CUDA_TRY(cudaMalloc(&p->d_w, sizeof(double) * kGsCap));
     GSM_CUDA_TRY(cudaMalloc(&p->d_tau, sizeof(double) * kGsCap));
@@ -480,7 +539,9 @@ gsm_status_t build_plan_data(Plan *p, cudaStream_t st)
                                                   p->d_khat);
     MultParams mp;
     mp.d = d;
-    mp.kind = p->kind;
+    // general dipolar directions: the octant holds the Coulomb multiplier and
+    // the dipolar symbol is applied in the full table built below
+    mp.kind = (p->kind == GSM_DIPOLAR_3D && p->dip_axis < 0) ? GSM_COULOMB_3D : p->kind;
     for (int a = 0; a < 3; ++a) {
         mp.n[a] = p->n[a];
         mp.M[a] = p->M[a];
@@ -488,7 +549,7 @@ gsm_status_t build_plan_data(Plan *p, cudaStream_t st)
     const double L = p->L;
     if (p->kind == GSM_COULOMB_3D || p->kind == GSM_DIPOLAR_3D) mp.scale = L * L / (4.0 * kPi);
     else if (p->kind == GSM_COULOMB_2D) mp.scale = L / (2.0 * kPi);
-    else mp.scale = -L * L / (2.0 * kPi);
+    else mp.scale = -L * L / (2.0 * kPi);   // ln kernel: Poisson and Davey-Stewartson
     mp.c0 = p->c0;
     mp.c2 = p->c2;
     double pm = 1.0;
@@ -507,6 +568,28 @@ gsm_status_t build_plan_data(Plan *p, cudaStream_t st)
         gsm_status_t s = make_twiddles(p, a, st);
         if (s != GSM_OK) return s;
     }
+    if (p->kind == GSM_DIPOLAR_3D && p->dip_axis < 0) {
+        DipFull dp;
+        for (int a = 0; a < 3; ++a) {
+            dp.n[a] = p->n[a];
+            dp.M[a] = p->M[a];
+            dp.nv[a] = p->opt.dip_n[a];
+            dp.mv[a] = p->opt.dip_m[a];
+        }
+        dp.L = L;
+        dp.norm = mp.norm;
+        dp.prec = p->opt.precision;
+        const size_t full = (size_t)(p->n[0] + 1) * p->M[1] * p->M[2];
+        const size_t eb = p->opt.precision == GSM_FP32 ? sizeof(float) : sizeof(double);
+        GSM_CUDA_TRY(cudaMalloc(&p->d_mult, eb * full));
+        p->mult_full = true;
+        p->mult_elems_pass = full;
+        k_multiplier_dip_full<<<(full + 255) / 256, 256, 0, st>>>(dp, p->d_mult64, p->d_mult);
+        GSM_CUDA_TRY(cudaGetLastError());
+        GSM_CUDA_TRY(cudaStreamSynchronize(st));
+        return GSM_OK;
+    }
+    p->mult_elems_pass = p->mult_elems;
     gsm_status_t s = make_pass_multiplier(p, st);
     if (s != GSM_OK) return s;
     GSM_CUDA_TRY(cudaStreamSynchronize(st));

@@ -72,3 +72,19 @@ def dipolar3d_gaussian(X, Y, Z, sigma, nv, mv):
     u = -np.dot(nv, mv) * e - 3.0 * (a * np.dot(nv, mv) + b * nx * mx)
     u = np.where(z, -np.dot(nv, mv) * 1.0 + np.dot(nv, mv), u)
     return u
+
+
+def ds2d_gaussian(X, Y):
+    """Example 5: for rho = pi exp(-pi^2 r^2), u = -(1/2pi) ln|x| * d_xx rho is
+    Phi = -( (pi/2) e^{-pi^2 r^2} + cos(2 theta) e^{-pi^2 r^2} (1 + pi^2 r^2 - e^{pi^2 r^2}) / (2 pi r^2) ),
+    the second term written as (e^{-a}(1 + a) - 1)/(2 pi r^2), a = pi^2 r^2,
+    which tends to 0 at the origin."""
+    r2 = X * X + Y * Y
+    a = np.pi ** 2 * r2
+    th = np.arctan2(Y, X)
+    z = r2 == 0
+    rr = np.where(z, 1.0, r2)
+    aa = np.where(z, 1.0, a)
+    g = (np.exp(-aa) * (1.0 + aa) - 1.0) / (2.0 * np.pi * rr)
+    g = np.where(z, 0.0, g)
+    return -(np.pi / 2.0 * np.exp(-a) + np.cos(2.0 * th) * g)

@@ -201,7 +201,9 @@ def test_invalid_arguments_raise_status(gsm):
     with pytest.raises(GSMError):
         gsm.Plan("coulomb3d", -1.0, 16)
     with pytest.raises(GSMError):
-        gsm.Plan("dipolar3d", 1.0, 16, dip_n=(0.6, 0.8, 0.0), dip_m=(0.0, 0.0, 1.0))
+        gsm.Plan("dipolar3d", 1.0, 16, dip_n=(0.6, 0.7, 0.0), dip_m=(0.0, 0.0, 1.0))   # not unit
+    with pytest.raises(ValueError):
+        gsm.Plan("ds2d", 1.0, (16, 16, 16))      # the binding checks the dimension
 
 
 def test_apply_host_equals_device(gsm):
@@ -332,3 +334,57 @@ def test_full_size_4096_square_parity(gsm, kernel):
     f = poisson2d_gaussian if kernel == "poisson2d" else coulomb2d_gaussian
     closed = sum(a * f(np.sqrt((X - c[0]) ** 2 + (Y - c[1]) ** 2), s[0]) for c, s, a in params)
     assert relmax(u, closed) < (1e-13 if kernel == "poisson2d" else 1e-12)
+
+
+# ------------------------------------------------------------------ general dipolar, Davey-Stewartson
+TABLE7_N = (0.82778, 0.41505, -0.37751)
+TABLE7_M = (0.3118, 0.9378, -0.15214)
+
+
+def _unit(v):
+    v = np.asarray(v, dtype=float)
+    return tuple(v / np.linalg.norm(v))
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32x2", "fp32"])
+def test_dipolar_general_parity(gsm, precision):
+    """Arbitrary n, m (Example 4's vectors, normalised): half-spectrum
+    multiplier, against the oracle's padded-grid derivative (taylor_mode 1),
+    on a smooth density and on a ragged random one."""
+    nv, mv = _unit(TABLE7_N), _unit(TABLE7_M)
+    for rho, L in ((wl.coulomb3d_gaussian(32, 8.0, 1.2), 8.0),
+                   (np.random.default_rng(15).standard_normal((12, 20, 16)), 3.0)):
+        u, plan = run(gsm, "dipolar3d", rho, L, precision, dip_n=nv, dip_m=mv)
+        uo, _ = oracle.apply("dipolar3d", rho, L, taylor_mode=1, S=plan.info()["S"], dip_n=nv, dip_m=mv)
+        assert relmax(u, uo) < TOL[precision], relmax(u, uo)
+
+
+def test_dipolar_general_closed_form(gsm):
+    """Example 4 at h = 1/4 (64^3 on [-8,8]^3): the printed error is 1.43e-14."""
+    import sys, os
+    sys.path.insert(0, os.path.dirname(__file__))
+    from closed_forms import dipolar3d_gaussian
+    nv, mv = _unit(TABLE7_N), _unit(TABLE7_M)
+    X, Y, Z = wl.mesh((64, 64, 64), 8.0)
+    rho = np.exp(-(X * X + Y * Y + Z * Z) / 1.44)
+    u, _ = run(gsm, "dipolar3d", rho, 8.0, dip_n=nv, dip_m=mv)
+    assert relmax(u, dipolar3d_gaussian(X, Y, Z, 1.2, nv, mv)) < 1e-13
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32x2", "fp32"])
+def test_davey_stewartson_parity(gsm, precision):
+    import sys, os
+    sys.path.insert(0, os.path.dirname(__file__))
+    from closed_forms import ds2d_gaussian
+    for n, L in ((128, 8.0), (256, 8.0)):
+        X, Y = wl.mesh((n, n), L)
+        rho = np.pi * np.exp(-np.pi ** 2 * (X * X + Y * Y))
+        u, plan = run(gsm, "ds2d", rho, L, precision)
+        uo, _ = oracle.apply("ds2d", rho, L, taylor_mode=1, S=plan.info()["S"])
+        assert relmax(u, uo) < TOL[precision], relmax(u, uo)
+        if precision == "fp64" and n == 256:
+            assert relmax(u, ds2d_gaussian(X, Y)) < 4.536e-13     # Table Tab_DS, h = 1/16
+    rho = np.random.default_rng(16).standard_normal((30, 40))
+    u, plan = run(gsm, "ds2d", rho, 2.0, precision)
+    uo, _ = oracle.apply("ds2d", rho, 2.0, taylor_mode=1, S=plan.info()["S"])
+    assert relmax(u, uo) < TOL[precision]

@@ -15,7 +15,7 @@ from scipy.special import erf, gamma, gammainc
 import oracle
 from paper_1501_04438_gb300 import workloads as wl
 
-from closed_forms import (coulomb2d_gaussian, coulomb3d_gaussian, dipolar3d_gaussian,
+from closed_forms import (coulomb2d_gaussian, coulomb3d_gaussian, dipolar3d_gaussian, ds2d_gaussian,
                           poisson2d_gaussian)
 
 GOLDEN = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_tables.json")))
@@ -290,7 +290,7 @@ def test_config1_closed_form():
 
 # --- invariants ---------------------------------------------------------------------
 
-@pytest.mark.parametrize("kernel", ["coulomb3d", "coulomb2d", "poisson2d", "dipolar3d"])
+@pytest.mark.parametrize("kernel", ["coulomb3d", "coulomb2d", "poisson2d", "dipolar3d", "ds2d"])
 @pytest.mark.parametrize("mode", [0, 1])
 def test_linear_and_symmetric(kernel, mode):
     d = oracle.KERNEL_DIM[kernel]
@@ -304,9 +304,9 @@ def test_linear_and_symmetric(kernel, mode):
     ub, _ = oracle.apply(kernel, b, 3.0, **kw)
     uab, _ = oracle.apply(kernel, 2.0 * a - 0.5 * b, 3.0, **kw)
     assert relmax(uab, 2.0 * ua - 0.5 * ub) < 1e-13
-    if kernel == "dipolar3d" and mode == 0:
+    if kernel in ("dipolar3d", "ds2d") and mode == 0:
         # the n-grid derivative does not commute with pad-convolve-crop, so the
-        # literal dipolar operator is symmetric only for resolved densities
+        # literal operator is symmetric only for resolved densities
         return
     assert abs(np.dot(a.ravel(), ub.ravel()) - np.dot(ua.ravel(), b.ravel())) < 1e-12 * np.abs(a).sum() * np.abs(ub).max()
 
@@ -352,3 +352,30 @@ def test_hartree_gradient_central_differences():
             fd = (Ep - Em) / (2 * hstep)
             an = g[idx].real if unit == 1.0 else g[idx].imag
             assert abs(fd - an) < 1e-7 * np.max(np.abs(g))
+
+
+@pytest.mark.parametrize("entry", GOLDEN["ds2d"], ids=[f"n{e['n']}" for e in GOLDEN["ds2d"]])
+def test_paper_table_davey_stewartson(entry):
+    """Table Tab_DS.  Resolved rows: the printed error (3.974e-9 at 128^2) and
+    the floor; the under-resolved rows depend on how d_xx rho is formed and
+    are checked for magnitude (E of order 1e-2 or worse)."""
+    L, n = entry["L"], entry["n"]
+    X, Y = wl.mesh((n, n), L)
+    rho = np.pi * np.exp(-np.pi ** 2 * (X * X + Y * Y))
+    u, _ = oracle.apply("ds2d", rho, L)
+    E = relmax(u, ds2d_gaussian(X, Y))
+    if entry.get("floor"):
+        assert E < entry["E"], E
+    elif entry.get("underresolved"):
+        assert E > 1e-4, E
+    else:
+        assert abs(E - entry["E"]) < 0.02 * entry["E"], E
+
+
+def test_davey_stewartson_folded_matches_literal_when_resolved():
+    L, n = 8.0, 256
+    X, Y = wl.mesh((n, n), L)
+    rho = np.pi * np.exp(-np.pi ** 2 * (X * X + Y * Y))
+    u0, _ = oracle.apply("ds2d", rho, L, taylor_mode=0)
+    u1, _ = oracle.apply("ds2d", rho, L, taylor_mode=1)
+    assert relmax(u1, u0) < 1e-13
