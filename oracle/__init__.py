@@ -28,8 +28,10 @@ KERNEL_DIM = {"coulomb3d": 3, "coulomb2d": 2, "poisson2d": 2, "dipolar3d": 3, "d
 GS_CAP = 1024
 
 # Default accuracy targets of the Gaussian sums (Sec. 3.2-3.3): relative error
-# of 1/r and absolute error of ln r over [delta, 2 sqrt(d)].
-DEFAULT_EPS = {"coulomb3d": 1e-15, "coulomb2d": 1e-15, "dipolar3d": 1e-15, "poisson2d": 1e-13, "ds2d": 1e-13}
+# of 1/r and absolute error of ln r over [delta, 2 sqrt(d)].  Both sit just above
+# the rounding floor of the sums built in double (1/r: 0.9e-15 for delta = 1e-3,
+# 1.2e-15 for delta = 1e-4; ln r: about 5e-14).
+DEFAULT_EPS = {"coulomb3d": 2e-15, "coulomb2d": 2e-15, "dipolar3d": 2e-15, "poisson2d": 1e-13, "ds2d": 1e-13}
 
 
 def build(force: bool = False) -> str:
@@ -59,6 +61,7 @@ class Params(ctypes.Structure):
         ("dip_n", ctypes.c_double * 3),
         ("dip_m", ctypes.c_double * 3),
         ("threads", ctypes.c_int),
+        ("box", ctypes.c_double * 3),
     ]
 
 
@@ -185,7 +188,8 @@ def taylor_coeffs(kernel: str, w, tau, delta: float):
 
 def make_params(kernel: str, n, L: float, pad: int = 2, delta: float = 1e-3, eps: float | None = None,
                 S: int = 0, taylor_mode: int = 0, dip_n=(0.0, 0.0, 1.0), dip_m=(0.0, 0.0, 1.0),
-                threads: int = 0) -> Params:
+                threads: int = 0, box=None) -> Params:
+    """box: per-axis half-widths (x first) of a rectangular box; L is then unused."""
     d = KERNEL_DIM[kernel]
     if isinstance(n, int):
         n = [n] * d
@@ -205,6 +209,9 @@ def make_params(kernel: str, n, L: float, pad: int = 2, delta: float = 1e-3, eps
         p.dip_n[i] = float(dip_n[i])
         p.dip_m[i] = float(dip_m[i])
     p.threads = int(threads)
+    bx = list(box) if box is not None else []
+    for i in range(3):
+        p.box[i] = float(bx[i]) if i < len(bx) else 0.0
     return p
 
 

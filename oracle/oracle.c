@@ -29,6 +29,10 @@
  *   - Arrays are C-ordered with x fastest: rho[z][y][x] (3D), rho[y][x] (2D).
  *   - Grid of Sec. 2.1: x_j = -L + j h, h = 2L/n, j = 1..n; array index i = j-1.
  *   - Unit-box coordinates x~ = x/L (Eq. rescale); delta is given in them.
+ *     A rectangular box [-L_a, L_a] per axis (Sec. 2.5, Eq. tensor_ani and
+ *     the remark after it) is rescaled by the largest half-width, L = max L_a:
+ *     axis a then spans [-eta_a, eta_a], eta_a = L_a / L <= 1, its kernel box
+ *     is [-2 eta_a, 2 eta_a] and its padded period 4 eta_a (6 eta_a for pad 3).
  *   - Padding factor 2 (remark after Eq. tensor: period 4) or 3 (Eq. FourSeriB3:
  *     period 6).  The kernel box of Eq. tensor is [-2,2]^d in both cases.
  *   - The GS must hold on [delta, 2 sqrt(d)]: for x in B_1 the density rho(x-y)
@@ -225,9 +229,9 @@ int orc_gs_build(int kernel, double delta, double rmax, double eps, int S_fixed,
 /* or b = 7/tau when that is smaller (the integrand is below e^{-49} there). */
 /* Panels are short enough to resolve both the Gaussian and the cosine.     */
 /* ------------------------------------------------------------------------ */
-static double factor_gl(const gl_rule *g, double tau, double omega)
+static double factor_gl(const gl_rule *g, double tau, double omega, double half)
 {
-    double b = 2.0;
+    double b = half;   /* integrate over [0, half], half = 2 eta */
     if (tau > 0.0 && 7.0 / tau < b) b = 7.0 / tau;
     double scale = tau > fabs(omega) ? tau : fabs(omega);
     int np = 2 + (int)ceil(b * scale / 2.0);
@@ -247,7 +251,7 @@ double orc_factor(double tau, double omega)
 {
     gl_rule g;
     gl_init(&g);
-    return factor_gl(&g, tau, omega);
+    return factor_gl(&g, tau, omega, 2.0);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -428,15 +432,35 @@ static double pairwise_sum(const double *a, size_t n)
 /* signed frequency of DFT index j of length N: j or j - N */
 static int signed_freq(int j, int N) { return j < (N + 1) / 2 ? j : j - N; }
 
+/* Reference half-width Lr and per-axis eta_a of Sec. 2.5 (all 1 for the     */
+/* cubic box [-L, L]^d).                                                     */
+static double box_eta(const orc_params_t *p, double *eta)
+{
+    int d = kernel_dim(p->kernel);
+    double Lr = 0.0;
+    for (int a = 0; a < d; a++)
+        if (p->box[a] > Lr) Lr = p->box[a];
+    if (Lr <= 0.0) {
+        for (int a = 0; a < 3; a++) eta[a] = 1.0;
+        return p->L;
+    }
+    for (int a = 0; a < 3; a++) eta[a] = a < d ? p->box[a] / Lr : 1.0;
+    return Lr;
+}
+
 int orc_plan_gs(const orc_params_t *p, double *w, double *tau, int cap, orc_info_t *info)
 {
     int kb = base_kernel(p->kernel);
     int d = kernel_dim(p->kernel);
-    double rmax = 2.0 * sqrt((double)d);
+    double eta[3];
+    box_eta(p, eta);
+    double rr = 0.0;   /* the kernel box B_2 (per axis [-2 eta, 2 eta]) has its corners at 2|eta| */
+    for (int a = 0; a < d; a++) rr += eta[a] * eta[a];
+    double rmax = 2.0 * sqrt(rr);
     int nt, S;
     double err;
     if (orc_gs_build(kb, p->delta, rmax, p->gs_eps, p->gs_S, cap, w, tau, &nt, &S, &err) != ORC_OK)
-        return ORC_ERR;
+        return -1;   /* no Gaussian sum meets gs_eps (callers test nt <= 0) */
     if (info) {
         info->S = S;
         info->nterms = nt;
@@ -453,7 +477,8 @@ int orc_kernel_hat(const orc_params_t *p, double *khat, orc_info_t *info)
     double w[ORC_GS_CAP], tau[ORC_GS_CAP];
     int nt = orc_plan_gs(p, w, tau, ORC_GS_CAP, info);
     if (nt <= 0) return ORC_ERR;
-    double P = 2.0 * p->pad;
+    double eta[3];
+    box_eta(p, eta);
     int no[3] = {1, 1, 1};
     for (int a = 0; a < d; a++) no[a] = p->pad * p->n[a] / 2 + 1;
     /* 1-D factors per axis: g[a][q][k] */
@@ -465,7 +490,8 @@ int orc_kernel_hat(const orc_params_t *p, double *khat, orc_info_t *info)
 #pragma omp parallel for collapse(2) schedule(dynamic)
         for (int q = 0; q < nt; q++)
             for (int k = 0; k < no[a]; k++)
-                g[a][(size_t)q * no[a] + k] = factor_gl(&gl, tau[q], 2.0 * PI * k / P);
+                g[a][(size_t)q * no[a] + k] =
+                    factor_gl(&gl, tau[q], 2.0 * PI * k / (2.0 * p->pad * eta[a]), 2.0 * eta[a]);
     }
     size_t tot = (size_t)no[0] * no[1] * no[2];
 #pragma omp parallel for schedule(static)
@@ -486,7 +512,7 @@ int orc_kernel_hat(const orc_params_t *p, double *khat, orc_info_t *info)
 /* Laplacian (unit-box coordinates) or the d_nm derivative (physical        */
 /* coordinates) of rho on the n-grid by FFT, period 2 in unit coordinates.  */
 /* which = 0: Laplacian; which = 1: d_nm = sum_ij n_i m_j d_i d_j.            */
-static void spectral_derivative(int d, const int *n, double L, int which,
+static void spectral_derivative(int d, const int *n, double L, const double *eta, int which,
                                 const double *dn, const double *dm,
                                 const double *rho, double *out)
 {
@@ -502,7 +528,7 @@ static void spectral_derivative(int d, const int *n, double L, int which,
         for (int j = 0; j < d; j++) {
             int f = signed_freq(k[j], n[j]);
             nyq[j] = (2 * f == -n[j]);
-            kap[j] = PI * f;              /* 2 pi f / period, period 2 */
+            kap[j] = PI * f / eta[j];     /* 2 pi f / period, period 2 eta_j */
         }
         double mult;
         if (which == 0) {
@@ -576,7 +602,8 @@ static int run_scalar(const struct orc_prepared_s *h, const double *rho, double 
     const int kernel = h->kernel, d = h->d;
     const int *n = p->n;
     const int *Nt = h->Nt, *no = h->no;
-    const double L = p->L, c0 = h->c0, c2 = h->c2;
+    double eta[3];
+    const double L = box_eta(p, eta), c0 = h->c0, c2 = h->c2;
     const double *khat = h->khat;
 
     /* Step 1: zero-padded density and rho_hat_k = DFT / Nt^d (Eq. rho_hat,  */
@@ -598,7 +625,9 @@ static int run_scalar(const struct orc_prepared_s *h, const double *rho, double 
     /* Step 2: I_1(x) = sum_k rho_hat_k (sum_q w_q G^q_k) e^{2 pi i k (x - a)/P} */
     /* (Eq. I1FFT).  taylor_mode 1 also folds c0 - c2 |kappa|^2 into the     */
     /* multiplier: the Taylor correction with a padded-grid spectral Laplacian. */
-    double P = 2.0 * p->pad;
+    /* Period of axis j: P_j = 2 pad eta_j.                                   */
+    double P[3];
+    for (int j = 0; j < 3; j++) P[j] = 2.0 * p->pad * eta[j];
     for (size_t idx = 0; idx < NT; idx++) {
         int k[3] = {(int)(idx % Nt[0]), (int)((idx / Nt[0]) % Nt[1]), (int)(idx / ((size_t)Nt[0] * Nt[1]))};
         int kk[3] = {0, 0, 0};
@@ -606,7 +635,7 @@ static int run_scalar(const struct orc_prepared_s *h, const double *rho, double 
         for (int j = 0; j < d; j++) {
             int f = signed_freq(k[j], Nt[j]);
             kk[j] = abs(f);
-            double kap = 2.0 * PI * f / P;
+            double kap = 2.0 * PI * f / P[j];
             kap2 += kap * kap;
         }
         double mult = khat[kk[0] + (size_t)no[0] * (kk[1] + (size_t)no[1] * kk[2])];
@@ -617,7 +646,7 @@ static int run_scalar(const struct orc_prepared_s *h, const double *rho, double 
             int nyq[3] = {0, 0, 0};
             for (int j = 0; j < d; j++) {
                 int f = signed_freq(k[j], Nt[j]);
-                kv[j] = 2.0 * PI * f / P;
+                kv[j] = 2.0 * PI * f / P[j];
                 nyq[j] = (2 * f == -Nt[j]);
             }
             for (int i = 0; i < d; i++)
@@ -635,7 +664,7 @@ static int run_scalar(const struct orc_prepared_s *h, const double *rho, double 
     double *lap = NULL;
     if (p->taylor_mode == 0) {
         lap = malloc(sizeof(double) * N);
-        spectral_derivative(d, n, L, 0, NULL, NULL, rho, lap);
+        spectral_derivative(d, n, L, eta, 0, NULL, NULL, rho, lap);
     }
 
     /* Rescaling of Sec. 2.1 (Eq. rescale and the two lines after it) */
@@ -647,7 +676,7 @@ static int run_scalar(const struct orc_prepared_s *h, const double *rho, double 
     if (kernel == ORC_POISSON_2D && !dn) {   /* a derivative source has zero mass */
         /* trapezoidal int rho~, summed pairwise (a sequential sum over n^2    */
         /* points drifts by ~1e-12 relative at n = 4096)                       */
-        double hu = 2.0 / n[0], hv = 2.0 / n[1];
+        double hu = 2.0 * eta[0] / n[0], hv = 2.0 * eta[1] / n[1];
         double mass = pairwise_sum(rho, N);
         extra = -L * L / (2.0 * PI) * log(L) * hu * hv * mass;
     }
@@ -670,7 +699,10 @@ static int run_scalar(const struct orc_prepared_s *h, const double *rho, double 
 static int check_params(const orc_params_t *p)
 {
     int d = kernel_dim(p->kernel);
-    if (p->d != d || p->L <= 0 || p->delta <= 0 || (p->pad != 2 && p->pad != 3)) return ORC_ERR;
+    double eta[3];
+    if (p->d != d || box_eta(p, eta) <= 0 || p->delta <= 0 || (p->pad != 2 && p->pad != 3)) return ORC_ERR;
+    for (int a = 0; a < d; a++)
+        if (p->delta >= eta[a]) return ORC_ERR;   /* Sec. 2.5: delta smaller than eta */
     for (int a = 0; a < d; a++)
         if (p->n[a] < 2 || p->n[a] % 2) return ORC_ERR;
 #ifdef _OPENMP
@@ -714,7 +746,9 @@ int orc_run(const orc_prepared_t *h, const double *rho, double *u, double *i1, d
         if (p->taylor_mode == 1) return run_scalar(h, rho, u, i1, i2, ex, ex);
         size_t N = prod(2, p->n);
         double *src = malloc(sizeof(double) * N);
-        spectral_derivative(2, p->n, p->L, 1, ex, ex, rho, src);
+        double eta[3];
+        double Lr = box_eta(p, eta);
+        spectral_derivative(2, p->n, Lr, eta, 1, ex, ex, rho, src);
         int rc = run_scalar(h, src, u, i1, i2, NULL, NULL);
         free(src);
         return rc;
@@ -724,7 +758,9 @@ int orc_run(const orc_prepared_t *h, const double *rho, double *u, double *i1, d
     double *src = malloc(sizeof(double) * N), *uc = malloc(sizeof(double) * N);
     int rc;
     if (p->taylor_mode == 0) {
-        spectral_derivative(3, p->n, p->L, 1, p->dip_n, p->dip_m, rho, src);
+        double eta[3];
+        double Lr = box_eta(p, eta);
+        spectral_derivative(3, p->n, Lr, eta, 1, p->dip_n, p->dip_m, rho, src);
         rc = run_scalar(h, src, uc, NULL, NULL, NULL, NULL);
     } else {
         rc = run_scalar(h, rho, uc, NULL, NULL, p->dip_n, p->dip_m);

@@ -29,6 +29,8 @@ typedef struct {
     double dip_n[3];    /* dipolar unit vectors n and m */
     double dip_m[3];
     int threads;        /* OpenMP threads (0: default) */
+    double box[3];      /* > 0: half-width of axis a (rectangular box, Sec. 2.5); */
+                        /* all 0: the cube [-L, L]^d                           */
 } orc_params_t;
 
 typedef struct {

@@ -26,11 +26,13 @@ def grid_1d(n: int, L: float) -> np.ndarray:
     return -L + (np.arange(n) + 1.0) * h
 
 
-def mesh(n, L: float):
-    """Coordinate arrays (X, Y[, Z]) on the grid, each shaped like rho."""
+def mesh(n, L):
+    """Coordinate arrays (X, Y[, Z]) on the grid, each shaped like rho.  L is the
+    half-width of every axis, or a sequence of per-axis half-widths (x first)."""
     if isinstance(n, int):
         raise TypeError("n must be a tuple (nx, ny[, nz])")
-    axes = [grid_1d(m, L) for m in n]
+    Ls = list(L) if hasattr(L, "__len__") else [L] * len(n)
+    axes = [grid_1d(m, a) for m, a in zip(n, Ls)]
     # meshgrid with 'ij' on reversed axes gives [z][y][x] ordering
     grids = np.meshgrid(*axes[::-1], indexing="ij")
     return tuple(grids[::-1])
@@ -77,6 +79,21 @@ def coulomb3d_anisotropic(n: int = 128, L: float = 12.0, gamma: float = 4.0) -> 
     """exp(-(x^2 + y^2 + z^2/gamma^2)) on [-L,L]^3."""
     X, Y, Z = mesh((n, n, n), L)
     return np.exp(-(X * X + Y * Y + Z * Z / gamma ** 2))
+
+
+def aniso_box(d: int, L: float = 12.0, gamma: float = 4.0):
+    """Box of the anisotropic rows of Sec. 4: [-L,L]^(d-1) x [-L/gamma, L/gamma]."""
+    return (L,) * (d - 1) + (L / gamma,)
+
+
+def aniso_gaussian(d: int, n: int, L: float = 12.0, sigma: float = 2.0, gamma: float = 4.0):
+    """exp(-(|x'|^2 + gamma^2 x_d^2)/sigma^2) on aniso_box with n points per axis
+    (h_d = h / gamma), the densities of the anisotropic rows of Examples 1 and 2.
+    Returns (rho, box)."""
+    box = aniso_box(d, L, gamma)
+    C = mesh((n,) * d, box)
+    r2 = sum(c * c for c in C[:-1]) + (gamma * C[-1]) ** 2
+    return np.exp(-r2 / sigma ** 2), box
 
 
 def mixture3d_params(seed: int = SEED_MIX3D, count: int = 8):

