@@ -5,7 +5,8 @@
  * Gaussian-sum approximation" (arXiv:1501.04438).
  *
  * Problem (Sec. 1, Eq. ConvGen, Eq. kernelPhy): given a density rho sampled on
- * the uniform grid of Sec. 2.1 of the box [-L, L]^d,
+ * the uniform grid of Sec. 2.1 of the box [-L, L]^d (or a rectangular box,
+ * gsm_options_t.box),
  *     x_j = -L + j h,  h = 2L/n,  j = 1..n    (array index i = j - 1),
  * compute u(x) = int U(x - y) rho(y) dy at the same points for
  *     3D Coulomb  U = 1/(4 pi |x|),   2D Coulomb U = 1/(2 pi |x|),
@@ -88,12 +89,17 @@ typedef struct {
     double delta;               /* radius of the near-field ball B_delta in unit-box
                                    coordinates, Sec. 2.3 (default 1e-3) */
     int S;                      /* > 0: use this sinc-quadrature S; 0: the smallest
-                                   S whose GS error on [delta, 2 sqrt(d)] is <= gs_eps */
+                                   S whose GS error on [delta, 2 |eta|] is <= gs_eps */
     gsm_precision_t precision;  /* default GSM_FP64 */
     double dip_n[3];            /* dipolar unit vectors n, m (default e_z, e_z); any */
     double dip_m[3];            /* directions (both along one axis: octant multiplier,
                                    otherwise a half-spectrum multiplier table) */
     int debug;                  /* reserved, 0 */
+    double box[3];              /* rectangular box (Sec. 2.5, Eq. tensor_ani): if all
+                                   d entries are > 0, axis a spans [-box[a], box[a]]
+                                   and L is ignored; all 0 (default): [-L, L]^d.  The
+                                   method is rescaled by the largest half-width; delta
+                                   must be smaller than every box[a] / max box */
 } gsm_options_t;
 
 /* Read-only facts about a plan. */
@@ -128,8 +134,9 @@ void gsm_default_options(gsm_options_t *opt);
  *   n      : d points per axis (x first), each even, >= 8, with 2n a product of
  *            2, 3 and 5 and 2n <= 8192.
  *   gs_eps : target accuracy of the Gaussian sum; <= 0 selects the default
- *            (1e-15 relative for 1/r, 1e-13 absolute for ln r).  The ln r sum
- *            built in double has a floor near 5e-14.
+ *            (2e-15 relative for 1/r, 1e-13 absolute for ln r), just above the
+ *            rounding floors of the sums built in double (1/r: 0.9e-15 for
+ *            delta = 1e-3, 1.2e-15 for delta = 1e-4; ln r: about 5e-14).
  *   opt    : NULL for defaults.
  * Errors: GSM_ERR_INVALID_ARG, GSM_ERR_UNSUPPORTED_SIZE, GSM_ERR_ACCURACY,
  *         GSM_ERR_OOM, GSM_ERR_CUDA.

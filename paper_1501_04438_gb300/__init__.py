@@ -59,11 +59,13 @@ class Plan:
     delta     : near-field radius in unit-box coordinates
     S         : force the sinc parameter (0: chosen from gs_eps)
     dip_n, dip_m : dipolar unit vectors
+    box       : per-axis half-widths (x first) of a rectangular box; L is then
+                ignored (Sec. 2.5)
     """
 
     def __init__(self, kernel: str, L: float, n, gs_eps: float = 0.0, precision: str = "fp64",
                  delta: float = 1e-3, S: int = 0, dip_n=(0.0, 0.0, 1.0), dip_m=(0.0, 0.0, 1.0),
-                 stream=None):
+                 stream=None, box=None):
         lib = _abi.load()
         if kernel not in KERNELS:
             raise ValueError(f"unknown kernel {kernel!r}")
@@ -83,6 +85,11 @@ class Plan:
         for i in range(3):
             opt.dip_n[i] = float(dip_n[i])
             opt.dip_m[i] = float(dip_m[i])
+        if box is not None:
+            if len(box) != d:
+                raise ValueError(f"{kernel} needs {d} box half-widths")
+            for i in range(d):
+                opt.box[i] = float(box[i])
         arr = (ctypes.c_int * 3)(*(list(n) + [1] * (3 - d)))
         h = ctypes.c_void_p()
         _abi.check(lib.gsm_plan(ctypes.byref(h), KERNELS[kernel], d, float(L), arr, float(gs_eps),
@@ -90,7 +97,8 @@ class Plan:
         self._h = h
         self.kernel = kernel
         self.d = d
-        self.L = float(L)
+        self.L = float(max(box)) if box is not None else float(L)
+        self.box = tuple(float(b) for b in box) if box is not None else (float(L),) * d
         self.n = n
         self.precision = precision
         self.shape = tuple(reversed(n))          # array shape, C order (x fastest)

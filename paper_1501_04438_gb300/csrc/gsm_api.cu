@@ -109,17 +109,38 @@ gsm_status_t gsm_plan(gsm_plan_t *out, gsm_kernel_t kind, int d, double L, const
         set_error("dimension does not match the kernel");
         return GSM_ERR_INVALID_ARG;
     }
+    gsm_options_t o;
+    if (opt) o = *opt;
+    else gsm_default_options(&o);
+    // rectangular box (Sec. 2.5): rescale by the largest half-width
+    double eta[3] = {1.0, 1.0, 1.0};
+    int nbox = 0;
+    for (int a = 0; a < d; ++a) nbox += o.box[a] != 0.0;
+    if (nbox != 0) {
+        double Lr = 0.0;
+        for (int a = 0; a < d; ++a) {
+            if (!(o.box[a] > 0.0) || !isfinite(o.box[a])) {
+                set_error("options.box must give d positive finite half-widths (or all 0)");
+                return GSM_ERR_INVALID_ARG;
+            }
+            Lr = fmax(Lr, o.box[a]);
+        }
+        for (int a = 0; a < d; ++a) eta[a] = o.box[a] / Lr;
+        L = Lr;
+    }
     if (!n || !(L > 0.0) || !isfinite(L)) {
         set_error("n is NULL or L is not a positive finite number");
         return GSM_ERR_INVALID_ARG;
     }
-    gsm_options_t o;
-    if (opt) o = *opt;
-    else gsm_default_options(&o);
     if (!(o.delta > 0.0) || o.delta >= 0.5) {
         set_error("options.delta must be in (0, 0.5)");
         return GSM_ERR_INVALID_ARG;
     }
+    for (int a = 0; a < d; ++a)
+        if (!(o.delta < eta[a])) {
+            set_error("options.delta must be smaller than every box half-width / the largest (Sec. 2.5)");
+            return GSM_ERR_INVALID_ARG;
+        }
     if (o.precision < GSM_FP64 || o.precision > GSM_FP32X2) {
         set_error("unknown precision");
         return GSM_ERR_INVALID_ARG;
@@ -159,10 +180,11 @@ gsm_status_t gsm_plan(gsm_plan_t *out, gsm_kernel_t kind, int d, double L, const
         p->M[a] = 2 * n[a];
     }
     p->L = L;
+    for (int a = 0; a < 3; ++a) p->eta[a] = eta[a];
     p->opt = o;
     p->dip_axis = dip_axis;
     const bool log_kernel = kind == GSM_POISSON_2D || kind == GSM_DAVEY_STEWARTSON_2D;
-    p->eps = gs_eps > 0.0 ? gs_eps : (log_kernel ? 1e-13 : 1e-15);
+    p->eps = gs_eps > 0.0 ? gs_eps : (log_kernel ? 1e-13 : 2e-15);
     cudaGetDevice(&p->device);
     p->magic = kPlanMagic;
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);

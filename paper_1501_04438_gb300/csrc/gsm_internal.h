@@ -34,7 +34,8 @@ struct Plan {
     int d = 3;
     int n[3] = {1, 1, 1};
     int M[3] = {1, 1, 1};
-    double L = 1.0;
+    double L = 1.0;                 // reference half-width (largest of the box)
+    double eta[3] = {1.0, 1.0, 1.0};   // half-width of each axis in units of L (Sec. 2.5)
     double eps = 0.0;
     gsm_options_t opt;
     int device = 0;

@@ -945,7 +945,7 @@ static gsm_status_t hartree_t(Plan *p, const T *psi, T *u, T *energy, T *grad, c
     double cell = 1.0;
     for (int a = 0; a < p->d; ++a) {
         N *= (size_t)p->n[a];
-        cell *= 2.0 * p->L / p->n[a];
+        cell *= 2.0 * p->L * p->eta[a] / p->n[a];
     }
     if (!p->d_scratch) {
         GSM_CUDA_TRY(cudaMalloc(&p->d_scratch, sizeof(double) * kEnergyBlocks));

@@ -245,12 +245,14 @@ __device__ double factor_g(double tau, int k, const double *weid)
     return 2.0 * s;
 }
 
-__global__ void k_factors(int nt, const double *tau, int nk, const double *weid, double *g)
+// Axis of half-width eta (Sec. 2.5, Eq. tensor_ani): kernel box [-2 eta, 2 eta],
+// period 4 eta; substituting y = eta y' gives eta * g(tau eta, k).
+__global__ void k_factors(int nt, const double *tau, int nk, double eta, const double *weid, double *g)
 {
     const long idx = blockIdx.x * (long)blockDim.x + threadIdx.x;
     if (idx >= (long)nt * nk) return;
     const int q = idx / nk, k = idx - (long)q * nk;
-    g[idx] = factor_g(tau[q], k, weid);
+    g[idx] = eta * factor_g(tau[q] * eta, k, weid);
 }
 
 // ---------------------------------------------------------------- Sec. 2.3 coefficients
@@ -341,6 +343,7 @@ __global__ void k_tensor(int d, int n0, int n1, int n2, int nt, const double *w,
 
 struct MultParams {
     int d, kind, n[3], M[3];
+    double eta[3];      // axis half-widths in units of L (Sec. 2.5)
     double scale;       // s of Sec. 2.1
     double c0, c2;
     double norm;        // 1/2 (pair packing of the real x transform) / prod M
@@ -366,7 +369,7 @@ __global__ void k_multiplier(MultParams mp, const double *khat, double *mult)
     const int k[3] = {kx, ky, kz};
     double kap2 = 0.0;
     for (int j = 0; j < d; ++j) {
-        const double kap = 0.5 * kPi * k[j];
+        const double kap = 0.5 * kPi * k[j] / mp.eta[j];   // 2 pi k / (4 eta_j)
         kap2 += kap * kap;
     }
     double v = mp.scale * (khat[idx] + mp.c0 - mp.c2 * kap2);
@@ -374,11 +377,11 @@ __global__ void k_multiplier(MultParams mp, const double *khat, double *mult)
     if (mp.kind == GSM_DAVEY_STEWARTSON_2D) {
         // source d_xx rho: symbol -kappa_x^2 in physical units; its k = 0 mode
         // vanishes, and with it the ln L term of the rescaling
-        const double kx = 0.5 * kPi * k[0];
+        const double kx = 0.5 * kPi * k[0] / mp.eta[0];
         v *= -kx * kx / (mp.L * mp.L);
     }
     if (mp.kind == GSM_DIPOLAR_3D) {
-        const double ka = 0.5 * kPi * k[mp.dip_axis];
+        const double ka = 0.5 * kPi * k[mp.dip_axis] / mp.eta[mp.dip_axis];
         v = -mp.dip_nm + 3.0 * mp.dip_nm * ka * ka / (mp.L * mp.L) * v;
     }
     mult[idx] = v * mp.norm;
@@ -394,6 +397,7 @@ __global__ void k_multiplier(MultParams mp, const double *khat, double *mult)
 // k_i or k_j is the Nyquist frequency.
 struct DipFull {
     int n[3], M[3];
+    double eta[3];
     double nv[3], mv[3];
     double L, norm;
     int prec;
@@ -410,7 +414,7 @@ __global__ void k_multiplier_dip_full(DipFull dp, const double *__restrict__ mC,
     double kap[3];
     bool nyq[3];
     for (int j = 0; j < 3; ++j) {
-        kap[j] = 0.5 * kPi * kk[j];
+        kap[j] = 0.5 * kPi * kk[j] / dp.eta[j];
         nyq[j] = 2 * (kk[j] < 0 ? -kk[j] : kk[j]) == dp.M[j];
     }
     double sym = 0.0;
@@ -439,7 +443,10 @@ gsm_status_t build_plan_data(Plan *p, cudaStream_t st)
 {
     const int d = p->d;
     const double delta = p->opt.delta;
-    const double rmax = 2.0 * sqrt((double)d);
+    // the kernel box has half-widths 2 eta_a: its corners lie at 2 |eta|
+    double eta2 = 0.0;
+    for (int a = 0; a < d; ++a) eta2 += p->eta[a] * p->eta[a];
+    const double rmax = 2.0 * sqrt(eta2);
     // the dipolar potential is built on the Coulomb sum, Davey-Stewartson on ln r
     const int kind_gs = p->kind == GSM_DIPOLAR_3D ? GSM_COULOMB_3D
                         : (p->kind == GSM_DAVEY_STEWARTSON_2D ? GSM_POISSON_2D : p->kind);
@@ -505,7 +512,7 @@ gsm_status_t build_plan_data(Plan *p, cudaStream_t st)
         const int nk = p->n[a] + 1;
         bool same = false;
         for (int b = 0; b < a; ++b)
-            if (p->n[b] == p->n[a]) {
+            if (p->n[b] == p->n[a] && p->eta[b] == p->eta[a]) {
                 p->d_g[a] = p->d_g[b];
                 same = true;
                 break;
@@ -513,7 +520,7 @@ gsm_status_t build_plan_data(Plan *p, cudaStream_t st)
         if (same) continue;
         GSM_CUDA_TRY(cudaMalloc(&p->d_g[a], sizeof(double) * p->nterms * nk));
         const long tot = (long)p->nterms * nk;
-        k_factors<<<(tot + 127) / 128, 128, 0, st>>>(p->nterms, p->d_tau, nk, d_weid, p->d_g[a]);
+        k_factors<<<(tot + 127) / 128, 128, 0, st>>>(p->nterms, p->d_tau, nk, p->eta[a], d_weid, p->d_g[a]);
     }
 
     // 3. Taylor coefficients
@@ -545,6 +552,7 @@ gsm_status_t build_plan_data(Plan *p, cudaStream_t st)
     for (int a = 0; a < 3; ++a) {
         mp.n[a] = p->n[a];
         mp.M[a] = p->M[a];
+        mp.eta[a] = p->eta[a];
     }
     const double L = p->L;
     if (p->kind == GSM_COULOMB_3D || p->kind == GSM_DIPOLAR_3D) mp.scale = L * L / (4.0 * kPi);
@@ -555,7 +563,11 @@ gsm_status_t build_plan_data(Plan *p, cudaStream_t st)
     double pm = 1.0;
     for (int a = 0; a < d; ++a) pm *= p->M[a];
     mp.norm = 0.5 / pm;
-    mp.extra0 = (p->kind == GSM_POISSON_2D) ? -L * L / (2.0 * kPi) * log(L) * pow(4.0, d) : 0.0;
+    // Poisson: -(L^2/2pi) ln L int rho~, and int rho~ = prod h_a sum rho with
+    // h_a M_a = 4 eta_a, so the k = 0 entry gains the constant times prod 4 eta_a
+    double vol = 1.0;
+    for (int a = 0; a < d; ++a) vol *= 4.0 * p->eta[a];
+    mp.extra0 = (p->kind == GSM_POISSON_2D) ? -L * L / (2.0 * kPi) * log(L) * vol : 0.0;
     mp.dip_axis = p->dip_axis;
     mp.dip_nm = p->opt.dip_n[0] * p->opt.dip_m[0] + p->opt.dip_n[1] * p->opt.dip_m[1] +
                 p->opt.dip_n[2] * p->opt.dip_m[2];
@@ -573,6 +585,7 @@ gsm_status_t build_plan_data(Plan *p, cudaStream_t st)
         for (int a = 0; a < 3; ++a) {
             dp.n[a] = p->n[a];
             dp.M[a] = p->M[a];
+            dp.eta[a] = p->eta[a];
             dp.nv[a] = p->opt.dip_n[a];
             dp.mv[a] = p->opt.dip_m[a];
         }

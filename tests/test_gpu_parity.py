@@ -388,3 +388,62 @@ def test_davey_stewartson_parity(gsm, precision):
     u, plan = run(gsm, "ds2d", rho, 2.0, precision)
     uo, _ = oracle.apply("ds2d", rho, 2.0, taylor_mode=1, S=plan.info()["S"])
     assert relmax(u, uo) < TOL[precision]
+
+
+# ------------------------------------------------------------------ rectangular boxes (Sec. 2.5)
+BOX_CASES = [
+    ("coulomb3d", "aniso96_g4", None, (12.0, 12.0, 3.0)),
+    ("coulomb3d", "ragged", (12, 20, 16), (3.0, 2.5, 1.2)),
+    ("coulomb2d", "aniso192_g16", None, (12.0, 0.75)),
+    ("coulomb2d", "ragged", (30, 40), (4.0, 1.5)),
+    ("poisson2d", "ragged", (30, 40), (4.0, 1.5)),
+    ("poisson2d", "tall", (48, 64), (1.5, 4.0)),
+    ("ds2d", "ragged", (30, 40), (4.0, 1.5)),
+    ("dipolar3d", "ragged", (12, 20, 16), (3.0, 2.5, 1.2)),
+]
+
+
+def _box_density(name, shape, box, kernel):
+    d = 3 if kernel.endswith("3d") else 2
+    if name.startswith("aniso"):
+        n = 96 if d == 3 else 192
+        rho, _ = wl.aniso_gaussian(d, n, 12.0, 2.0, 12.0 / box[-1])
+        return rho
+    return np.random.default_rng(21).standard_normal(shape[::-1])
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32x2", "fp32"])
+@pytest.mark.parametrize("kernel,name,shape,box", BOX_CASES, ids=[f"{c[0]}-{c[1]}" for c in BOX_CASES])
+def test_box_parity(gsm, kernel, name, shape, box, precision):
+    """Per-axis half-widths: factors eta g(tau eta, k), kappa = pi k / (2 eta L),
+    Gaussian sum on [delta, 2 |eta|], Poisson mass with prod 4 eta."""
+    rho = _box_density(name, shape, box, kernel)
+    kw = dict(delta=1e-4) if name.startswith("aniso192") else {}
+    if kernel == "dipolar3d":
+        kw.update(dip_n=(0.0, 0.0, 1.0), dip_m=(0.0, 0.0, 1.0))
+    u, plan = run(gsm, kernel, rho, 1.0, precision, box=box, **kw)
+    uo, _ = oracle.apply(kernel, rho, 1.0, taylor_mode=1, S=plan.info()["S"], box=box, **kw)
+    assert relmax(u, uo) < TOL[precision], relmax(u, uo)
+    if kernel == "dipolar3d" and precision != "fp32":
+        nv, mv = _unit(TABLE7_N), _unit(TABLE7_M)
+        u, plan = run(gsm, kernel, rho, 1.0, precision, box=box, dip_n=nv, dip_m=mv)
+        uo, _ = oracle.apply(kernel, rho, 1.0, taylor_mode=1, S=plan.info()["S"], box=box,
+                             dip_n=nv, dip_m=mv)
+        assert relmax(u, uo) < TOL[precision], relmax(u, uo)
+
+
+def test_box_cube_is_bit_identical(gsm):
+    """box = (L, L, L) is the cube: the same plan data and the same bits."""
+    torch = _torch()
+    rho = torch.tensor(wl.coulomb3d_gaussian(32, 8.0, 1.2), device="cuda")
+    a = gsm.Plan("coulomb3d", 8.0, (32, 32, 32)).apply(rho)
+    b = gsm.Plan("coulomb3d", 1.0, (32, 32, 32), box=(8.0, 8.0, 8.0)).apply(rho)
+    torch.cuda.synchronize()
+    assert torch.equal(a, b)
+
+
+def test_box_rejects_delta_above_eta(gsm):
+    with pytest.raises(Exception):
+        gsm.Plan("coulomb3d", 1.0, (16, 16, 16), box=(10.0, 10.0, 0.005))
+    with pytest.raises(ValueError):
+        gsm.Plan("coulomb3d", 1.0, (16, 16, 16), box=(10.0, 10.0))
