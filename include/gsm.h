@@ -116,6 +116,7 @@ typedef struct {
     int launch_nl[5];           /* per pass: lines per CTA, */
     int launch_threads[5];      /*   threads per line, */
     int launch_emax[5];         /*   elements per thread (see gsm_plan_autotune) */
+    double box[3];              /* half-width of each axis (L for a cube), x first */
 } gsm_plan_info_t;
 
 void gsm_default_options(gsm_options_t *opt);
@@ -227,6 +228,32 @@ gsm_status_t gsm_hartree(gsm_plan_t p, const void *psi, void *u, void *energy, v
                          void *cuda_stream);
 
 gsm_status_t gsm_plan_info(gsm_plan_t p, gsm_plan_info_t *info);
+
+/*
+ * Saved plans (Sec. 2.2: the sum over q of w_q G_k^q does not depend on rho,
+ * so it is computed once per discretisation and stored).
+ *
+ * gsm_plan_save writes into the HOST buffer `buf` (capacity bytes) the plan's
+ * problem (kernel, d, n, box, delta, dipolar n and m, requested accuracy), its
+ * Gaussian sum (S, w_q, tau_q), Taylor coefficients c0, c2, the FP64 octant
+ * kernel tensor ((n_x+1)(n_y+1)(n_z+1) doubles) and the launch shape of every
+ * pass (as tuned by gsm_plan_autotune), followed by a 64-bit FNV-1a checksum.
+ * *bytes always receives the size needed; with buf == NULL nothing else
+ * happens (size query).  A buffer smaller than that size:
+ * GSM_ERR_INVALID_ARG.  Synchronous (device-to-host copies).
+ *
+ * gsm_plan_load creates a plan from such bytes without recomputing the
+ * Gaussian sum, the Taylor coefficients or the tensor; the multiplier,
+ * twiddles and workspace are rebuilt on `cuda_stream`.  precision < 0 keeps
+ * the saved precision (and its launch shapes); GSM_FP64 / GSM_FP32 /
+ * GSM_FP32X2 reuse the same FP64 tensor for another pass precision with
+ * default launch shapes.  The result equals the saved plan bit for bit.  A
+ * wrong magic, version, size or checksum: GSM_ERR_INVALID_ARG, *out = NULL.
+ * The format is native little-endian; the caller owns buf.
+ */
+gsm_status_t gsm_plan_save(gsm_plan_t p, void *buf, size_t capacity, size_t *bytes);
+gsm_status_t gsm_plan_load(gsm_plan_t *out, const void *buf, size_t bytes, int precision,
+                           void *cuda_stream);
 
 /* Free the plan's device memory (synchronises the device first). */
 gsm_status_t gsm_plan_destroy(gsm_plan_t p);

@@ -104,6 +104,53 @@ class Plan:
         self.shape = tuple(reversed(n))          # array shape, C order (x fastest)
         self.dtype = _io_dtype(precision)
 
+    # ------------------------------------------------------------------ save / load
+    def save(self, path=None) -> bytes:
+        """The plan's stored form (gsm_plan_save): Gaussian sum, Taylor
+        coefficients, FP64 kernel tensor and launch shapes.  Written to `path`
+        when given; returned either way."""
+        lib = _abi.load()
+        size = ctypes.c_size_t()
+        _abi.check(lib.gsm_plan_save(self.handle, None, 0, ctypes.byref(size)))
+        buf = ctypes.create_string_buffer(size.value)
+        _abi.check(lib.gsm_plan_save(self.handle, buf, size.value, ctypes.byref(size)))
+        data = buf.raw[: size.value]
+        if path is not None:
+            with open(path, "wb") as f:
+                f.write(data)
+        return data
+
+    @classmethod
+    def load(cls, src, precision: str | None = None, stream=None) -> "Plan":
+        """A plan from gsm_plan_save's bytes (or a file holding them), without
+        recomputing its Gaussian sum or tensor (gsm_plan_load).  `precision`
+        reuses the stored FP64 tensor for another pass precision."""
+        if isinstance(src, (bytes, bytearray, memoryview)):
+            data = bytes(src)
+        else:
+            with open(src, "rb") as f:
+                data = f.read()
+        if precision is not None and precision not in PRECISIONS:
+            raise ValueError(f"unknown precision {precision!r}")
+        lib = _abi.load()
+        buf = ctypes.create_string_buffer(data, len(data))
+        h = ctypes.c_void_p()
+        _abi.check(lib.gsm_plan_load(ctypes.byref(h), buf, len(data),
+                                     -1 if precision is None else PRECISIONS[precision], _stream_ptr(stream)))
+        self = cls.__new__(cls)
+        self._h = h
+        inf = _abi.PlanInfo()
+        _abi.check(lib.gsm_plan_info(h, ctypes.byref(inf)))
+        self.kernel = {v: k for k, v in KERNELS.items()}[inf.kernel]
+        self.d = inf.d
+        self.L = float(inf.L)
+        self.box = tuple(float(inf.box[a]) for a in range(inf.d))
+        self.n = tuple(int(inf.n[a]) for a in range(inf.d))
+        self.precision = {v: k for k, v in PRECISIONS.items()}[inf.precision]
+        self.shape = tuple(reversed(self.n))
+        self.dtype = _io_dtype(self.precision)
+        return self
+
     # ------------------------------------------------------------------ info
     @property
     def handle(self):
@@ -119,7 +166,8 @@ class Plan:
                 "bytes_workspace": inf.bytes_workspace, "npasses": inf.npasses,
                 "launch_nl": list(inf.launch_nl[: inf.npasses]),
                 "launch_threads": list(inf.launch_threads[: inf.npasses]),
-                "launch_emax": list(inf.launch_emax[: inf.npasses])}
+                "launch_emax": list(inf.launch_emax[: inf.npasses]),
+                "box": tuple(inf.box[: self.d])}
 
     def gs_terms(self):
         nt = self.info()["nterms"]

@@ -18,7 +18,8 @@ STATUS = {0: "GSM_OK", 1: "GSM_ERR_INVALID_ARG", 2: "GSM_ERR_UNSUPPORTED_SIZE", 
 EXPORTS = ["gsm_default_options", "gsm_plan", "gsm_apply", "gsm_apply_pass", "gsm_plan_autotune", "gsm_apply_host", "gsm_apply_batched",
            "gsm_hartree", "gsm_plan_info", "gsm_plan_destroy", "gsm_status_string", "gsm_last_error",
            "gsm_plan_gs_terms", "gsm_plan_kernel_tensor", "gsm_plan_factors", "gsm_fft_lines",
-           "gsm_fft_lines_noalloc", "gsm_batch_create", "gsm_batch_launch", "gsm_batch_destroy"]
+           "gsm_fft_lines_noalloc", "gsm_batch_create", "gsm_batch_launch", "gsm_batch_destroy",
+           "gsm_plan_save", "gsm_plan_load"]
 
 
 class Options(ctypes.Structure):
@@ -34,7 +35,7 @@ class PlanInfo(ctypes.Structure):
                 ("precision", ctypes.c_int), ("bytes_multiplier", ctypes.c_size_t),
                 ("bytes_workspace", ctypes.c_size_t), ("npasses", ctypes.c_int),
                 ("launch_nl", ctypes.c_int * 5), ("launch_threads", ctypes.c_int * 5),
-                ("launch_emax", ctypes.c_int * 5)]
+                ("launch_emax", ctypes.c_int * 5), ("box", ctypes.c_double * 3)]
 
 
 class GSMError(RuntimeError):
@@ -78,6 +79,8 @@ def load(path: str = LIB_PATH):
         L.gsm_hartree.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp]
         L.gsm_plan_info.argtypes = [_vp, ctypes.POINTER(PlanInfo)]
         L.gsm_plan_destroy.argtypes = [_vp]
+        L.gsm_plan_save.argtypes = [_vp, _vp, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)]
+        L.gsm_plan_load.argtypes = [ctypes.POINTER(_vp), _vp, ctypes.c_size_t, ctypes.c_int, _vp]
         L.gsm_status_string.argtypes = [ctypes.c_int]
         L.gsm_status_string.restype = ctypes.c_char_p
         L.gsm_last_error.argtypes = []

@@ -92,8 +92,8 @@ const char *gsm_status_string(gsm_status_t s)
 
 const char *gsm_last_error(void) { return g_last_error.c_str(); }
 
-gsm_status_t gsm_plan(gsm_plan_t *out, gsm_kernel_t kind, int d, double L, const int *n, double gs_eps,
-                      const gsm_options_t *opt, void *cuda_stream)
+static gsm_status_t create_plan(gsm_plan_t *out, gsm_kernel_t kind, int d, double L, const int *n, double gs_eps,
+                                const gsm_options_t *opt, void *cuda_stream, const StoredPlanData *stored)
 {
     if (!out) {
         set_error("out is NULL");
@@ -135,6 +135,11 @@ gsm_status_t gsm_plan(gsm_plan_t *out, gsm_kernel_t kind, int d, double L, const
     if (!(o.delta > 0.0) || o.delta >= 0.5) {
         set_error("options.delta must be in (0, 0.5)");
         return GSM_ERR_INVALID_ARG;
+    }
+    if (stored) {
+        // the box exactly as saved (L eta_a / L need not round back to eta_a)
+        L = stored->L;
+        for (int a = 0; a < d; ++a) eta[a] = stored->eta[a];
     }
     for (int a = 0; a < d; ++a)
         if (!(o.delta < eta[a])) {
@@ -189,12 +194,194 @@ gsm_status_t gsm_plan(gsm_plan_t *out, gsm_kernel_t kind, int d, double L, const
     p->magic = kPlanMagic;
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
     gsm_status_t s = configure_passes(p);
-    if (s == GSM_OK) s = build_plan_data(p, st);
+    if (s == GSM_OK) s = build_plan_data(p, st, stored);
     if (s != GSM_OK) {
         free_plan(p);
         return s;
     }
     *out = reinterpret_cast<gsm_plan_t>(p);
+    return GSM_OK;
+}
+
+gsm_status_t gsm_plan(gsm_plan_t *out, gsm_kernel_t kind, int d, double L, const int *n, double gs_eps,
+                      const gsm_options_t *opt, void *cuda_stream)
+{
+    return create_plan(out, kind, d, L, n, gs_eps, opt, cuda_stream, nullptr);
+}
+
+// ---------------------------------------------------------------- save / load
+// Layout (native little-endian, both supported hosts): a fixed header, the
+// Gaussian sum (w, tau), the FP64 octant kernel tensor, then a 64-bit FNV-1a
+// checksum of everything before it.
+static const uint64_t kSaveMagic = 0x47534d5341564531ull;   // "GSMSAVE1"
+static const uint32_t kSaveVersion = 1;
+
+struct SaveHeader {
+    uint64_t magic;
+    uint32_t version, header_bytes;
+    int32_t kind, d, n[3], precision, S, nterms, npasses, nl[5], emax[5], pad_;
+    double L, eta[3], eps, delta, dip_n[3], dip_m[3], gs_err, c0, c2;
+    uint64_t mult_elems;
+};
+
+static uint64_t fnv1a(const unsigned char *b, size_t len)
+{
+    uint64_t h = 14695981039346656037ull;
+    for (size_t i = 0; i < len; ++i) {
+        h ^= b[i];
+        h *= 1099511628211ull;
+    }
+    return h;
+}
+
+gsm_status_t gsm_plan_save(gsm_plan_t h, void *buf, size_t capacity, size_t *bytes)
+{
+    Plan *p = checked(h);
+    if (!p) {
+        set_error("bad plan handle");
+        return GSM_ERR_BAD_PLAN;
+    }
+    if (!bytes) {
+        set_error("bytes is NULL");
+        return GSM_ERR_INVALID_ARG;
+    }
+    const size_t need = sizeof(SaveHeader) + sizeof(double) * (2 * (size_t)p->nterms + p->mult_elems) +
+                        sizeof(uint64_t);
+    *bytes = need;
+    if (!buf) return GSM_OK;
+    if (capacity < need) {
+        set_error("buffer smaller than the saved plan (query the size with buf = NULL)");
+        return GSM_ERR_INVALID_ARG;
+    }
+    SaveHeader hd;
+    memset(&hd, 0, sizeof(hd));
+    hd.magic = kSaveMagic;
+    hd.version = kSaveVersion;
+    hd.header_bytes = sizeof(SaveHeader);
+    hd.kind = p->kind;
+    hd.d = p->d;
+    for (int a = 0; a < 3; ++a) {
+        hd.n[a] = a < p->d ? p->n[a] : 1;
+        hd.eta[a] = p->eta[a];
+        hd.dip_n[a] = p->opt.dip_n[a];
+        hd.dip_m[a] = p->opt.dip_m[a];
+    }
+    hd.precision = p->opt.precision;
+    hd.S = p->S;
+    hd.nterms = p->nterms;
+    hd.npasses = p->d == 3 ? 5 : 3;
+    const PassCfg *cf3[5] = {&p->cfg_xf, &p->cfg_yf, &p->cfg_conv, &p->cfg_yi, &p->cfg_xi};
+    const PassCfg *cf2[3] = {&p->cfg_xf, &p->cfg_conv, &p->cfg_xi};
+    for (int i = 0; i < hd.npasses; ++i) {
+        const PassCfg *c = p->d == 3 ? cf3[i] : cf2[i];
+        hd.nl[i] = c->nl;
+        hd.emax[i] = c->emax;
+    }
+    hd.L = p->L;
+    hd.eps = p->eps;
+    hd.delta = p->opt.delta;
+    hd.gs_err = p->gs_err;
+    hd.c0 = p->c0;
+    hd.c2 = p->c2;
+    hd.mult_elems = p->mult_elems;
+    unsigned char *b = static_cast<unsigned char *>(buf);
+    memcpy(b, &hd, sizeof(hd));
+    size_t off = sizeof(hd);
+    const size_t wb = sizeof(double) * p->nterms, kb = sizeof(double) * p->mult_elems;
+    GSM_CUDA_TRY(cudaSetDevice(p->device));
+    GSM_CUDA_TRY(cudaMemcpy(b + off, p->d_w, wb, cudaMemcpyDeviceToHost));
+    off += wb;
+    GSM_CUDA_TRY(cudaMemcpy(b + off, p->d_tau, wb, cudaMemcpyDeviceToHost));
+    off += wb;
+    GSM_CUDA_TRY(cudaMemcpy(b + off, p->d_khat, kb, cudaMemcpyDeviceToHost));
+    off += kb;
+    const uint64_t sum = fnv1a(b, off);
+    memcpy(b + off, &sum, sizeof(sum));
+    return GSM_OK;
+}
+
+gsm_status_t gsm_plan_load(gsm_plan_t *out, const void *buf, size_t bytes, int precision, void *cuda_stream)
+{
+    if (!out || !buf) {
+        set_error("out or buf is NULL");
+        return GSM_ERR_INVALID_ARG;
+    }
+    *out = nullptr;
+    const unsigned char *b = static_cast<const unsigned char *>(buf);
+    SaveHeader hd;
+    if (bytes < sizeof(hd) + sizeof(uint64_t)) {
+        set_error("saved plan: buffer too short");
+        return GSM_ERR_INVALID_ARG;
+    }
+    memcpy(&hd, b, sizeof(hd));
+    if (hd.magic != kSaveMagic || hd.version != kSaveVersion || hd.header_bytes != sizeof(SaveHeader)) {
+        set_error("saved plan: not a plan of this format version");
+        return GSM_ERR_INVALID_ARG;
+    }
+    if (hd.d < 2 || hd.d > 3 || hd.nterms < 1 || hd.nterms > kGsCap) {
+        set_error("saved plan: header out of range");
+        return GSM_ERR_INVALID_ARG;
+    }
+    uint64_t me = 1;
+    for (int a = 0; a < hd.d; ++a) {
+        if (hd.n[a] < kMinN || hd.n[a] > kMaxM) {
+            set_error("saved plan: header out of range");
+            return GSM_ERR_INVALID_ARG;
+        }
+        me *= (uint64_t)(hd.n[a] + 1);
+    }
+    const size_t need = sizeof(hd) + sizeof(double) * (2 * (size_t)hd.nterms + me) + sizeof(uint64_t);
+    if (hd.mult_elems != me || bytes != need) {
+        set_error("saved plan: size does not match its header");
+        return GSM_ERR_INVALID_ARG;
+    }
+    uint64_t sum;
+    memcpy(&sum, b + need - sizeof(sum), sizeof(sum));
+    if (sum != fnv1a(b, need - sizeof(sum))) {
+        set_error("saved plan: checksum mismatch (corrupted data)");
+        return GSM_ERR_INVALID_ARG;
+    }
+    // copy the arrays out (the buffer need not be 8-byte aligned)
+    std::vector<double> w(hd.nterms), tau(hd.nterms), khat(me);
+    size_t off = sizeof(hd);
+    memcpy(w.data(), b + off, sizeof(double) * hd.nterms);
+    off += sizeof(double) * hd.nterms;
+    memcpy(tau.data(), b + off, sizeof(double) * hd.nterms);
+    off += sizeof(double) * hd.nterms;
+    memcpy(khat.data(), b + off, sizeof(double) * me);
+
+    gsm_options_t o;
+    gsm_default_options(&o);
+    o.delta = hd.delta;
+    o.S = hd.S;
+    o.precision = (gsm_precision_t)(precision >= 0 ? precision : hd.precision);
+    for (int a = 0; a < 3; ++a) {
+        o.dip_n[a] = hd.dip_n[a];
+        o.dip_m[a] = hd.dip_m[a];
+    }
+    StoredPlanData sd;
+    sd.L = hd.L;
+    for (int a = 0; a < 3; ++a) sd.eta[a] = hd.eta[a];
+    sd.S = hd.S;
+    sd.nterms = hd.nterms;
+    sd.gs_err = hd.gs_err;
+    sd.c0 = hd.c0;
+    sd.c2 = hd.c2;
+    sd.w = w.data();
+    sd.tau = tau.data();
+    sd.khat = khat.data();
+    gsm_plan_t h = nullptr;
+    gsm_status_t s = create_plan(&h, (gsm_kernel_t)hd.kind, hd.d, hd.L, hd.n, hd.eps, &o, cuda_stream, &sd);
+    if (s != GSM_OK) return s;
+    Plan *p = reinterpret_cast<Plan *>(h);
+    p->eps = hd.eps;
+    if (o.precision == hd.precision && hd.npasses == (hd.d == 3 ? 5 : 3)) {
+        // the saved (possibly tuned) launch shapes; a shape this device
+        // cannot run keeps the default
+        for (int i = 0; i < hd.npasses; ++i)
+            if (set_pass_shape(p, i, hd.nl[i], hd.emax[i]) != GSM_OK) set_error("");
+    }
+    *out = h;
     return GSM_OK;
 }
 
@@ -475,6 +662,7 @@ gsm_status_t gsm_plan_info(gsm_plan_t h, gsm_plan_info_t *info)
         info->M[a] = a < p->d ? p->M[a] : 1;
     }
     info->L = p->L;
+    for (int a = 0; a < p->d; ++a) info->box[a] = p->L * p->eta[a];
     info->delta = p->opt.delta;
     info->S = p->S;
     info->nterms = p->nterms;

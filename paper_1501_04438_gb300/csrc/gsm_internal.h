@@ -68,14 +68,28 @@ struct Plan {
 // thread-local last error
 void set_error(const std::string &msg);
 
-// plan construction on the GPU (gsm_plan.cu)
-gsm_status_t build_plan_data(Plan *p, cudaStream_t st);
+// Precomputed results a saved plan carries (Sec. 2.2: the sum over q of
+// w_q G_k^q is stored once per discretisation and reused).  Host arrays.
+struct StoredPlanData {
+    double L = 0.0, eta[3] = {1.0, 1.0, 1.0};    // box, exactly as saved
+    int S = 0, nterms = 0;
+    double gs_err = 0.0, c0 = 0.0, c2 = 0.0;
+    const double *w = nullptr, *tau = nullptr;   // nterms each
+    const double *khat = nullptr;                // octant tensor, mult_elems entries
+};
+
+// plan construction on the GPU (gsm_plan.cu); with stored != NULL the
+// Gaussian sum, the Taylor coefficients and the kernel tensor are taken from
+// it instead of being computed
+gsm_status_t build_plan_data(Plan *p, cudaStream_t st, const StoredPlanData *stored = nullptr);
 
 // passes (gsm_passes.cu)
 gsm_status_t configure_passes(Plan *p);
 gsm_status_t launch_apply(const Plan *p, const void *rho, void *u, cudaStream_t st);
 gsm_status_t launch_pass(const Plan *p, int pass, const void *rho, void *u, cudaStream_t st);
 gsm_status_t autotune_plan(Plan *p, cudaStream_t st, std::string *report);
+// set the launch shape of one pass (nl lines per CTA, emax elements per thread)
+gsm_status_t set_pass_shape(Plan *p, int pass, int nl, int emax);
 gsm_status_t launch_batched(int count, const Plan *const *plans, const void *const *rho, void *const *u,
                             int nl, cudaStream_t st, bool dry);
 constexpr int kBatchLines = 4;      // default lines (warps) per CTA of the grouped batch kernels

@@ -919,6 +919,32 @@ gsm_status_t launch_pass(const Plan *p, int pass, const void *rho, void *u, cuda
     }
 }
 
+template <class Pol>
+gsm_status_t set_pass_shape_t(Plan *p, int pass, int nl, int emax)
+{
+    PassCfg c;
+    if (!make_cfg<Pol>(pass_len(p, pass), nl, emax, &c)) {
+        set_error("launch shape not valid for this pass");
+        return GSM_ERR_INVALID_ARG;
+    }
+    GSM_CUDA_TRY(raise_pass_smem<Pol>(p, pass, c));
+    *pass_cfg(p, pass) = c;
+    return GSM_OK;
+}
+
+gsm_status_t set_pass_shape(Plan *p, int pass, int nl, int emax)
+{
+    if (pass < 0 || pass >= (p->d == 3 ? 5 : 3)) {
+        set_error("pass out of range");
+        return GSM_ERR_INVALID_ARG;
+    }
+    switch (p->opt.precision) {
+    case GSM_FP64: return set_pass_shape_t<F64>(p, pass, nl, emax);
+    case GSM_FP32: return set_pass_shape_t<F32>(p, pass, nl, emax);
+    default: return set_pass_shape_t<DF64>(p, pass, nl, emax);
+    }
+}
+
 gsm_status_t autotune_plan(Plan *p, cudaStream_t st, std::string *report)
 {
     switch (p->opt.precision) {

@@ -439,7 +439,7 @@ __global__ void k_multiplier_dip_full(DipFull dp, const double *__restrict__ mC,
 }  // namespace
 
 // ---------------------------------------------------------------- host side
-gsm_status_t build_plan_data(Plan *p, cudaStream_t st)
+gsm_status_t build_plan_data(Plan *p, cudaStream_t st, const StoredPlanData *stored)
 {
     const int d = p->d;
     const double delta = p->opt.delta;
@@ -455,13 +455,19 @@ gsm_status_t build_plan_data(Plan *p, cudaStream_t st)
     GSM_CUDA_TRY(cudaMalloc(&p->d_tau, sizeof(double) * kGsCap));
 
     // 1. choose S (smallest meeting eps), scanning a first window then the rest
-    int S = p->opt.S;
-    double err = 0.0;
+    int S = stored ? stored->S : p->opt.S;
+    double err = stored ? stored->gs_err : 0.0;
     if (S > kSmax || S < 0) {
         set_error("options.S must be in [0, 500]");
         return GSM_ERR_INVALID_ARG;
     }
-    {
+    if (stored) {
+        const int want = (kind_gs == GSM_POISSON_2D) ? 2 * S + 2 : S + 1;
+        if (S < 1 || stored->nterms != want || stored->nterms > kGsCap) {
+            set_error("stored plan: Gaussian-sum size does not match its kernel");
+            return GSM_ERR_INVALID_ARG;
+        }
+    } else {
         double *d_err = nullptr;
         const int S_first = 4;
         const int count = kSmax - S_first + 1;
@@ -502,7 +508,12 @@ gsm_status_t build_plan_data(Plan *p, cudaStream_t st)
     p->S = S;
     p->gs_err = err;
     p->nterms = (kind_gs == GSM_POISSON_2D) ? 2 * S + 2 : S + 1;
-    k_gs_terms<<<1, 1024, 0, st>>>(kind_gs, S, delta, p->d_w, p->d_tau);
+    if (stored) {
+        GSM_CUDA_TRY(cudaMemcpyAsync(p->d_w, stored->w, sizeof(double) * p->nterms, cudaMemcpyHostToDevice, st));
+        GSM_CUDA_TRY(cudaMemcpyAsync(p->d_tau, stored->tau, sizeof(double) * p->nterms, cudaMemcpyHostToDevice, st));
+    } else {
+        k_gs_terms<<<1, 1024, 0, st>>>(kind_gs, S, delta, p->d_w, p->d_tau);
+    }
 
     // 2. 1-D factors per axis
     double *d_weid = nullptr;
@@ -524,16 +535,23 @@ gsm_status_t build_plan_data(Plan *p, cudaStream_t st)
     }
 
     // 3. Taylor coefficients
-    double *d_c = nullptr;
-    GSM_CUDA_TRY(cudaMalloc(&d_c, sizeof(double) * 2));
-    k_taylor<<<1, 256, 0, st>>>(kind_gs, d, p->nterms, p->d_w, p->d_tau, delta, d_c);
-    double hc[2];
-    GSM_CUDA_TRY(cudaMemcpyAsync(hc, d_c, sizeof(hc), cudaMemcpyDeviceToHost, st));
-    GSM_CUDA_TRY(cudaStreamSynchronize(st));
-    cudaFree(d_c);
-    cudaFree(d_weid);
-    p->c0 = hc[0];
-    p->c2 = hc[1];
+    if (stored) {
+        GSM_CUDA_TRY(cudaStreamSynchronize(st));
+        cudaFree(d_weid);
+        p->c0 = stored->c0;
+        p->c2 = stored->c2;
+    } else {
+        double *d_c = nullptr;
+        GSM_CUDA_TRY(cudaMalloc(&d_c, sizeof(double) * 2));
+        k_taylor<<<1, 256, 0, st>>>(kind_gs, d, p->nterms, p->d_w, p->d_tau, delta, d_c);
+        double hc[2];
+        GSM_CUDA_TRY(cudaMemcpyAsync(hc, d_c, sizeof(hc), cudaMemcpyDeviceToHost, st));
+        GSM_CUDA_TRY(cudaStreamSynchronize(st));
+        cudaFree(d_c);
+        cudaFree(d_weid);
+        p->c0 = hc[0];
+        p->c2 = hc[1];
+    }
 
     // 4. tensor and multiplier on the octant
     size_t tot = 1;
@@ -541,9 +559,12 @@ gsm_status_t build_plan_data(Plan *p, cudaStream_t st)
     p->mult_elems = tot;
     GSM_CUDA_TRY(cudaMalloc(&p->d_khat, sizeof(double) * tot));
     GSM_CUDA_TRY(cudaMalloc(&p->d_mult64, sizeof(double) * tot));
-    k_tensor<<<(tot + 127) / 128, 128, 0, st>>>(d, p->n[0], p->n[1], p->n[2], p->nterms, p->d_w,
-                                                  p->d_g[0], p->d_g[1], d > 2 ? p->d_g[2] : p->d_g[1],
-                                                  p->d_khat);
+    if (stored)
+        GSM_CUDA_TRY(cudaMemcpyAsync(p->d_khat, stored->khat, sizeof(double) * tot, cudaMemcpyHostToDevice, st));
+    else
+        k_tensor<<<(tot + 127) / 128, 128, 0, st>>>(d, p->n[0], p->n[1], p->n[2], p->nterms, p->d_w,
+                                                      p->d_g[0], p->d_g[1], d > 2 ? p->d_g[2] : p->d_g[1],
+                                                      p->d_khat);
     MultParams mp;
     mp.d = d;
     // general dipolar directions: the octant holds the Coulomb multiplier and

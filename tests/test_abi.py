@@ -58,6 +58,45 @@ def test_status_strings_without_gpu(libpath):
     assert b"L" in lib.gsm_last_error()
 
 
+def test_box_and_saved_plan_errors_without_gpu(libpath):
+    """Box validation and the checks of a saved plan run on the host, before
+    any CUDA call: a bad box, a short buffer, a wrong magic, a size that does
+    not match the header, a corrupted checksum."""
+    import struct
+    from paper_1501_04438_gb300 import _abi
+    lib = _abi.load(libpath)
+    h = ctypes.c_void_p()
+    n = (ctypes.c_int * 3)(16, 16, 16)
+    opt = _abi.Options()
+    lib.gsm_default_options(ctypes.byref(opt))
+    opt.box[0], opt.box[1], opt.box[2] = 4.0, -1.0, 2.0
+    assert lib.gsm_plan(ctypes.byref(h), 0, 3, 1.0, n, 0.0, ctypes.byref(opt), None) == 1
+    opt.box[1] = 4.0
+    opt.box[2] = 0.002          # eta = 5e-4 < delta = 1e-3
+    assert lib.gsm_plan(ctypes.byref(h), 0, 3, 1.0, n, 0.0, ctypes.byref(opt), None) == 1
+    assert b"delta" in lib.gsm_last_error()
+
+    size = ctypes.c_size_t()
+    assert lib.gsm_plan_save(None, None, 0, ctypes.byref(size)) == 7
+    assert lib.gsm_plan_load(ctypes.byref(h), b"short", 5, -1, None) == 1
+    # a header of the saved layout: magic, version, header bytes, 20 int32, 15 doubles, u64
+    nterms = 4
+    ints = [0, 3, 8, 8, 8, 0, 3, nterms, 5] + [1] * 5 + [8] * 5 + [0]
+    dbl = [1.0, 1.0, 1.0, 1.0, 2e-15, 1e-3, 0, 0, 1, 0, 0, 1, 0.0, 0.0, 0.0]
+    hdr = struct.pack("<QII20i15dQ", 0x47534D5341564531, 1, 224, *ints, *dbl, 9 ** 3)
+    assert len(hdr) == 224
+    body = hdr + b"\0" * (8 * (2 * nterms + 9 ** 3))
+    bad = body + struct.pack("<Q", 12345)
+    assert lib.gsm_plan_load(ctypes.byref(h), bad, len(bad), -1, None) == 1
+    assert b"checksum" in lib.gsm_last_error()
+    assert lib.gsm_plan_load(ctypes.byref(h), bad[:-8], len(bad) - 8, -1, None) == 1
+    assert b"size" in lib.gsm_last_error()
+    wrong = struct.pack("<Q", 7) + bad[8:]
+    assert lib.gsm_plan_load(ctypes.byref(h), wrong, len(wrong), -1, None) == 1
+    assert b"format" in lib.gsm_last_error()
+    assert h.value is None
+
+
 def test_missing_library_fails_loudly(tmp_path):
     from paper_1501_04438_gb300 import _abi
     saved = _abi._lib

@@ -447,3 +447,50 @@ def test_box_rejects_delta_above_eta(gsm):
         gsm.Plan("coulomb3d", 1.0, (16, 16, 16), box=(10.0, 10.0, 0.005))
     with pytest.raises(ValueError):
         gsm.Plan("coulomb3d", 1.0, (16, 16, 16), box=(10.0, 10.0))
+
+
+# ------------------------------------------------------------------ saved plans (Sec. 2.2)
+SAVE_CASES = [
+    ("coulomb3d", (24, 20, 16), dict(L=6.0)),
+    ("dipolar3d", (16, 16, 20), dict(L=5.0, dip_n=_unit(TABLE7_N), dip_m=_unit(TABLE7_M))),
+    ("coulomb2d", (40, 30), dict(L=1.0, box=(5.0, 3.0))),
+    ("poisson2d", (48, 32), dict(L=7.0)),
+    ("ds2d", (32, 40), dict(L=1.0, box=(4.0, 6.5))),
+]
+
+
+@pytest.mark.parametrize("kernel,n,kw", SAVE_CASES, ids=[c[0] for c in SAVE_CASES])
+def test_saved_plan_is_bit_identical(gsm, kernel, n, kw, tmp_path):
+    torch = _torch()
+    kw = dict(kw)
+    L = kw.pop("L")
+    plan = gsm.Plan(kernel, L, n, **kw)
+    if kernel == "coulomb3d":
+        plan.autotune()
+    path = tmp_path / "plan.gsm"
+    data = plan.save(path)
+    loaded = gsm.Plan.load(path)
+    assert loaded.kernel == kernel and loaded.n == plan.n and loaded.shape == plan.shape
+    assert np.allclose(loaded.box, plan.box, rtol=1e-15)
+    a, b = plan.info(), loaded.info()
+    for k in ("S", "nterms", "gs_err", "c0", "c2", "launch_nl", "launch_emax", "M"):
+        assert a[k] == b[k], k
+    assert np.array_equal(plan.kernel_tensor(), loaded.kernel_tensor())
+    assert all(np.array_equal(x, y) for x, y in zip(plan.gs_terms(), loaded.gs_terms()))
+    rho = torch.tensor(np.random.default_rng(31).standard_normal(plan.shape), device="cuda")
+    u0, u1 = plan.apply(rho), loaded.apply(rho)
+    torch.cuda.synchronize()
+    assert torch.equal(u0, u1)
+    # the same FP64 tensor serves the other pass precisions
+    for prec in ("fp32x2", "fp32"):
+        fresh = gsm.Plan(kernel, L, n, precision=prec, **kw)
+        other = gsm.Plan.load(data, precision=prec)
+        r = rho.to(fresh.dtype)
+        x, y = fresh.apply(r), other.apply(r)
+        torch.cuda.synchronize()
+        assert torch.equal(x, y), prec
+    # a flipped payload byte is caught by the checksum
+    bad = bytearray(data)
+    bad[300] ^= 1
+    with pytest.raises(gsm.GSMError, match="checksum"):
+        gsm.Plan.load(bytes(bad))
