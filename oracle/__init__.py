@@ -23,15 +23,17 @@ _LIB = os.path.join(_HERE, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
 
-KERNELS = {"coulomb3d": 0, "coulomb2d": 1, "poisson2d": 2, "dipolar3d": 3, "ds2d": 4}
-KERNEL_DIM = {"coulomb3d": 3, "coulomb2d": 2, "poisson2d": 2, "dipolar3d": 3, "ds2d": 2}
+KERNELS = {"coulomb3d": 0, "coulomb2d": 1, "poisson2d": 2, "dipolar3d": 3, "ds2d": 4, "power3d": 5, "power2d": 6}
+KERNEL_DIM = {"coulomb3d": 3, "coulomb2d": 2, "poisson2d": 2, "dipolar3d": 3, "ds2d": 2, "power3d": 3,
+              "power2d": 2}
 GS_CAP = 1024
 
 # Default accuracy targets of the Gaussian sums (Sec. 3.2-3.3): relative error
 # of 1/r and absolute error of ln r over [delta, 2 sqrt(d)].  Both sit just above
 # the rounding floor of the sums built in double (1/r: 0.9e-15 for delta = 1e-3,
 # 1.2e-15 for delta = 1e-4; ln r: about 5e-14).
-DEFAULT_EPS = {"coulomb3d": 2e-15, "coulomb2d": 2e-15, "dipolar3d": 2e-15, "poisson2d": 1e-13, "ds2d": 1e-13}
+DEFAULT_EPS = {"coulomb3d": 2e-15, "coulomb2d": 2e-15, "dipolar3d": 2e-15, "poisson2d": 1e-13, "ds2d": 1e-13,
+               "power3d": 2e-15, "power2d": 2e-15}
 
 
 def build(force: bool = False) -> str:
@@ -62,6 +64,7 @@ class Params(ctypes.Structure):
         ("dip_m", ctypes.c_double * 3),
         ("threads", ctypes.c_int),
         ("box", ctypes.c_double * 3),
+        ("beta", ctypes.c_double),
     ]
 
 
@@ -88,15 +91,15 @@ def lib():
             L.orc_gauss_legendre.argtypes = [ctypes.c_int, _dp, _dp]
             L.orc_gs_eval.argtypes = [ctypes.c_int, _dp, _dp, ctypes.c_double]
             L.orc_gs_eval.restype = ctypes.c_double
-            L.orc_gs_error.argtypes = [ctypes.c_int, ctypes.c_int, _dp, _dp, ctypes.c_double,
+            L.orc_gs_error.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_int, _dp, _dp, ctypes.c_double,
                                        ctypes.c_double, ctypes.c_int]
             L.orc_gs_error.restype = ctypes.c_double
             L.orc_gs_build.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double,
-                                       ctypes.c_int, ctypes.c_int, _dp, _dp, _ip, _ip, _dp]
+                                       ctypes.c_double, ctypes.c_int, ctypes.c_int, _dp, _dp, _ip, _ip, _dp]
             L.orc_factor.argtypes = [ctypes.c_double, ctypes.c_double]
             L.orc_factor.restype = ctypes.c_double
             L.orc_fftn.argtypes = [ctypes.c_int, _ip, _dp, ctypes.c_int]
-            L.orc_taylor_coeffs.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp, _dp,
+            L.orc_taylor_coeffs.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_int, _dp, _dp,
                                             ctypes.c_double, _dp, _dp]
             L.orc_kernel_hat.argtypes = [ctypes.POINTER(Params), _dp, ctypes.POINTER(Info)]
             L.orc_apply_parts.argtypes = [ctypes.POINTER(Params), _dp, _dp, _dp, _dp, ctypes.POINTER(Info)]
@@ -124,8 +127,10 @@ def gauss_legendre(m: int):
     return x, w
 
 
-def gs(kernel: str, delta: float = 1e-3, eps: float | None = None, S: int = 0, rmax: float | None = None):
-    """Gaussian sum (w_q, tau_q) of 1/r (Coulomb kernels) or ln r (Poisson).
+def gs(kernel: str, delta: float = 1e-3, eps: float | None = None, S: int = 0, rmax: float | None = None,
+       beta: float = 1.0):
+    """Gaussian sum (w_q, tau_q) of 1/r (Coulomb kernels), ln r (Poisson) or
+    r^-beta (power kernels).
 
     Returns (w, tau, S, err), err being E_rel or E_abs on [delta, rmax]."""
     base = {"dipolar3d": "coulomb3d", "ds2d": "poisson2d"}.get(kernel, kernel)
@@ -139,7 +144,7 @@ def gs(kernel: str, delta: float = 1e-3, eps: float | None = None, S: int = 0, r
     nt = ctypes.c_int()
     So = ctypes.c_int()
     err = ctypes.c_double()
-    rc = lib().orc_gs_build(KERNELS[base], delta, rmax, eps, S, GS_CAP, _ptr(w), _ptr(tau),
+    rc = lib().orc_gs_build(KERNELS[base], float(beta), delta, rmax, eps, S, GS_CAP, _ptr(w), _ptr(tau),
                             ctypes.byref(nt), ctypes.byref(So), ctypes.byref(err))
     if rc != 0:
         raise RuntimeError("oracle: no Gaussian sum meets the requested accuracy")
@@ -153,11 +158,11 @@ def gs_eval(w, tau, r):
     return np.array([lib().orc_gs_eval(len(w), _ptr(w), _ptr(tau), float(x)) for x in r])
 
 
-def gs_error(kernel, w, tau, delta, rmax, ns=4000):
+def gs_error(kernel, w, tau, delta, rmax, ns=4000, beta: float = 1.0):
     base = {"dipolar3d": "coulomb3d", "ds2d": "poisson2d"}.get(kernel, kernel)
     w = np.ascontiguousarray(w, dtype=np.float64)
     tau = np.ascontiguousarray(tau, dtype=np.float64)
-    return lib().orc_gs_error(KERNELS[base], len(w), _ptr(w), _ptr(tau), delta, rmax, ns)
+    return lib().orc_gs_error(KERNELS[base], float(beta), len(w), _ptr(w), _ptr(tau), delta, rmax, ns)
 
 
 def factor(tau: float, omega: float) -> float:
@@ -174,22 +179,23 @@ def fftn(a: np.ndarray, sign: int = -1) -> np.ndarray:
     return c
 
 
-def taylor_coeffs(kernel: str, w, tau, delta: float):
+def taylor_coeffs(kernel: str, w, tau, delta: float, beta: float = 1.0):
     base = {"dipolar3d": "coulomb3d", "ds2d": "poisson2d"}.get(kernel, kernel)
     d = KERNEL_DIM[kernel]
     w = np.ascontiguousarray(w, dtype=np.float64)
     tau = np.ascontiguousarray(tau, dtype=np.float64)
     c0 = ctypes.c_double()
     c2 = ctypes.c_double()
-    lib().orc_taylor_coeffs(KERNELS[base], d, len(w), _ptr(w), _ptr(tau), delta,
+    lib().orc_taylor_coeffs(KERNELS[base], float(beta), d, len(w), _ptr(w), _ptr(tau), delta,
                             ctypes.byref(c0), ctypes.byref(c2))
     return c0.value, c2.value
 
 
 def make_params(kernel: str, n, L: float, pad: int = 2, delta: float = 1e-3, eps: float | None = None,
                 S: int = 0, taylor_mode: int = 0, dip_n=(0.0, 0.0, 1.0), dip_m=(0.0, 0.0, 1.0),
-                threads: int = 0, box=None) -> Params:
-    """box: per-axis half-widths (x first) of a rectangular box; L is then unused."""
+                threads: int = 0, box=None, beta: float = 1.0) -> Params:
+    """box: per-axis half-widths (x first) of a rectangular box; L is then unused.
+    beta: exponent of the power kernels |x|^-beta."""
     d = KERNEL_DIM[kernel]
     if isinstance(n, int):
         n = [n] * d
@@ -212,6 +218,7 @@ def make_params(kernel: str, n, L: float, pad: int = 2, delta: float = 1e-3, eps
     bx = list(box) if box is not None else []
     for i in range(3):
         p.box[i] = float(bx[i]) if i < len(bx) else 0.0
+    p.beta = float(beta)
     return p
 
 

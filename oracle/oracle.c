@@ -11,6 +11,10 @@
  * The code is slow on purpose and follows the paper's steps in the paper's
  * order (Algorithm 1), so that a reader can check it against the paper by eye:
  *
+ * Kernels: 1/(4 pi |x|) and 1/(2 pi |x|) (Coulomb), -ln|x|/(2 pi) (Poisson),
+ * the dipolar and Davey-Stewartson potentials built on them (Sec. 2.4), and
+ * |x|^-beta, 0 < beta < d (remark after Eq. sinc_quad).
+ *
  *   Precomputation
  *     1. Gaussian sum (GS) of the kernel by sinc quadrature   (Sec. 3.1-3.3)
  *     2. Fourier coefficients sum_q w_q G_k^q of the kernel   (Eq. tensor)
@@ -174,6 +178,60 @@ static int gs_log(int S, double delta, double *w, double *tau)
     return q;   /* 2S + 2 terms */
 }
 
+/* ------------------------------------------------------------------------ */
+/* Remark after Eq. sinc_quad: GS of r^{-beta}, 0 < beta < d.  Eq. Gauss_int  */
+/* with alpha = beta - 1 and rho = r^2 (the identity needs a factor 1/2 on   */
+/* its right side: alpha = 0 must give Eq. GauInte) reads                    */
+/*   r^{-beta} = (2/Gamma(beta/2)) int_0^inf tau^{beta-1} exp(-r^2 tau^2) dtau. */
+/* The change of variables is left open.  tau = sinh t of Sec. 3.2 leaves    */
+/* |sinh t|^{beta-1}, not analytic at t = 0 unless beta is odd; we take the  */
+/* double-exponential map tau = exp(s - e^{-s}) (the transformation of       */
+/* Takahashi and Mori for half-infinite integrals), under which              */
+/*   r^{-beta} = (2/Gamma(beta/2)) int_R tau^beta (1 + e^{-s}) e^{-r^2 tau^2} ds */
+/* decays double-exponentially at both ends, and apply the sinc rule of     */
+/* Sec. 3.1 with S+1 nodes s_k = s_lo + k (s_hi - s_lo)/S.  The ends leave    */
+/* tails below eps/4 relative to r^{-beta} on [delta, rmax]:                 */
+/*   left:  (2/Gamma(beta/2)) tau_lo^beta / beta = (eps/4) rmax^{-beta}       */
+/*          (the integrand is below tau^{beta-1});                           */
+/*   right: delta^2 tau_hi^2 = ln(1/eps) + 10, where the relative tail is    */
+/*          the regularised Q(beta/2, delta^2 tau_hi^2) < e^{-10} eps/4 (beta < 3); */
+/* s_lo and s_hi solve s - e^{-s} = ln tau by Newton's method, started left */
+/* of the root (the map is concave, so the iterates increase to it).         */
+/* ------------------------------------------------------------------------ */
+static double de_solve(double X)
+{
+    double s = X > -1.0 ? X - 1.0 : -log(-X);
+    for (int it = 0; it < 100; it++) {
+        double ds = (s - exp(-s) - X) / (1.0 + exp(-s));
+        s -= ds;
+        if (fabs(ds) <= 1e-15 * (1.0 + fabs(s))) break;
+    }
+    return s;
+}
+
+static void power_ends(double beta, double delta, double rmax, double eps, double *slo, double *shi)
+{
+    double cn = 2.0 / tgamma(0.5 * beta);
+    double ln_tau_lo = (log(0.25 * eps * beta / cn) - beta * log(rmax)) / beta;
+    double ln_tau_hi = 0.5 * log(log(1.0 / eps) + 10.0) - log(delta);
+    *slo = de_solve(ln_tau_lo);
+    *shi = de_solve(ln_tau_hi);
+}
+
+static int gs_power(int S, double beta, double delta, double rmax, double eps, double *w, double *tau)
+{
+    double slo, shi;
+    power_ends(beta, delta, rmax, eps, &slo, &shi);
+    double th = (shi - slo) / S, cn = 2.0 / tgamma(0.5 * beta);
+    for (int k = 0; k <= S; k++) {
+        double s = slo + k * th;
+        double lt = s - exp(-s);               /* ln tau */
+        tau[k] = exp(lt);
+        w[k] = cn * th * exp(beta * lt) * (1.0 + exp(-s));
+    }
+    return S + 1;
+}
+
 double orc_gs_eval(int nterms, const double *w, const double *tau, double r)
 {
     double s = 0.0;
@@ -185,23 +243,27 @@ double orc_gs_eval(int nterms, const double *w, const double *tau, double r)
 }
 
 static int kernel_is_log(int kernel) { return kernel == ORC_POISSON_2D; }
+static int kernel_is_power(int kernel) { return kernel == ORC_POWER_3D || kernel == ORC_POWER_2D; }
 
-/* E_rel (1/r, Sec. 3.2) or E_abs (ln r, Sec. 3.3) on a geometric sample of  */
-/* [delta, rmax] with ns points, both end points included.                   */
-double orc_gs_error(int kernel, int nterms, const double *w, const double *tau,
+/* E_rel (1/r, Sec. 3.2; r^{-beta}) or E_abs (ln r, Sec. 3.3) on a geometric */
+/* sample of [delta, rmax] with ns points, both end points included.         */
+double orc_gs_error(int kernel, double beta, int nterms, const double *w, const double *tau,
                     double delta, double rmax, int ns)
 {
     double e = 0.0;
     for (int i = 0; i < ns; i++) {
         double r = delta * pow(rmax / delta, (double)i / (ns - 1));
         double g = orc_gs_eval(nterms, w, tau, r);
-        double err = kernel_is_log(kernel) ? fabs(log(r) - g) : fabs(1.0 - r * g);
+        double err;
+        if (kernel_is_log(kernel)) err = fabs(log(r) - g);
+        else if (kernel_is_power(kernel)) err = fabs(1.0 - pow(r, beta) * g);
+        else err = fabs(1.0 - r * g);
         if (err > e) e = err;
     }
     return e;
 }
 
-int orc_gs_build(int kernel, double delta, double rmax, double eps, int S_fixed,
+int orc_gs_build(int kernel, double beta, double delta, double rmax, double eps, int S_fixed,
                  int cap, double *w, double *tau, int *nterms, int *S_out, double *err)
 {
     int Smin = S_fixed > 0 ? S_fixed : 4;
@@ -209,9 +271,11 @@ int orc_gs_build(int kernel, double delta, double rmax, double eps, int S_fixed,
     for (int S = Smin; S <= Smax; S++) {
         int need = kernel_is_log(kernel) ? 2 * S + 2 : S + 1;
         if (need > cap) return ORC_ERR;
-        int nt = kernel_is_log(kernel) ? gs_log(S, delta, w, tau)
-                                       : gs_coulomb(S, 2.1, w, tau);
-        double e = orc_gs_error(kernel, nt, w, tau, delta, rmax, ORC_GS_NSAMPLE);
+        int nt;
+        if (kernel_is_log(kernel)) nt = gs_log(S, delta, w, tau);
+        else if (kernel_is_power(kernel)) nt = gs_power(S, beta, delta, rmax, eps, w, tau);
+        else nt = gs_coulomb(S, 2.1, w, tau);
+        double e = orc_gs_error(kernel, beta, nt, w, tau, delta, rmax, ORC_GS_NSAMPLE);
         if (S_fixed > 0 || e <= eps) {
             *nterms = nt;
             *S_out = S;
@@ -367,15 +431,17 @@ static double gauss_moment(const gl_rule *g, int m, double tau, double delta)
     return sum;
 }
 
-static double kernel_moment(int kernel, int m, double delta)
+static double kernel_moment(int kernel, double beta, int m, double delta)
 {
     /* int_0^delta r^m U1(r) dr */
     if (kernel_is_log(kernel))
         return pow(delta, m + 1) * (log(delta) / (m + 1) - 1.0 / ((m + 1.0) * (m + 1.0)));
+    if (kernel_is_power(kernel))
+        return pow(delta, m + 1 - beta) / (m + 1 - beta);   /* U1 = r^{-beta}, beta < m + 1 */
     return pow(delta, m) / m;   /* U1 = 1/r */
 }
 
-int orc_taylor_coeffs(int kernel, int d, int nterms, const double *w, const double *tau,
+int orc_taylor_coeffs(int kernel, double beta, int d, int nterms, const double *w, const double *tau,
                       double delta, double *c0, double *c2)
 {
     gl_rule g;
@@ -386,7 +452,7 @@ int orc_taylor_coeffs(int kernel, int d, int nterms, const double *w, const doub
     for (int i = 0; i < 2; i++) {
         double gs = 0.0;
         for (int q = 0; q < nterms; q++) gs += w[q] * gauss_moment(&g, ms[i], tau[q], delta);
-        A[i] = kernel_moment(kernel, ms[i], delta) - gs;
+        A[i] = kernel_moment(kernel, beta, ms[i], delta) - gs;
     }
     *c0 = area * A[0];
     *c2 = area / (2.0 * d) * A[1];
@@ -408,7 +474,7 @@ static int base_kernel(int kernel)
 
 static int kernel_dim(int kernel)
 {
-    return (kernel == ORC_COULOMB_3D || kernel == ORC_DIPOLAR_3D) ? 3 : 2;
+    return (kernel == ORC_COULOMB_3D || kernel == ORC_DIPOLAR_3D || kernel == ORC_POWER_3D) ? 3 : 2;
 }
 
 static size_t prod(int d, const int *n)
@@ -459,7 +525,7 @@ int orc_plan_gs(const orc_params_t *p, double *w, double *tau, int cap, orc_info
     double rmax = 2.0 * sqrt(rr);
     int nt, S;
     double err;
-    if (orc_gs_build(kb, p->delta, rmax, p->gs_eps, p->gs_S, cap, w, tau, &nt, &S, &err) != ORC_OK)
+    if (orc_gs_build(kb, p->beta, p->delta, rmax, p->gs_eps, p->gs_S, cap, w, tau, &nt, &S, &err) != ORC_OK)
         return -1;   /* no Gaussian sum meets gs_eps (callers test nt <= 0) */
     if (info) {
         info->S = S;
@@ -576,7 +642,7 @@ static struct orc_prepared_s *prepare_scalar(const orc_params_t *p, int kernel)
         free(h);
         return NULL;
     }
-    orc_taylor_coeffs(kernel, h->d, nt, w, tau, p->delta, &h->c0, &h->c2);
+    orc_taylor_coeffs(kernel, p->beta, h->d, nt, w, tau, p->delta, &h->c0, &h->c2);
     h->info.c0 = h->c0;
     h->info.c2 = h->c2;
     for (int a = 0; a < 3; a++) {
@@ -671,6 +737,7 @@ static int run_scalar(const struct orc_prepared_s *h, const double *rho, double 
     double s;
     if (kernel == ORC_COULOMB_3D) s = L * L / (4.0 * PI);
     else if (kernel == ORC_COULOMB_2D) s = L / (2.0 * PI);
+    else if (kernel_is_power(kernel)) s = pow(L, d - p->beta);   /* |L x~|^{-beta} L^d dx~ */
     else s = -L * L / (2.0 * PI);              /* ln kernel, -1/(2 pi) ln|x| */
     double extra = 0.0;
     if (kernel == ORC_POISSON_2D && !dn) {   /* a derivative source has zero mass */
@@ -703,6 +770,7 @@ static int check_params(const orc_params_t *p)
     if (p->d != d || box_eta(p, eta) <= 0 || p->delta <= 0 || (p->pad != 2 && p->pad != 3)) return ORC_ERR;
     for (int a = 0; a < d; a++)
         if (p->delta >= eta[a]) return ORC_ERR;   /* Sec. 2.5: delta smaller than eta */
+    if (kernel_is_power(p->kernel) && !(p->beta > 0.0 && p->beta < d)) return ORC_ERR;
     for (int a = 0; a < d; a++)
         if (p->n[a] < 2 || p->n[a] % 2) return ORC_ERR;
 #ifdef _OPENMP

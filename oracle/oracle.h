@@ -9,7 +9,8 @@
 extern "C" {
 #endif
 
-enum { ORC_COULOMB_3D = 0, ORC_COULOMB_2D = 1, ORC_POISSON_2D = 2, ORC_DIPOLAR_3D = 3, ORC_DS_2D = 4 };
+enum { ORC_COULOMB_3D = 0, ORC_COULOMB_2D = 1, ORC_POISSON_2D = 2, ORC_DIPOLAR_3D = 3, ORC_DS_2D = 4,
+       ORC_POWER_3D = 5, ORC_POWER_2D = 6 };   /* power: U = |x|^{-beta}, 0 < beta < d */
 enum { ORC_OK = 0, ORC_ERR = 1 };
 
 #define ORC_GS_CAP 1024      /* max number of Gaussian terms */
@@ -31,6 +32,7 @@ typedef struct {
     int threads;        /* OpenMP threads (0: default) */
     double box[3];      /* > 0: half-width of axis a (rectangular box, Sec. 2.5); */
                         /* all 0: the cube [-L, L]^d                           */
+    double beta;        /* exponent of the power kernels */
 } orc_params_t;
 
 typedef struct {
@@ -40,13 +42,13 @@ typedef struct {
 
 void orc_gauss_legendre(int m, double *x, double *w);
 double orc_gs_eval(int nterms, const double *w, const double *tau, double r);
-double orc_gs_error(int kernel, int nterms, const double *w, const double *tau,
+double orc_gs_error(int kernel, double beta, int nterms, const double *w, const double *tau,
                     double delta, double rmax, int ns);
-int orc_gs_build(int kernel, double delta, double rmax, double eps, int S_fixed,
+int orc_gs_build(int kernel, double beta, double delta, double rmax, double eps, int S_fixed,
                  int cap, double *w, double *tau, int *nterms, int *S_out, double *err);
 double orc_factor(double tau, double omega);
 int orc_fftn(int d, const int *shape, double *data, int sign);
-int orc_taylor_coeffs(int kernel, int d, int nterms, const double *w, const double *tau,
+int orc_taylor_coeffs(int kernel, double beta, int d, int nterms, const double *w, const double *tau,
                       double delta, double *c0, double *c2);
 int orc_plan_gs(const orc_params_t *p, double *w, double *tau, int cap, orc_info_t *info);
 int orc_kernel_hat(const orc_params_t *p, double *khat, orc_info_t *info);

@@ -107,3 +107,15 @@ def coulomb_gaussian_axes_points(points, widths, dim):
         val, _ = integrate.quad(f, 0, np.inf, epsabs=0, epsrel=1e-13, limit=400)
         out[k] = pref * 2.0 / np.sqrt(np.pi) * val
     return out
+
+
+def power_gaussian(r, sigma, beta, d):
+    """Potential of exp(-|x|^2/sigma^2) under U = |x|^-beta in R^d (0 < beta < d):
+    from r^-beta = (2/Gamma(beta/2)) int_0^inf tau^(beta-1) exp(-r^2 tau^2) dtau
+    (Eq. Gauss_int, alpha = beta - 1) and the Gaussian convolution,
+    u = pi^(d/2) sigma^(d-beta) Gamma((d-beta)/2)/Gamma(d/2) 1F1(beta/2; d/2; -r^2/sigma^2),
+    the confluent hypergeometric function from scipy.special."""
+    from scipy.special import gamma, hyp1f1
+    r = np.asarray(r, dtype=np.float64)
+    c = np.pi ** (d / 2) * sigma ** (d - beta) * gamma((d - beta) / 2) / gamma(d / 2)
+    return c * hyp1f1(beta / 2, d / 2, -r * r / sigma ** 2)

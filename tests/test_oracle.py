@@ -16,7 +16,7 @@ import oracle
 from paper_1501_04438_gb300 import workloads as wl
 
 from closed_forms import (coulomb2d_gaussian, coulomb3d_gaussian, coulomb_gaussian_axes_points,
-                          dipolar3d_gaussian, ds2d_gaussian, poisson2d_gaussian)
+                          dipolar3d_gaussian, ds2d_gaussian, poisson2d_gaussian, power_gaussian)
 
 GOLDEN = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_tables.json")))
 
@@ -106,6 +106,42 @@ def test_gs_log_converges():
         assert b < a / 5.0
 
 
+POWER_BETAS = [("power3d", b) for b in (0.5, 1.0, 1.7, 2.5, 2.9)] + [("power2d", b) for b in (0.3, 1.0, 1.5, 1.9)]
+
+
+@pytest.mark.parametrize("kernel,beta", POWER_BETAS, ids=[f"{k}-b{b}" for k, b in POWER_BETAS])
+def test_gs_power_relative_error_on_interval(kernel, beta):
+    """r^-beta (remark after Eq. sinc_quad): relative error on [delta, 2 sqrt(d)]
+    at an independent random sample, with a term count of the Coulomb sum's order."""
+    delta = 1e-3
+    d = oracle.KERNEL_DIM[kernel]
+    w, tau, S, err = oracle.gs(kernel, delta=delta, beta=beta)
+    rng = np.random.default_rng(4)
+    r = delta * (2 * np.sqrt(d) / delta) ** rng.uniform(0, 1, 20000)
+    e = np.max(np.abs(1.0 - r ** beta * _indep_eval(w, tau, r)))
+    assert e < 3e-15, e
+    assert err <= 2e-15 and 80 < S < 200
+    assert np.all(w > 0) and np.all(np.diff(tau) > 0)
+
+
+def test_gs_power_converges_exponentially():
+    errs = [oracle.gs("power3d", S=S, beta=1.7)[3] for S in (40, 60, 80, 100)]
+    for a, b in zip(errs, errs[1:]):
+        assert b < a / 20.0, errs
+
+
+def test_gs_power_moment():
+    """int_delta^R r^2 e^{-r^2} U_GS(r) dr for U = r^-1.5 against QUADPACK on the
+    exact kernel (a wrong normalisation Gamma(beta/2) shows here)."""
+    delta, R, beta = 1e-3, 2 * np.sqrt(3), 1.5
+    w, tau, _, _ = oracle.gs("power3d", delta=delta, beta=beta)
+    f = lambda r: r * r * np.exp(-r * r) * float(_indep_eval(w, tau, np.array([r]))[0])
+    val, _ = integrate.quad(f, delta, R, epsabs=1e-17, epsrel=2e-14, limit=200)
+    ref, _ = integrate.quad(lambda r: r ** (2 - beta) * np.exp(-r * r), delta, R, epsabs=1e-17, epsrel=2e-14,
+                            limit=200)
+    assert abs(val - ref) < 2e-14 * ref
+
+
 # --- 1-D factors of Eq. tensor ---------------------------------------------------
 
 def test_factor_tau_zero_is_exact():
@@ -153,19 +189,22 @@ def _moment(m, tau, delta):
     return gamma(a) * gammainc(a, (tau * delta) ** 2) / (2.0 * tau ** (m + 1))
 
 
-@pytest.mark.parametrize("kernel", ["coulomb3d", "coulomb2d", "poisson2d"])
-def test_taylor_coefficients_incomplete_gamma(kernel):
+@pytest.mark.parametrize("kernel,beta", [("coulomb3d", 1.0), ("coulomb2d", 1.0), ("poisson2d", 1.0),
+                                         ("power3d", 0.5), ("power3d", 2.5), ("power2d", 1.5)])
+def test_taylor_coefficients_incomplete_gamma(kernel, beta):
     """c0, c2 against the same integrals through the regularised incomplete gamma."""
     d = oracle.KERNEL_DIM[kernel]
     delta = 1e-3
-    w, tau, _, _ = oracle.gs(kernel, delta=delta)
-    c0, c2 = oracle.taylor_coeffs(kernel, w, tau, delta)
+    w, tau, _, _ = oracle.gs(kernel, delta=delta, beta=beta)
+    c0, c2 = oracle.taylor_coeffs(kernel, w, tau, delta, beta=beta)
     area = 4 * np.pi if d == 3 else 2 * np.pi
     ref = []
     for m in (d - 1, d + 1):
         gs = sum(wq * _moment(m, tq, delta) for wq, tq in zip(w, tau))
         if kernel == "poisson2d":
             exact = delta ** (m + 1) * (np.log(delta) / (m + 1) - 1.0 / (m + 1) ** 2)
+        elif kernel.startswith("power"):
+            exact = delta ** (m + 1 - beta) / (m + 1 - beta)
         else:
             exact = delta ** m / m
         ref.append(exact - gs)
@@ -346,6 +385,44 @@ def test_box_axis_permutation():
         assert relmax(u2.T, u) < 1e-13, kernel
 
 
+POWER_CASES = [(3, 0.5, 64, 3e-15), (3, 1.7, 64, 3e-15), (3, 2.5, 64, 1e-14), (3, 2.9, 64, 4e-14),
+               (2, 0.3, 128, 4e-15), (2, 1.5, 128, 4e-15), (2, 1.9, 128, 2e-14),
+               (3, 1.0, 32, None), (2, 1.0, 32, None)]
+
+
+@pytest.mark.parametrize("d,beta,n,tol", POWER_CASES, ids=[f"d{c[0]}-b{c[1]}-n{c[2]}" for c in POWER_CASES])
+def test_power_kernel_closed_form(d, beta, n, tol):
+    """U = |x|^-beta on [-8,8]^d, rho = exp(-|x|^2/1.44), against the
+    confluent-hypergeometric form (scipy.special.hyp1f1).  Resolved grids
+    (h = 1/4, 1/8) sit at the floor, which rises as beta -> d with the
+    cancellation in c0; at h = 1/2 the error is the discretisation error the
+    Coulomb tables print for the same density (Tables Tab_Coulomb3D and
+    Tab_Coulomb2D, h = 1/2: 1.130e-9 and 1.720e-9)."""
+    C = wl.mesh((n,) * d, 8.0)
+    r = np.sqrt(sum(c * c for c in C))
+    rho = np.exp(-r * r / 1.44)
+    u, _ = oracle.apply("power3d" if d == 3 else "power2d", rho, 8.0, beta=beta)
+    E = relmax(u, power_gaussian(r, 1.2, beta, d))
+    if tol is None:
+        printed = 1.130e-9 if d == 3 else 1.720e-9
+        assert abs(E - printed) <= 0.002 * printed, E
+    else:
+        assert E < tol, E
+
+
+def test_power_beta_one_is_coulomb():
+    """|x|^-1 is 4 pi (3D) or 2 pi (2D) times the Coulomb kernel: two different
+    Gaussian sums (Sec. 3.2's and the power construction) agree to the floor on
+    a resolved density (their near fields differ inside B_delta, which the
+    Taylor correction accounts for only to the order of Eq. I_2h)."""
+    for kernel, c, shape in (("coulomb3d", 4 * np.pi, (32, 28, 36)), ("coulomb2d", 2 * np.pi, (40, 36))):
+        C = wl.mesh(shape, 4.0)
+        rho = wl.gaussian(C, [0.4, -0.3, 0.2][: len(shape)], [0.8, 0.7, 0.9][: len(shape)])
+        u1, _ = oracle.apply("power" + kernel[-2:], rho, 4.0, beta=1.0)
+        u2, _ = oracle.apply(kernel, rho, 4.0)
+        assert relmax(u1, c * u2) < 5e-15, kernel
+
+
 def test_config1_closed_form():
     """3D Coulomb, [-8,8]^3, n=32, rho = exp(-|x|^2): error against the erf form
     is the method's discretisation error at h = 1/2."""
@@ -359,7 +436,8 @@ def test_config1_closed_form():
 
 # --- invariants ---------------------------------------------------------------------
 
-@pytest.mark.parametrize("kernel", ["coulomb3d", "coulomb2d", "poisson2d", "dipolar3d", "ds2d"])
+@pytest.mark.parametrize("kernel", ["coulomb3d", "coulomb2d", "poisson2d", "dipolar3d", "ds2d", "power3d",
+                                    "power2d"])
 @pytest.mark.parametrize("mode", [0, 1])
 def test_linear_and_symmetric(kernel, mode):
     d = oracle.KERNEL_DIM[kernel]
@@ -367,7 +445,7 @@ def test_linear_and_symmetric(kernel, mode):
     rng = np.random.default_rng(5)
     a = rng.standard_normal((n,) * d)
     b = rng.standard_normal((n,) * d)
-    kw = dict(taylor_mode=mode, dip_n=(0.6, 0.0, 0.8), dip_m=(0.0, 1.0, 0.0))
+    kw = dict(taylor_mode=mode, dip_n=(0.6, 0.0, 0.8), dip_m=(0.0, 1.0, 0.0), beta=1.3)
     # the additive ln L term of Sec. 2.1 is symmetric too: (mass a)(sum b)
     ua, _ = oracle.apply(kernel, a, 3.0, **kw)
     ub, _ = oracle.apply(kernel, b, 3.0, **kw)
