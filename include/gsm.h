@@ -57,7 +57,9 @@ typedef enum {
     GSM_COULOMB_2D = 1,
     GSM_POISSON_2D = 2,
     GSM_DIPOLAR_3D = 3,
-    GSM_DAVEY_STEWARTSON_2D = 4
+    GSM_DAVEY_STEWARTSON_2D = 4,
+    GSM_POWER_3D = 5,            /* U = |x|^-beta, 0 < beta < 3 (remark after Eq. sinc_quad) */
+    GSM_POWER_2D = 6             /* U = |x|^-beta, 0 < beta < 2 */
 } gsm_kernel_t;
 
 /* Arithmetic of the FFT passes and of the multiplier product.
@@ -100,6 +102,8 @@ typedef struct {
                                    and L is ignored; all 0 (default): [-L, L]^d.  The
                                    method is rescaled by the largest half-width; delta
                                    must be smaller than every box[a] / max box */
+    double beta;                /* exponent of GSM_POWER_3D / GSM_POWER_2D, 0 < beta < d
+                                   (default 1) */
 } gsm_options_t;
 
 /* Read-only facts about a plan. */
@@ -117,25 +121,28 @@ typedef struct {
     int launch_threads[5];      /*   threads per line, */
     int launch_emax[5];         /*   elements per thread (see gsm_plan_autotune) */
     double box[3];              /* half-width of each axis (L for a cube), x first */
+    double beta;                /* exponent of the power kernels (1 otherwise) */
 } gsm_plan_info_t;
 
 void gsm_default_options(gsm_options_t *opt);
 
 /*
- * Make a plan (Algorithm 1, "Precomputation"): the Gaussian sum of 1/r or ln r
- * by sinc quadrature (Sec. 3.1-3.3), the 1-D factors of Eq. tensor, the stored
+ * Make a plan (Algorithm 1, "Precomputation"): the Gaussian sum of 1/r, ln r or
+ * r^-beta by sinc quadrature (Sec. 3.1-3.3; r^-beta through Eq. Gauss_int with
+ * alpha = beta - 1 and the map tau = exp(s - e^-s)), the 1-D factors of Eq. tensor, the stored
  * tensor sum_q w_q G_k^q with the Taylor coefficients of Sec. 2.3 and the
  * rescaling constants of Sec. 2.1 folded in, and the twiddle tables.  All of it
  * is computed on the current CUDA device, in FP64, on `cuda_stream`; the call
  * synchronises that stream before it returns.
  *   out    : receives the handle (set to NULL on failure).
- *   kind   : kernel; d must be 3 for GSM_COULOMB_3D and GSM_DIPOLAR_3D, 2 otherwise.
- *            GSM_DAVEY_STEWARTSON_2D uses the Gaussian sum of ln r.
+ *   kind   : kernel; d must be 3 for GSM_COULOMB_3D, GSM_DIPOLAR_3D and
+ *            GSM_POWER_3D, 2 otherwise.  GSM_DAVEY_STEWARTSON_2D uses the Gaussian
+ *            sum of ln r.  The power kernels take beta from opt (0 < beta < d).
  *   L      : half-width of the box [-L, L]^d, > 0.
  *   n      : d points per axis (x first), each even, >= 8, with 2n a product of
  *            2, 3 and 5 and 2n <= 8192.
  *   gs_eps : target accuracy of the Gaussian sum; <= 0 selects the default
- *            (2e-15 relative for 1/r, 1e-13 absolute for ln r), just above the
+ *            (2e-15 relative for 1/r and r^-beta, 1e-13 absolute for ln r), just above the
  *            rounding floors of the sums built in double (1/r: 0.9e-15 for
  *            delta = 1e-3, 1.2e-15 for delta = 1e-4; ln r: about 5e-14).
  *   opt    : NULL for defaults.
@@ -234,7 +241,7 @@ gsm_status_t gsm_plan_info(gsm_plan_t p, gsm_plan_info_t *info);
  * so it is computed once per discretisation and stored).
  *
  * gsm_plan_save writes into the HOST buffer `buf` (capacity bytes) the plan's
- * problem (kernel, d, n, box, delta, dipolar n and m, requested accuracy), its
+ * problem (kernel, d, n, box, delta, beta, dipolar n and m, requested accuracy), its
  * Gaussian sum (S, w_q, tau_q), Taylor coefficients c0, c2, the FP64 octant
  * kernel tensor ((n_x+1)(n_y+1)(n_z+1) doubles) and the launch shape of every
  * pass (as tuned by gsm_plan_autotune), followed by a 64-bit FNV-1a checksum.

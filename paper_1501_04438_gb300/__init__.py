@@ -61,11 +61,13 @@ class Plan:
     dip_n, dip_m : dipolar unit vectors
     box       : per-axis half-widths (x first) of a rectangular box; L is then
                 ignored (Sec. 2.5)
+    beta      : exponent of the power kernels |x|^-beta ("power3d", "power2d"),
+                0 < beta < d
     """
 
     def __init__(self, kernel: str, L: float, n, gs_eps: float = 0.0, precision: str = "fp64",
                  delta: float = 1e-3, S: int = 0, dip_n=(0.0, 0.0, 1.0), dip_m=(0.0, 0.0, 1.0),
-                 stream=None, box=None):
+                 stream=None, box=None, beta: float = 1.0):
         lib = _abi.load()
         if kernel not in KERNELS:
             raise ValueError(f"unknown kernel {kernel!r}")
@@ -82,6 +84,7 @@ class Plan:
         opt.delta = float(delta)
         opt.S = int(S)
         opt.precision = PRECISIONS[precision]
+        opt.beta = float(beta)
         for i in range(3):
             opt.dip_n[i] = float(dip_n[i])
             opt.dip_m[i] = float(dip_m[i])
@@ -167,7 +170,7 @@ class Plan:
                 "launch_nl": list(inf.launch_nl[: inf.npasses]),
                 "launch_threads": list(inf.launch_threads[: inf.npasses]),
                 "launch_emax": list(inf.launch_emax[: inf.npasses]),
-                "box": tuple(inf.box[: self.d])}
+                "box": tuple(inf.box[: self.d]), "beta": inf.beta}
 
     def gs_terms(self):
         nt = self.info()["nterms"]

@@ -8,8 +8,9 @@ import threading
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libgsm.so")
 
-KERNELS = {"coulomb3d": 0, "coulomb2d": 1, "poisson2d": 2, "dipolar3d": 3, "ds2d": 4}
-KERNEL_DIM = {"coulomb3d": 3, "coulomb2d": 2, "poisson2d": 2, "dipolar3d": 3, "ds2d": 2}
+KERNELS = {"coulomb3d": 0, "coulomb2d": 1, "poisson2d": 2, "dipolar3d": 3, "ds2d": 4, "power3d": 5, "power2d": 6}
+KERNEL_DIM = {"coulomb3d": 3, "coulomb2d": 2, "poisson2d": 2, "dipolar3d": 3, "ds2d": 2, "power3d": 3,
+              "power2d": 2}
 PRECISIONS = {"fp64": 0, "fp32": 1, "fp32x2": 2}
 STATUS = {0: "GSM_OK", 1: "GSM_ERR_INVALID_ARG", 2: "GSM_ERR_UNSUPPORTED_SIZE", 3: "GSM_ERR_OOM",
           4: "GSM_ERR_CUDA", 5: "GSM_ERR_ACCURACY", 6: "GSM_ERR_TIMEOUT", 7: "GSM_ERR_BAD_PLAN"}
@@ -25,7 +26,7 @@ EXPORTS = ["gsm_default_options", "gsm_plan", "gsm_apply", "gsm_apply_pass", "gs
 class Options(ctypes.Structure):
     _fields_ = [("delta", ctypes.c_double), ("S", ctypes.c_int), ("precision", ctypes.c_int),
                 ("dip_n", ctypes.c_double * 3), ("dip_m", ctypes.c_double * 3), ("debug", ctypes.c_int),
-                ("box", ctypes.c_double * 3)]
+                ("box", ctypes.c_double * 3), ("beta", ctypes.c_double)]
 
 
 class PlanInfo(ctypes.Structure):
@@ -35,7 +36,7 @@ class PlanInfo(ctypes.Structure):
                 ("precision", ctypes.c_int), ("bytes_multiplier", ctypes.c_size_t),
                 ("bytes_workspace", ctypes.c_size_t), ("npasses", ctypes.c_int),
                 ("launch_nl", ctypes.c_int * 5), ("launch_threads", ctypes.c_int * 5),
-                ("launch_emax", ctypes.c_int * 5), ("box", ctypes.c_double * 3)]
+                ("launch_emax", ctypes.c_int * 5), ("box", ctypes.c_double * 3), ("beta", ctypes.c_double)]
 
 
 class GSMError(RuntimeError):

@@ -73,6 +73,7 @@ void gsm_default_options(gsm_options_t *opt)
     opt->dip_n[2] = 1.0;
     opt->dip_m[2] = 1.0;
     opt->debug = 0;
+    opt->beta = 1.0;
 }
 
 const char *gsm_status_string(gsm_status_t s)
@@ -100,11 +101,11 @@ static gsm_status_t create_plan(gsm_plan_t *out, gsm_kernel_t kind, int d, doubl
         return GSM_ERR_INVALID_ARG;
     }
     *out = nullptr;
-    if (kind < GSM_COULOMB_3D || kind > GSM_DAVEY_STEWARTSON_2D) {
+    if (kind < GSM_COULOMB_3D || kind > GSM_POWER_2D) {
         set_error("unknown kernel");
         return GSM_ERR_INVALID_ARG;
     }
-    const int want_d = (kind == GSM_COULOMB_3D || kind == GSM_DIPOLAR_3D) ? 3 : 2;
+    const int want_d = (kind == GSM_COULOMB_3D || kind == GSM_DIPOLAR_3D || kind == GSM_POWER_3D) ? 3 : 2;
     if (d != want_d) {
         set_error("dimension does not match the kernel");
         return GSM_ERR_INVALID_ARG;
@@ -146,6 +147,10 @@ static gsm_status_t create_plan(gsm_plan_t *out, gsm_kernel_t kind, int d, doubl
             set_error("options.delta must be smaller than every box half-width / the largest (Sec. 2.5)");
             return GSM_ERR_INVALID_ARG;
         }
+    if ((kind == GSM_POWER_3D || kind == GSM_POWER_2D) && !(o.beta > 0.0 && o.beta < d)) {
+        set_error("options.beta must lie in (0, d) for the power kernels");
+        return GSM_ERR_INVALID_ARG;
+    }
     if (o.precision < GSM_FP64 || o.precision > GSM_FP32X2) {
         set_error("unknown precision");
         return GSM_ERR_INVALID_ARG;
@@ -214,13 +219,13 @@ gsm_status_t gsm_plan(gsm_plan_t *out, gsm_kernel_t kind, int d, double L, const
 // Gaussian sum (w, tau), the FP64 octant kernel tensor, then a 64-bit FNV-1a
 // checksum of everything before it.
 static const uint64_t kSaveMagic = 0x47534d5341564531ull;   // "GSMSAVE1"
-static const uint32_t kSaveVersion = 1;
+static const uint32_t kSaveVersion = 2;
 
 struct SaveHeader {
     uint64_t magic;
     uint32_t version, header_bytes;
     int32_t kind, d, n[3], precision, S, nterms, npasses, nl[5], emax[5], pad_;
-    double L, eta[3], eps, delta, dip_n[3], dip_m[3], gs_err, c0, c2;
+    double L, eta[3], eps, delta, dip_n[3], dip_m[3], gs_err, c0, c2, beta;
     uint64_t mult_elems;
 };
 
@@ -283,6 +288,7 @@ gsm_status_t gsm_plan_save(gsm_plan_t h, void *buf, size_t capacity, size_t *byt
     hd.gs_err = p->gs_err;
     hd.c0 = p->c0;
     hd.c2 = p->c2;
+    hd.beta = p->opt.beta;
     hd.mult_elems = p->mult_elems;
     unsigned char *b = static_cast<unsigned char *>(buf);
     memcpy(b, &hd, sizeof(hd));
@@ -353,6 +359,7 @@ gsm_status_t gsm_plan_load(gsm_plan_t *out, const void *buf, size_t bytes, int p
     gsm_options_t o;
     gsm_default_options(&o);
     o.delta = hd.delta;
+    o.beta = hd.beta;
     o.S = hd.S;
     o.precision = (gsm_precision_t)(precision >= 0 ? precision : hd.precision);
     for (int a = 0; a < 3; ++a) {
@@ -663,6 +670,7 @@ gsm_status_t gsm_plan_info(gsm_plan_t h, gsm_plan_info_t *info)
     }
     info->L = p->L;
     for (int a = 0; a < p->d; ++a) info->box[a] = p->L * p->eta[a];
+    info->beta = p->opt.beta;
     info->delta = p->opt.delta;
     info->S = p->S;
     info->nterms = p->nterms;

@@ -1,8 +1,9 @@
 // gsm_plan.cu -- Algorithm 1, "Precomputation", on the GPU in FP64.
 //
-//   1. Gaussian sum U_GS(r) = sum_q w_q exp(-tau_q^2 r^2) of 1/r (Sec. 3.2) or
-//      ln r (Sec. 3.3) by truncated sinc quadrature (Sec. 3.1), S chosen as
-//      the smallest value whose error on [delta, 2 sqrt(d)] meets the target.
+//   1. Gaussian sum U_GS(r) = sum_q w_q exp(-tau_q^2 r^2) of 1/r (Sec. 3.2),
+//      ln r (Sec. 3.3) or r^-beta (remark after Eq. sinc_quad) by truncated
+//      sinc quadrature (Sec. 3.1), S chosen as the smallest value whose error
+//      on [delta, 2 |eta|] meets the target.
 //   2. One-dimensional factors g_q(k) of Eq. tensor.
 //   3. Near-field coefficients c0, c2 of Sec. 2.3.
 //   4. The tensor sum_q w_q g_q(kx) g_q(ky) g_q(kz) on the octant, and the
@@ -11,6 +12,7 @@
 #include <math.h>
 
 #include <algorithm>
+#include <cmath>
 #include <vector>
 
 #include "gsm_internal.h"
@@ -27,10 +29,23 @@ constexpr int kTaylorJ = 44;     // terms of the small-tau series of g
 constexpr double kTauSeries = 1.0;   // g by series below, by w(z) above
 constexpr double kTauGauss = 4.0;    // g by the Gaussian transform at and above
 
-__device__ __forceinline__ bool is_log_kernel(int kind)
+__host__ __device__ __forceinline__ bool is_log_kernel(int kind)
 {
     return kind == GSM_POISSON_2D || kind == GSM_DAVEY_STEWARTSON_2D;
 }
+__host__ __device__ __forceinline__ bool is_power_kernel(int kind)
+{
+    return kind == GSM_POWER_3D || kind == GSM_POWER_2D;
+}
+
+// What the Gaussian-sum kernels need to know about the sum being built.
+struct GsSpec {
+    int kind;                   // kernel whose sum is built
+    double delta, rmax;         // interval [delta, rmax] of the error
+    double beta;                // power kernels: exponent,
+    double s_lo, s_hi;          //   node range in s,
+    double cgam;                //   2 / Gamma(beta / 2)
+};
 
 // ---------------------------------------------------------------- Sec. 3: GS terms
 // Coulomb (Sec. 3.2): 1/r = (1/sqrt(pi)) int_R exp(-r^2 sinh^2 t) cosh t dt,
@@ -71,11 +86,34 @@ __device__ void log_node(int k, int S, double &t, double &tp_over_t)
     }
 }
 
+// r^-beta (remark after Eq. sinc_quad): Eq. Gauss_int with alpha = beta - 1,
+// r^-beta = (2/Gamma(beta/2)) int_0^inf tau^(beta-1) exp(-r^2 tau^2) dtau, and
+// with tau = exp(s - e^-s) (double-exponential decay at both ends of the s
+// axis) the integrand in s is (2/Gamma(beta/2)) tau^beta (1 + e^-s) exp(-r^2 tau^2).
+// S+1 sinc nodes with step (s_hi - s_lo)/S.
+__device__ void power_term(int q, int S, const GsSpec &g, double &w, double &tau)
+{
+    const double h = (g.s_hi - g.s_lo) / (double)S;
+    const double s = g.s_lo + q * h;
+    const double em = exp(-s);
+    const double ln_tau = s - em;
+    tau = exp(ln_tau);
+    w = g.cgam * h * (1.0 + em) * exp(g.beta * ln_tau);
+}
+
 // Block-cooperative construction of all terms into w[], tau[] (shared or
 // global).  Returns nt.  Uses red[] (blockDim.x doubles of shared memory) for
 // the constant C0 of the log kernel.
-__device__ int build_terms(int kind, int S, double delta, double *w, double *tau, double *red)
+__device__ int build_terms(const GsSpec &gs, int S, double *w, double *tau, double *red)
 {
+    const int kind = gs.kind;
+    const double delta = gs.delta;
+    if (is_power_kernel(kind)) {
+        const int nt = S + 1;
+        for (int q = threadIdx.x; q < nt; q += blockDim.x) power_term(q, S, gs, w[q], tau[q]);
+        __syncthreads();
+        return nt;
+    }
     if (!is_log_kernel(kind)) {
         const int nt = S + 1;
         for (int q = threadIdx.x; q < nt; q += blockDim.x) coulomb_term(q, S, w[q], tau[q]);
@@ -108,11 +146,13 @@ __device__ int build_terms(int kind, int S, double delta, double *w, double *tau
 }
 
 // One block per candidate S: maximum error over the sample.
-__global__ void k_gs_scan(int kind, int S0, double delta, double rmax, double *err_out)
+__global__ void k_gs_scan(GsSpec gs, int S0, double *err_out)
 {
     __shared__ double w[kGsCap], tau[kGsCap], red[1024];
     const int S = S0 + blockIdx.x;
-    const int nt = build_terms(kind, S, delta, w, tau, red);
+    const int nt = build_terms(gs, S, w, tau, red);
+    const int kind = gs.kind;
+    const double delta = gs.delta, rmax = gs.rmax;
     double emax = 0.0;
     for (int i = threadIdx.x; i < kNSample + 2; i += blockDim.x) {
         double r;
@@ -124,7 +164,10 @@ __global__ void k_gs_scan(int kind, int S0, double delta, double rmax, double *e
             const double a = tau[q] * r;
             g += w[q] * exp(-a * a);
         }
-        const double e = is_log_kernel(kind) ? fabs(log(r) - g) : fabs(1.0 - r * g);
+        double e;
+        if (is_log_kernel(kind)) e = fabs(log(r) - g);
+        else if (is_power_kernel(kind)) e = fabs(1.0 - pow(r, gs.beta) * g);
+        else e = fabs(1.0 - r * g);
         emax = fmax(emax, e);
     }
     __syncthreads();
@@ -137,10 +180,40 @@ __global__ void k_gs_scan(int kind, int S0, double delta, double rmax, double *e
     if (threadIdx.x == 0) err_out[blockIdx.x] = red[0];
 }
 
-__global__ void k_gs_terms(int kind, int S, double delta, double *w, double *tau)
+__global__ void k_gs_terms(GsSpec gs, int S, double *w, double *tau)
 {
     __shared__ double red[1024];
-    build_terms(kind, S, delta, w, tau, red);
+    build_terms(gs, S, w, tau, red);
+}
+
+// Node range of the r^-beta sum.  Left end: the part of the integral below
+// tau_lo is at most (2/Gamma(beta/2)) tau_lo^beta / beta; it is set to eps/4
+// times rmax^-beta, the smallest kernel value.  Right end: relative to r^-beta
+// the part above tau_hi is the regularised upper incomplete gamma
+// Q(beta/2, r^2 tau_hi^2), largest at r = delta; delta^2 tau_hi^2 = ln(1/eps) + 10
+// puts it below eps/4 for beta < 3.  Each end is the root of
+// f(s) = s - e^-s - ln tau, found by Newton steps from a point where f < 0:
+// f is increasing and concave, so the steps climb to the root.
+double s_of_ln_tau(double y)
+{
+    double s = (y < -1.0) ? -log(-y) : y - 1.0;
+    for (int i = 0; i < 200; ++i) {
+        const double em = exp(-s);
+        const double step = (s - em - y) / (1.0 + em);
+        s -= step;
+        if (!(fabs(step) > 1e-15 * (1.0 + fabs(s)))) break;
+    }
+    return s;
+}
+
+void power_node_range(double beta, double delta, double rmax, double eps, double *s_lo, double *s_hi,
+                      double *cgam)
+{
+    *cgam = 2.0 / std::tgamma(0.5 * beta);
+    const double ln_tau_lo = (log(0.25 * eps * beta / *cgam) - beta * log(rmax)) / beta;
+    const double ln_tau_hi = 0.5 * log(log(1.0 / eps) + 10.0) - log(delta);
+    *s_lo = s_of_ln_tau(ln_tau_lo);
+    *s_hi = s_of_ln_tau(ln_tau_hi);
 }
 
 // ---------------------------------------------------------------- Faddeeva w(z)
@@ -283,8 +356,8 @@ __device__ double gauss_moment(int m, double tau, double delta)
 }
 
 // c0 = |S^{d-1}| A_{d-1}, c2 = |S^{d-1}|/(2d) A_{d+1},
-// A_m = int_0^delta r^m (U1(r) - U_GS(r)) dr, U1 = 1/r or ln r.
-__global__ void k_taylor(int kind, int d, int nt, const double *w, const double *tau, double delta,
+// A_m = int_0^delta r^m (U1(r) - U_GS(r)) dr, U1 = 1/r, ln r or r^-beta.
+__global__ void k_taylor(int kind, double beta, int d, int nt, const double *w, const double *tau, double delta,
                          double *out)
 {
     __shared__ double r0[256], r1[256];
@@ -311,6 +384,9 @@ __global__ void k_taylor(int kind, int d, int nt, const double *w, const double 
             const double ld = log(delta);
             e0 = pow(delta, m0 + 1) * (ld / (m0 + 1) - 1.0 / ((m0 + 1.0) * (m0 + 1.0)));
             e1 = pow(delta, m1 + 1) * (ld / (m1 + 1) - 1.0 / ((m1 + 1.0) * (m1 + 1.0)));
+        } else if (is_power_kernel(kind)) {
+            e0 = pow(delta, m0 + 1 - beta) / (m0 + 1 - beta);   // beta < d = m0 + 1
+            e1 = pow(delta, m1 + 1 - beta) / (m1 + 1 - beta);
         } else {
             e0 = pow(delta, m0) / m0;
             e1 = pow(delta, m1) / m1;
@@ -453,6 +529,14 @@ gsm_status_t build_plan_data(Plan *p, cudaStream_t st, const StoredPlanData *sto
 
     GSM_CUDA_TRY(cudaMalloc(&p->d_w, sizeof(double) * kGsCap));
     GSM_CUDA_TRY(cudaMalloc(&p->d_tau, sizeof(double) * kGsCap));
+    GsSpec gs;
+    gs.kind = kind_gs;
+    gs.delta = delta;
+    gs.rmax = rmax;
+    gs.beta = p->opt.beta;
+    gs.s_lo = gs.s_hi = 0.0;
+    gs.cgam = 0.0;
+    if (is_power_kernel(kind_gs)) power_node_range(gs.beta, delta, rmax, p->eps, &gs.s_lo, &gs.s_hi, &gs.cgam);
 
     // 1. choose S (smallest meeting eps), scanning a first window then the rest
     int S = stored ? stored->S : p->opt.S;
@@ -481,7 +565,7 @@ gsm_status_t build_plan_data(Plan *p, cudaStream_t st, const StoredPlanData *sto
                 if (S < a || S > b) continue;
                 a = b = S;
             }
-            k_gs_scan<<<b - a + 1, 256, 0, st>>>(kind_gs, a, delta, rmax, d_err + (a - S_first));
+            k_gs_scan<<<b - a + 1, 256, 0, st>>>(gs, a, d_err + (a - S_first));
             cudaError_t e = cudaMemcpyAsync(h.data() + (a - S_first), d_err + (a - S_first),
                                             sizeof(double) * (b - a + 1), cudaMemcpyDeviceToHost, st);
             if (e == cudaSuccess) e = cudaStreamSynchronize(st);
@@ -512,7 +596,7 @@ gsm_status_t build_plan_data(Plan *p, cudaStream_t st, const StoredPlanData *sto
         GSM_CUDA_TRY(cudaMemcpyAsync(p->d_w, stored->w, sizeof(double) * p->nterms, cudaMemcpyHostToDevice, st));
         GSM_CUDA_TRY(cudaMemcpyAsync(p->d_tau, stored->tau, sizeof(double) * p->nterms, cudaMemcpyHostToDevice, st));
     } else {
-        k_gs_terms<<<1, 1024, 0, st>>>(kind_gs, S, delta, p->d_w, p->d_tau);
+        k_gs_terms<<<1, 1024, 0, st>>>(gs, S, p->d_w, p->d_tau);
     }
 
     // 2. 1-D factors per axis
@@ -543,7 +627,7 @@ gsm_status_t build_plan_data(Plan *p, cudaStream_t st, const StoredPlanData *sto
     } else {
         double *d_c = nullptr;
         GSM_CUDA_TRY(cudaMalloc(&d_c, sizeof(double) * 2));
-        k_taylor<<<1, 256, 0, st>>>(kind_gs, d, p->nterms, p->d_w, p->d_tau, delta, d_c);
+        k_taylor<<<1, 256, 0, st>>>(kind_gs, p->opt.beta, d, p->nterms, p->d_w, p->d_tau, delta, d_c);
         double hc[2];
         GSM_CUDA_TRY(cudaMemcpyAsync(hc, d_c, sizeof(hc), cudaMemcpyDeviceToHost, st));
         GSM_CUDA_TRY(cudaStreamSynchronize(st));
@@ -578,6 +662,7 @@ gsm_status_t build_plan_data(Plan *p, cudaStream_t st, const StoredPlanData *sto
     const double L = p->L;
     if (p->kind == GSM_COULOMB_3D || p->kind == GSM_DIPOLAR_3D) mp.scale = L * L / (4.0 * kPi);
     else if (p->kind == GSM_COULOMB_2D) mp.scale = L / (2.0 * kPi);
+    else if (is_power_kernel(p->kind)) mp.scale = pow(L, d - p->opt.beta);   // |L x|^-beta L^d
     else mp.scale = -L * L / (2.0 * kPi);   // ln kernel: Poisson and Davey-Stewartson
     mp.c0 = p->c0;
     mp.c2 = p->c2;

@@ -60,27 +60,30 @@ def test_fft_engine_matches_oracle_fft(gsm, M, precision):
 
 # ------------------------------------------------------------------ plan data
 def test_plan_gaussian_sum_meets_accuracy(gsm):
-    for kernel, d in (("coulomb3d", 3), ("poisson2d", 2), ("coulomb2d", 2)):
+    for kernel, d, beta in (("coulomb3d", 3, 1.0), ("poisson2d", 2, 1.0), ("coulomb2d", 2, 1.0),
+                            ("power3d", 3, 0.4), ("power3d", 3, 2.7), ("power2d", 2, 1.2)):
         n = 16
-        plan = gsm.Plan(kernel, 4.0, (n,) * d)
+        plan = gsm.Plan(kernel, 4.0, (n,) * d, beta=beta)
         w, tau = plan.gs_terms()
         delta, rmax = 1e-3, 2 * np.sqrt(d)
         r = delta * (rmax / delta) ** np.linspace(0, 1, 7919)
         g = np.sum(w[None, :] * np.exp(-(tau[None, :] * r[:, None]) ** 2), axis=1)
         if kernel == "poisson2d":
             assert np.max(np.abs(np.log(r) - g)) < 1.5e-13
+        elif kernel.startswith("power"):
+            assert np.max(np.abs(1 - r ** beta * g)) < 3e-15, (kernel, beta)
         else:
             assert np.max(np.abs(1 - r * g)) < 2e-15
 
 
-@pytest.mark.parametrize("kernel", ["coulomb3d", "poisson2d"])
-def test_plan_factors_and_tensor_match_oracle(gsm, kernel):
-    d = 3 if kernel == "coulomb3d" else 2
+@pytest.mark.parametrize("kernel,beta", [("coulomb3d", 1.0), ("poisson2d", 1.0), ("power3d", 1.7), ("power2d", 0.5)])
+def test_plan_factors_and_tensor_match_oracle(gsm, kernel, beta):
+    d = oracle.KERNEL_DIM[kernel]
     n = 24 if d == 3 else 96
-    plan = gsm.Plan(kernel, 5.0, (n,) * d)
+    plan = gsm.Plan(kernel, 5.0, (n,) * d, beta=beta)
     info = plan.info()
     # same S on both sides so that the Gaussian sums are the same terms
-    w_o, tau_o, S_o, _ = oracle.gs(kernel, S=info["S"])
+    w_o, tau_o, S_o, _ = oracle.gs(kernel, S=info["S"], beta=beta)
     w_g, tau_g = plan.gs_terms()
     assert len(w_g) == len(w_o)
     assert np.max(np.abs(w_g - w_o) / np.abs(w_o)) < 1e-13
@@ -91,7 +94,7 @@ def test_plan_factors_and_tensor_match_oracle(gsm, kernel):
     # integrand; its rounding reaches ~1e-14 (factors are at most 4)
     assert np.max(np.abs(g - ref)) < 2e-14
     kh = plan.kernel_tensor()
-    kho, _ = oracle.kernel_hat(kernel, n, 5.0, S=info["S"])
+    kho, _ = oracle.kernel_hat(kernel, n, 5.0, S=info["S"], beta=beta)
     kho = kho.transpose(*range(d)[::-1])       # oracle is [kz][ky][kx]; plan is [kx][ky][kz]
     # rounding of sum_q w_q prod g_q is relative to sum_q |w_q| prod |g_q|, which
     # for ln r (terms of both signs, constant C0 ~ S/4) is ~100x the result
@@ -100,7 +103,7 @@ def test_plan_factors_and_tensor_match_oracle(gsm, kernel):
     dg = np.max(np.abs(g - ref), axis=1)
     prop = d * np.sum(np.abs(w_o) * dg * np.max(np.abs(ref), axis=1) ** (d - 1))
     assert np.max(np.abs(kh - kho)) < 4e-16 * scale + prop
-    c0, c2 = oracle.taylor_coeffs(kernel, w_o, tau_o, 1e-3)
+    c0, c2 = oracle.taylor_coeffs(kernel, w_o, tau_o, 1e-3, beta=beta)
     # c = |S^{d-1}| (int_0^delta r^m U1 - sum_q w_q mu_m(tau_q)) cancels heavily
     # (for ln r, sum |w_q mu_q| is ~2e4 |c0/2pi|): both sides round at the level
     # eps * sum_q |w_q mu_q|, so that is the scale of the tolerance
@@ -456,6 +459,7 @@ SAVE_CASES = [
     ("coulomb2d", (40, 30), dict(L=1.0, box=(5.0, 3.0))),
     ("poisson2d", (48, 32), dict(L=7.0)),
     ("ds2d", (32, 40), dict(L=1.0, box=(4.0, 6.5))),
+    ("power3d", (16, 20, 24), dict(L=5.0, beta=2.2)),
 ]
 
 
@@ -494,3 +498,37 @@ def test_saved_plan_is_bit_identical(gsm, kernel, n, kw, tmp_path):
     bad[300] ^= 1
     with pytest.raises(gsm.GSMError, match="checksum"):
         gsm.Plan.load(bytes(bad))
+
+
+# ------------------------------------------------------------------ power kernels |x|^-beta
+POWER_CASES = [
+    ("power3d", 1.7, "mixture 48^3", lambda: wl.coulomb3d_mixture(48, 12.0), 12.0, None),
+    ("power3d", 0.6, "random 12x20x16", lambda: np.random.default_rng(41).standard_normal((16, 20, 12)), 3.0, None),
+    ("power3d", 2.6, "random box", lambda: np.random.default_rng(42).standard_normal((12, 16, 20)), 1.0,
+     (3.0, 2.0, 1.5)),
+    ("power2d", 1.3, "mixture 128^2", lambda: wl.mixture2d(128, 16.0), 16.0, None),
+    ("power2d", 0.4, "random box", lambda: np.random.default_rng(43).standard_normal((40, 30)), 1.0, (4.0, 1.5)),
+]
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32x2", "fp32"])
+@pytest.mark.parametrize("kernel,beta,name,make,L,box", POWER_CASES, ids=[f"{c[0]}-b{c[1]}-{c[2]}" for c in POWER_CASES])
+def test_power_parity(gsm, kernel, beta, name, make, L, box, precision):
+    rho = make()
+    kw = dict(beta=beta) if box is None else dict(beta=beta, box=box)
+    u, plan = run(gsm, kernel, rho, L, precision, **kw)
+    uo, _ = oracle.apply(kernel, rho, L, taylor_mode=1, S=plan.info()["S"], **kw)
+    assert relmax(u, uo) < TOL[precision], relmax(u, uo)
+
+
+def test_power_closed_form(gsm):
+    """|x|^-2.5 on [-8,8]^3 at h = 1/4 and |x|^-1.5 on [-8,8]^2 at h = 1/8
+    against the 1F1 closed form of a Gaussian density."""
+    import sys, os
+    sys.path.insert(0, os.path.dirname(__file__))
+    from closed_forms import power_gaussian
+    for kernel, d, beta, n, tol in (("power3d", 3, 2.5, 64, 1e-14), ("power2d", 2, 1.5, 128, 5e-15)):
+        C = wl.mesh((n,) * d, 8.0)
+        r = np.sqrt(sum(c * c for c in C))
+        u, _ = run(gsm, kernel, np.exp(-r * r / 1.44), 8.0, beta=beta)
+        assert relmax(u, power_gaussian(r, 1.2, beta, d)) < tol, kernel
