@@ -191,6 +191,26 @@ def relmax(a, b):
     return float(np.max(np.abs(a - b)) / np.max(np.abs(b)))
 
 
+# ------------------------------------------------------------------ multi-rank host logic
+def max_over_ranks(x: float, device) -> float:
+    """Maximum of a per-rank float over all ranks of the default process group
+    (the value itself when there is no group): every rank gets the same result."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(points_per_rank: int, world: int, total_ms_max: float, steps: int):
+    """(ms per step, whole-job Mpts/s): every rank applies its own replica, so the
+    job processes world * points_per_rank points per step in the slowest rank's time."""
+    ms_per_step = total_ms_max / steps
+    return ms_per_step, world * points_per_rank / (ms_per_step / 1e3) / 1e6
+
+
 # ------------------------------------------------------------------ reference arm
 def run_reference(a, rank, world):
     """The CPU oracle, as it stands, on the host cores: each step is one apply
@@ -273,13 +293,8 @@ def main():
         barrier()
         t_wall = time.perf_counter() - t_wall0
     clocks = clk.summary()
-    total_ms = float(sum(step_ms))
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    ms_per_step = total_ms / a.steps
-    value = world * n ** 3 / (ms_per_step / 1e3) / 1e6
+    total_ms = max_over_ranks(float(sum(step_ms)), dev)
+    ms_per_step, value = job_throughput(n ** 3, world, total_ms, a.steps)
 
     # dominant kernel and its roofline
     avg_pass = [float(np.mean(x)) for x in pass_ms]
