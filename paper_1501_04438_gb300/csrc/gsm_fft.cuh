@@ -341,6 +341,154 @@ __device__ __forceinline__ void fft_stage(typename Pol::scplx *s, int M, int Ns,
     group_sync(g);
 }
 
+// ---------------------------------------------------------------- FMA-form radix 8 (FP64)
+// Doubles of the FMA-form constants for a schedule: 16 per index j of every
+// radix-8 stage after the first (Ns = 8, 64, ...).
+inline size_t g8_table_doubles(const Sched &sc)
+{
+    size_t tot = 0, Ns = 1;
+    for (int st = 0; st < sc.nst && sc.r[st] == 8; ++st, Ns *= 8)
+        if (Ns > 1) tot += Ns * 16;
+    return tot;
+}
+
+// A twiddled radix-8 stage in which every multiplication is fused into an
+// addition: the "tangent" form of the twiddle factors (E. N. Linzer and
+// E. Feig, IEEE Trans. Signal Process. 41 (1993); S. Goedecker, SIAM J. Sci.
+// Comput. 18 (1997)).  Each twiddle W_t = w^(jt) is written
+//   W_t = f_t i^(k_t) (1 + i tau_t),  |tau_t| <= 1,  f_t = cos(phi_t) >= 1/sqrt2,
+// with i^(k_t) the nearest quarter turn.  X_t = i^(k_t)(1 + i tau_t) x_t costs
+// two FMAs (the quarter turn is a swap and sign flips, done on the integer
+// side); the real scales f_t are carried as ratios through the three layers of
+// the radix-8 butterfly (t vs t+4, then the two radix-4 layers), each layer a
+// pair of FMAs per complex value, and cancel at the end because f_0 = 1.
+// 66 FP64 instructions per butterfly instead of 80 (14 complex multiplications'
+// worth of DMUL/DFMA, then the additions).  The constants of stage Ns, index j,
+// are 16 doubles (one 128-byte line) at gt[16 j]:
+//   0..6  tau_t sigma_t (t = 1..7; sigma_t = -1 for odd k_t, which folds the
+//         swap's sign into the tangent)
+//   7..10 r_t = f_(t+4) / f_t (t = 0..3)
+//   11 f_2, 12 f_3 / f_1, 13 f_1, 14 f_1 / sqrt2
+//   15    k_t mod 4 in bits 2(t-1), 2(t-1)+1 (an integer in the double's bits)
+// for the forward direction; the inverse uses conj(W_t) = f_t i^(-k_t)(1 - i tau_t).
+constexpr int kG8Slots = 16;
+
+__device__ __forceinline__ double flip_sign(double x, unsigned neg)
+{
+    return __hiloint2double(__double2hiint(x) ^ (int)(neg << 31), __double2loint(x));
+}
+
+// i^k (1 + i tt) x with tt the signed tangent of the stored convention.
+__device__ __forceinline__ cx<double> tangent_rot(cx<double> x, int k, double tt)
+{
+    const bool sw = k & 1;
+    const double a = sw ? x.im : x.re, b = sw ? x.re : x.im;
+    const double re = fma(-tt, b, a), im = fma(tt, a, b);
+    return {flip_sign(re, (unsigned)((k ^ (k >> 1)) & 1)), flip_sign(im, (unsigned)((k >> 1) & 1))};
+}
+
+// In-place DFT4 of z_0..z_3 carried as z_t = h_t zh_t with h_0 = 1 (ratios
+// q2 = h_2, q31 = h_3 / h_1, q1 = h_1): z_n <- Z_n; with HALFOUT only Z_0, Z_1.
+template <bool FWD, bool HALFOUT>
+__device__ __forceinline__ void dft4_scaled(cx<double> &z0, cx<double> &z1, cx<double> &z2, cx<double> &z3,
+                                            double q2, double q31, double q1)
+{
+    const cx<double> P = {fma(q2, z2.re, z0.re), fma(q2, z2.im, z0.im)};
+    const cx<double> Q = {fma(-q2, z2.re, z0.re), fma(-q2, z2.im, z0.im)};
+    const cx<double> R = {fma(q31, z3.re, z1.re), fma(q31, z3.im, z1.im)};
+    const cx<double> S = {fma(-q31, z3.re, z1.re), fma(-q31, z3.im, z1.im)};
+    // Z_1 = Q -+ i S (forward: -i), Z_3 = Q +- i S
+    const cx<double> iS = FWD ? cx<double>{S.im, -S.re} : cx<double>{-S.im, S.re};
+    z0 = {fma(q1, R.re, P.re), fma(q1, R.im, P.im)};
+    z1 = {fma(q1, iS.re, Q.re), fma(q1, iS.im, Q.im)};
+    if (!HALFOUT) {
+        z2 = {fma(-q1, R.re, P.re), fma(-q1, R.im, P.im)};
+        z3 = {fma(-q1, iS.re, Q.re), fma(-q1, iS.im, Q.im)};
+    }
+}
+
+// One twiddled radix-8 butterfly in FMA form, in place: v[0..7] in,
+// Y_0..Y_(NOUT-1) out.  Constants are read where they are used.
+template <bool FWD, int NOUT>
+__device__ __forceinline__ void bfly8_fma(cx<double> *v, const double *__restrict__ c)
+{
+    const int codes = __double2loint(__ldg(c + 15));
+#pragma unroll
+    for (int t = 1; t < 8; ++t) {
+        int k = (codes >> (2 * (t - 1))) & 3;
+        if (!FWD) k = (4 - k) & 3;
+        const double tt = __ldg(c + t - 1);
+        v[t] = tangent_rot(v[t], k, FWD ? tt : -tt);
+    }
+    // layer 1: v_t <- E_t = X_t + r_t X_(t+4) (scale f_t), v_(t+4) <- O_t = X_t - r_t X_(t+4)
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+        const double r = __ldg(c + 7 + t);
+        const cx<double> x = v[t], y = v[t + 4];
+        v[t] = {fma(r, y.re, x.re), fma(r, y.im, x.im)};
+        v[t + 4] = {fma(-r, y.re, x.re), fma(-r, y.im, x.im)};
+    }
+    // odd branch: O_t w8^t; the 1/sqrt2 of w8, w8^3 joins the scale of O_1, O_3
+    {
+        const cx<double> a = v[5], d = v[6], b = v[7];
+        if (FWD) {
+            v[5] = {a.re + a.im, a.im - a.re};        // (1 - i) a
+            v[6] = {d.im, -d.re};                     // -i d
+            v[7] = {b.im - b.re, -b.im - b.re};       // (-1 - i) b
+        } else {
+            v[5] = {a.re - a.im, a.im + a.re};        // (1 + i) a
+            v[6] = {-d.im, d.re};                     // i d
+            v[7] = {-b.re - b.im, b.re - b.im};       // (-1 + i) b
+        }
+    }
+    const double f2 = __ldg(c + 11), f31 = __ldg(c + 12);
+    dft4_scaled<FWD, NOUT == 4>(v[0], v[1], v[2], v[3], f2, f31, __ldg(c + 13));   // Y_0, Y_2, Y_4, Y_6
+    dft4_scaled<FWD, NOUT == 4>(v[4], v[5], v[6], v[7], f2, f31, __ldg(c + 14));   // Y_1, Y_3, Y_5, Y_7
+    // interleave (register renaming only)
+    const cx<double> e1 = v[1], e2 = v[2], e3 = v[3], o0 = v[4], o1 = v[5], o2 = v[6];
+    v[1] = o0;
+    v[2] = e1;
+    v[3] = o1;
+    if (NOUT == 8) {
+        v[4] = e2;
+        v[5] = o2;
+        v[6] = e3;
+    }
+}
+
+// Twiddled radix-8 Stockham stage (Ns > 1) in FMA form; HALF = 2: only the
+// outputs t < 4 (the crop).  Same data movement as fft_stage.
+template <bool FWD, int NB, int HALF>
+__device__ __forceinline__ void fft_stage8_fma(double2 *s, int M, int Ns, const double *__restrict__ gt,
+                                               const Group &g)
+{
+    constexpr int NOUT = HALF == 2 ? 4 : 8;
+    const int nb = M / 8;
+    cx<double> v[NB][8];
+#pragma unroll
+    for (int i = 0; i < NB; ++i) {
+        const int b = g.t + i * g.T;
+        if (b < nb) {
+#pragma unroll
+            for (int t = 0; t < 8; ++t) v[i][t] = F64::ld(s[pidx<F64>(b + t * nb)]);
+            const int j = b & (Ns - 1);   // Ns is a power of 8
+            bfly8_fma<FWD, NOUT>(v[i], gt + (size_t)j * kG8Slots);
+        }
+    }
+    group_sync(g);
+#pragma unroll
+    for (int i = 0; i < NB; ++i) {
+        const int b = g.t + i * g.T;
+        if (b < nb) {
+            const int j = b & (Ns - 1);
+            const int d0 = (b - j) * 8 + j;
+#pragma unroll
+            for (int t = 0; t < NOUT; ++t) s[pidx<F64>(d0 + t * Ns)] = F64::st(v[i][t]);
+        }
+    }
+    group_sync(g);
+}
+
 // All stages of the FFT of one line by one group.  EMAX bounds the elements
 // per thread (M <= EMAX * T).  The caller synchronises the group (or CTA)
 // after writing the line; the last stage ends with a group barrier, so the
@@ -352,9 +500,13 @@ __device__ __forceinline__ void fft_stage(typename Pol::scplx *s, int M, int Ns,
 // output is needed (the last stage is pruned when its radix is even; the
 // second half of the line is then left undefined).  Both apply to policies
 // with kPrune only; for the others the full stages run.
+// gt (FP64 only, may be NULL): the constants of the FMA-form radix-8 stages
+// (fft_stage8_fma), stage Ns = 8^s at gt + 16 (8 + 64 + ... + 8^(s-1)); with
+// NULL every stage takes the twiddle table tw.
 template <class Pol, bool FWD, int EMAX, bool ZPAD_ = false, bool CROP_ = false>
 __device__ __forceinline__ void fft_line(typename Pol::scplx *s, const Sched &sc,
-                                         const typename Pol::tw_t *__restrict__ tw, const Group &g)
+                                         const typename Pol::tw_t *__restrict__ tw, const Group &g,
+                                         const double *__restrict__ gt = nullptr)
 {
     // pruning pays where the arithmetic pipe is the limit: FP64 only
     constexpr bool ZPAD = ZPAD_ && Pol::kPrune, CROP = CROP_ && Pol::kPrune;
@@ -370,6 +522,25 @@ __device__ __forceinline__ void fft_line(typename Pol::scplx *s, const Sched &sc
         else                                                                                   \
             fft_stage<Pol, RAD, FWD, NB, 0>(s, M, Ns, tw, g);                                  \
     } while (0)
+    if constexpr (std::is_same<Pol, F64>::value) {
+        // radix-8 stages come first in the schedule: Ns = 1, 8, 64, ...  The
+        // first (no twiddles) is peeled off so that the loop holds only the
+        // FMA-form stage (a loop mixing several large stage bodies costs the
+        // register allocator dearly).
+        if (gt != nullptr && sc.nst > 0 && sc.r[0] == 8) {
+            constexpr int NB8 = (EMAX + 7) / 8;
+            if (ZPAD) fft_stage<Pol, 8, FWD, NB8, 1>(s, M, 1, tw, g);
+            else fft_stage<Pol, 8, FWD, NB8, 0>(s, M, 1, tw, g);
+            st = 1;
+            Ns = 8;
+            size_t goff = 0;
+            for (; st < sc.nst && sc.r[st] == 8; ++st, Ns *= 8) {
+                if (CROP && st == last) fft_stage8_fma<FWD, NB8, 2>(s, M, Ns, gt + goff, g);
+                else fft_stage8_fma<FWD, NB8, 0>(s, M, Ns, gt + goff, g);
+                goff += (size_t)Ns * kG8Slots;
+            }
+        }
+    }
     for (; st < sc.nst && sc.r[st] == 8; ++st, Ns *= 8) GSM_STAGE(8);
     for (; st < sc.nst && sc.r[st] == 4; ++st, Ns *= 4) GSM_STAGE(4);
     for (; st < sc.nst && sc.r[st] == 2; ++st, Ns *= 2) GSM_STAGE(2);

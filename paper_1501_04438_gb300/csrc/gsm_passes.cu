@@ -37,6 +37,15 @@ constexpr int kMaxThreads = 512;   // CTA size cap: leaves 128 registers per thr
 template <class Pol>
 using S_t = typename Pol::scplx;
 
+// FP64 twiddle tables hold, after the M twiddles w^m, the constants of the
+// FMA-form radix-8 stages (fft_stage8_fma); the other precisions have none.
+template <class Pol>
+__device__ __forceinline__ const double *g8_table(const typename Pol::tw_t *tw, int M)
+{
+    if constexpr (std::is_same<Pol, F64>::value) return reinterpret_cast<const double *>(tw + M);
+    else return nullptr;
+}
+
 // Launch shape (see PassCfg): a CTA holds nl lines; line l is transformed by
 // group l of gthr threads (blockDim.x = nl * gthr).  Loads and stores that
 // touch one line are done by its group; the transposed side of a pass is
@@ -70,7 +79,7 @@ __device__ __forceinline__ void body_xf(const typename Pol::io_t *__restrict__ r
         s[pidx<Pol>(x)] = Pol::st(cx<R>{a, b});
     }
     group_sync(g);
-    fft_line<Pol, true, EMAX, true, false>(s, sc, tw, g);
+    fft_line<Pol, true, EMAX, true, false>(s, sc, tw, g, g8_table<Pol>(tw, M));
     __syncthreads();
     // Z = A + iB with A, B the transforms of the two real rows:
     // 2A[k] = Z[k] + conj Z[-k], 2B[k] = -i (Z[k] - conj Z[-k]); the factor 2
@@ -119,7 +128,7 @@ __device__ __forceinline__ void body_yf(const S_t<Pol> *__restrict__ W1, S_t<Pol
         s[pidx<Pol>(y)] = v;
     }
     group_sync(g);
-    fft_line<Pol, true, EMAX, true, false>(s, sc, tw, g);
+    fft_line<Pol, true, EMAX, true, false>(s, sc, tw, g, g8_table<Pol>(tw, M));
     __syncthreads();
     const S_t<Pol> *s0 = reinterpret_cast<const S_t<Pol> *>(smem_raw);
     S_t<Pol> *out = W2 + (size_t)kx * M * nz;
@@ -165,7 +174,7 @@ __device__ __forceinline__ void body_conv(S_t<Pol> *__restrict__ W, const typena
         s[pidx<Pol>(z)] = v;
     }
     group_sync(g);
-    fft_line<Pol, true, EMAX, true, false>(s, sc, tw, g);
+    fft_line<Pol, true, EMAX, true, false>(s, sc, tw, g, g8_table<Pol>(tw, M));
     if (full) {
         const typename Pol::mult_t *mrow = mult + (size_t)line * M;
         for (int k = g.t; k < M; k += g.T) {
@@ -188,7 +197,7 @@ __device__ __forceinline__ void body_conv(S_t<Pol> *__restrict__ W, const typena
         }
     }
     group_sync(g);
-    fft_line<Pol, false, EMAX, false, true>(s, sc, tw, g);
+    fft_line<Pol, false, EMAX, false, true>(s, sc, tw, g, g8_table<Pol>(tw, M));
     for (int z = g.t; z < n; z += g.T) w[z] = s[pidx<Pol>(z)];
 }
 
@@ -224,7 +233,7 @@ __device__ __forceinline__ void body_yi(const S_t<Pol> *__restrict__ W2, S_t<Pol
     }
     __syncthreads();
     const int z = z0 + l;
-    fft_line<Pol, false, EMAX, false, true>(s, sc, tw, g);
+    fft_line<Pol, false, EMAX, false, true>(s, sc, tw, g, g8_table<Pol>(tw, M));
     if (z < nz) {
         S_t<Pol> *out = W1 + ((size_t)z * hx + kx) * ny;
         for (int y = g.t; y < ny; y += g.T) out[y] = s[pidx<Pol>(y)];
@@ -272,7 +281,7 @@ __device__ __forceinline__ void body_xi(const S_t<Pol> *__restrict__ W1, typenam
         if (k > 0 && k < nx) s0[ll * LS + pidx<Pol>(M - k)] = Pol::st(cadd(cconj(A), cmul_posi(cconj(B))));
     }
     __syncthreads();
-    fft_line<Pol, false, EMAX, false, true>(s, sc, tw, g);
+    fft_line<Pol, false, EMAX, false, true>(s, sc, tw, g, g8_table<Pol>(tw, M));
     const int ya = y0 + 2 * l;
     typename Pol::io_t *slab = u + (size_t)z * ny * nx;
     for (int x = g.t; x < nx; x += g.T) {
@@ -295,7 +304,7 @@ __global__ void __launch_bounds__(kMaxThreads) k_xi(const S_t<Pol> *__restrict__
 template <class Pol, bool FWD, int EMAX>
 __global__ void __launch_bounds__(kMaxThreads) k_fft_hook(const double2 *__restrict__ in, double2 *__restrict__ out,
                                                           int nlines, Sched sc, int nl, int gthr,
-                                                          const typename Pol::tw_t *__restrict__ tw)
+                                                          const typename Pol::tw_t *__restrict__ tw, int use_g8)
 {
     using R = typename Pol::real;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -310,7 +319,7 @@ __global__ void __launch_bounds__(kMaxThreads) k_fft_hook(const double2 *__restr
         s[pidx<Pol>(k)] = Pol::st(cx<R>{Pol::from_io((typename Pol::io_t)v.x), Pol::from_io((typename Pol::io_t)v.y)});
     }
     group_sync(g);
-    fft_line<Pol, FWD, EMAX>(s, sc, tw, g);
+    fft_line<Pol, FWD, EMAX>(s, sc, tw, g, use_g8 ? g8_table<Pol>(tw, M) : nullptr);
     for (int k = g.t; k < M; k += g.T) {
         const cx<R> c = Pol::ld(s[pidx<Pol>(k)]);
         out[(size_t)line * M + k] = make_double2((double)Pol::to_io(c.re), (double)Pol::to_io(c.im));
@@ -384,6 +393,58 @@ __global__ void __launch_bounds__(32 * kBatchMaxLines) k_batch(const __grid_cons
 }
 
 // ------------------------------------------------------------------ tables
+// Constants of the FMA-form radix-8 stages (layout in gsm_fft.cuh, before
+// fft_stage8_fma) for the radix-8 stages s = 1..n8-1 of a schedule, Ns = 8^s,
+// one thread per (stage, j).  Forward twiddle W_t = exp(-2 pi i j t / (8 Ns)):
+// with q = j t, K = round(q / 2Ns) and m = q - 2 Ns K (|m| <= Ns),
+// W_t = i^(-K) exp(-i pi m / (4 Ns)), so k_t = -K mod 4, f_t = cos(pi m / 4Ns),
+// tau_t = -tan(pi m / 4Ns).
+__global__ void k_g8table(int n8, double *out)
+{
+    long idx = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    long Ns = 8, base = 0;
+    int s = 1;
+    for (; s < n8 && idx >= base + Ns; ++s) {
+        base += Ns;
+        Ns *= 8;
+    }
+    if (s >= n8) return;
+    const long j = idx - base;
+    double f[8], tau[8];
+    int codes = 0;
+    f[0] = 1.0;
+    tau[0] = 0.0;
+    for (int t = 1; t < 8; ++t) {
+        const long q = j * t;
+        const long K = (q + Ns) / (2 * Ns);
+        const long m = q - 2 * Ns * K;
+        const int k = (int)((4 - (K & 3)) & 3);
+        double sn, cs;
+        sincospi((double)m / (double)(4 * Ns), &sn, &cs);
+        f[t] = cs;
+        tau[t] = (k & 1) ? sn / cs : -sn / cs;   // tau sigma_t, sigma_t = -1 for odd k
+        codes |= k << (2 * (t - 1));
+    }
+    double *c = out + (base + j) * 16;
+    for (int t = 1; t < 8; ++t) c[t - 1] = tau[t];
+    for (int t = 0; t < 4; ++t) c[7 + t] = f[t + 4] / f[t];
+    c[11] = f[2];
+    c[12] = f[3] / f[1];
+    c[13] = f[1];
+    c[14] = f[1] * 0.707106781186547524400844362104849039;
+    c[15] = __hiloint2double(0, codes);
+}
+
+// Fills the FMA-form constants of schedule sc at `dst` (just after the M
+// twiddles of an FP64 table, so 16-byte aligned).
+void launch_g8table(const Sched &sc, double2 *dst, cudaStream_t st)
+{
+    int n8 = 0;
+    while (n8 < sc.nst && sc.r[n8] == 8) ++n8;
+    const long entries = (long)(g8_table_doubles(sc) / kG8Slots);
+    if (entries > 0) k_g8table<<<(entries + 127) / 128, 128, 0, st>>>(n8, reinterpret_cast<double *>(dst));
+}
+
 // w[m] = exp(-2 pi i m / M) from sincospi in FP64, then rounded or split.
 __global__ void k_twiddles(int M, int prec, void *out)
 {
@@ -693,7 +754,7 @@ std::string tune_key(const Plan *p, int pass)
     for (char &ch : name)
         if (ch == ' ') ch = '_';
     char buf[256];
-    snprintf(buf, sizeof(buf), "v2 %s p%d d%d n%d,%d,%d pass%d", name.c_str(), (int)p->opt.precision, p->d, p->n[0],
+    snprintf(buf, sizeof(buf), "v3 %s p%d d%d n%d,%d,%d pass%d", name.c_str(), (int)p->opt.precision, p->d, p->n[0],
              p->n[1], p->d == 3 ? p->n[2] : 1, pass);
     return buf;
 }
@@ -812,8 +873,10 @@ gsm_status_t fft_hook_t(int M, int nlines, int sign, const double *in, double *o
         return GSM_ERR_UNSUPPORTED_SIZE;
     }
     void *d_tw = nullptr;
-    GSM_CUDA_TRY(cudaMallocAsync(&d_tw, sizeof(typename Pol::tw_t) * M, st));
+    const size_t g8 = std::is_same<Pol, F64>::value ? g8_table_doubles(sc) : 0;
+    GSM_CUDA_TRY(cudaMallocAsync(&d_tw, sizeof(typename Pol::tw_t) * M + sizeof(double) * g8, st));
     k_twiddles<<<(M + 255) / 256, 256, 0, st>>>(M, Pol::kId, d_tw);
+    if (g8 > 0) launch_g8table(sc, static_cast<double2 *>(d_tw) + M, st);
     const PassCfg c = choose_cfg<Pol>(M, std::max(1, 2048 / M));
     const auto *tw = static_cast<const typename Pol::tw_t *>(d_tw);
     const int blocks = (nlines + c.nl - 1) / c.nl;
@@ -823,12 +886,12 @@ gsm_status_t fft_hook_t(int M, int nlines, int sign, const double *in, double *o
             e = raise_smem(k_fft_hook<Pol, true, E()>, c.smem);
             if (e == cudaSuccess)
                 k_fft_hook<Pol, true, E()><<<blocks, c.nthr, c.smem, st>>>((const double2 *)in, (double2 *)out,
-                                                                           nlines, sc, c.nl, c.gthr, tw);
+                                                                           nlines, sc, c.nl, c.gthr, tw, 1);
         } else {
             e = raise_smem(k_fft_hook<Pol, false, E()>, c.smem);
             if (e == cudaSuccess)
                 k_fft_hook<Pol, false, E()><<<blocks, c.nthr, c.smem, st>>>((const double2 *)in, (double2 *)out,
-                                                                            nlines, sc, c.nl, c.gthr, tw);
+                                                                            nlines, sc, c.nl, c.gthr, tw, 1);
         }
     });
     GSM_CUDA_TRY(e);
@@ -867,8 +930,10 @@ gsm_status_t make_twiddles(Plan *p, int axis, cudaStream_t st)
             return GSM_OK;
         }
     const int M = p->M[axis];
-    GSM_CUDA_TRY(cudaMalloc(&p->d_tw[axis], cplx_bytes(p->opt.precision) * M));
+    const size_t g8 = p->opt.precision == GSM_FP64 ? g8_table_doubles(p->sched[axis]) : 0;
+    GSM_CUDA_TRY(cudaMalloc(&p->d_tw[axis], cplx_bytes(p->opt.precision) * M + sizeof(double) * g8));
     k_twiddles<<<(M + 255) / 256, 256, 0, st>>>(M, p->opt.precision, p->d_tw[axis]);
+    if (g8 > 0) launch_g8table(p->sched[axis], static_cast<double2 *>(p->d_tw[axis]) + M, st);
     GSM_CUDA_TRY(cudaGetLastError());
     return GSM_OK;
 }
@@ -1051,12 +1116,12 @@ gsm_status_t fft_hook_static_t(int M, int nlines, int sign, const double *in, do
             e = raise_smem(k_fft_hook<Pol, true, E()>, c.smem);
             if (e == cudaSuccess)
                 k_fft_hook<Pol, true, E()><<<blocks, c.nthr, c.smem, st>>>((const double2 *)in, (double2 *)out,
-                                                                           nlines, sc, c.nl, c.gthr, tw);
+                                                                           nlines, sc, c.nl, c.gthr, tw, 0);
         } else {
             e = raise_smem(k_fft_hook<Pol, false, E()>, c.smem);
             if (e == cudaSuccess)
                 k_fft_hook<Pol, false, E()><<<blocks, c.nthr, c.smem, st>>>((const double2 *)in, (double2 *)out,
-                                                                            nlines, sc, c.nl, c.gthr, tw);
+                                                                            nlines, sc, c.nl, c.gthr, tw, 0);
         }
     });
     GSM_CUDA_TRY(e);
