@@ -160,7 +160,7 @@ def profiled_traffic(kernel: str, precision: str):
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
             t = json.load(f)
         e = t["kernels"][f"{kernel}:{precision}"]
-        if t.get("source_hash") == kernel_source_hash():
+        if e.get("source_hash", t.get("source_hash")) == kernel_source_hash():
             return e["dram_bytes_per_launch_full_size"]
     except Exception:
         pass
