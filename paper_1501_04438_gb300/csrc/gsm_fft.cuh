@@ -293,6 +293,12 @@ __device__ __forceinline__ Group make_group(int T, int nl)
     return g;
 }
 
+// b mod Ns; the radix-8/4/2 stages come first, so Ns is usually a power of two
+__device__ __forceinline__ int stage_mod(int b, int Ns)
+{
+    return (Ns & (Ns - 1)) == 0 ? (b & (Ns - 1)) : b % Ns;
+}
+
 // ---------------------------------------------------------------- one stage
 // One Stockham stage on one line s[pidx(0..M-1)] by the group.  NB = upper
 // bound of butterflies per thread (compile time); every thread first loads
@@ -317,7 +323,7 @@ __device__ __forceinline__ void fft_stage(typename Pol::scplx *s, int M, int Ns,
 #pragma unroll
             for (int t = 0; t < NIN; ++t) v[i][t] = Pol::ld(s[pidx<Pol>(b + t * nb)]);
             if (Ns > 1) {
-                const int j = b % Ns;
+                const int j = stage_mod(b, Ns);
 #pragma unroll
                 for (int t = 1; t < NIN; ++t) {
                     cx<R> w = Pol::tw(tw[j * t * step]);
@@ -332,7 +338,7 @@ __device__ __forceinline__ void fft_stage(typename Pol::scplx *s, int M, int Ns,
     for (int i = 0; i < NB; ++i) {
         const int b = g.t + i * g.T;
         if (b < nb) {
-            const int j = b % Ns;
+            const int j = stage_mod(b, Ns);
             const int d0 = (b - j) * RAD + j;
 #pragma unroll
             for (int t = 0; t < NOUT; ++t) s[pidx<Pol>(d0 + t * Ns)] = Pol::st(v[i][t]);
@@ -506,12 +512,15 @@ __device__ __forceinline__ void fft_stage8_fma(double2 *s, int M, int Ns, const 
 template <class Pol, bool FWD, int EMAX, bool ZPAD_ = false, bool CROP_ = false>
 __device__ __forceinline__ void fft_line(typename Pol::scplx *s, const Sched &sc,
                                          const typename Pol::tw_t *__restrict__ tw, const Group &g,
-                                         const double *__restrict__ gt = nullptr)
+                                         const double *__restrict__ gt = nullptr, int st_begin = 0,
+                                         int st_end = -1)
 {
     // pruning pays where the arithmetic pipe is the limit: FP64 only
     constexpr bool ZPAD = ZPAD_ && Pol::kPrune, CROP = CROP_ && Pol::kPrune;
-    int Ns = 1, st = 0;
     const int M = sc.M, last = sc.nst - 1;
+    const int nend = st_end < 0 ? sc.nst : st_end;   // stages [st_begin, nend) run
+    int Ns = 1, st = st_begin;
+    for (int i = 0; i < st_begin; ++i) Ns *= sc.r[i];
 #define GSM_STAGE(RAD)                                                                         \
     do {                                                                                       \
         constexpr int NB = (EMAX + RAD - 1) / RAD;                                             \
@@ -529,24 +538,87 @@ __device__ __forceinline__ void fft_line(typename Pol::scplx *s, const Sched &sc
         // register allocator dearly).
         if (gt != nullptr && sc.nst > 0 && sc.r[0] == 8) {
             constexpr int NB8 = (EMAX + 7) / 8;
-            if (ZPAD) fft_stage<Pol, 8, FWD, NB8, 1>(s, M, 1, tw, g);
-            else fft_stage<Pol, 8, FWD, NB8, 0>(s, M, 1, tw, g);
-            st = 1;
-            Ns = 8;
-            size_t goff = 0;
-            for (; st < sc.nst && sc.r[st] == 8; ++st, Ns *= 8) {
+            if (st == 0 && st < nend) {
+                if (ZPAD) fft_stage<Pol, 8, FWD, NB8, 1>(s, M, 1, tw, g);
+                else fft_stage<Pol, 8, FWD, NB8, 0>(s, M, 1, tw, g);
+                st = 1;
+                Ns = 8;
+            }
+            size_t goff = 0;   // constants of stage Ns start after those of 8, 64, ..., Ns/8
+            for (size_t q = 8; q < (size_t)Ns; q *= 8) goff += q * kG8Slots;
+            for (; st < nend && sc.r[st] == 8; ++st, Ns *= 8) {
                 if (CROP && st == last) fft_stage8_fma<FWD, NB8, 2>(s, M, Ns, gt + goff, g);
                 else fft_stage8_fma<FWD, NB8, 0>(s, M, Ns, gt + goff, g);
                 goff += (size_t)Ns * kG8Slots;
             }
         }
     }
-    for (; st < sc.nst && sc.r[st] == 8; ++st, Ns *= 8) GSM_STAGE(8);
-    for (; st < sc.nst && sc.r[st] == 4; ++st, Ns *= 4) GSM_STAGE(4);
-    for (; st < sc.nst && sc.r[st] == 2; ++st, Ns *= 2) GSM_STAGE(2);
-    for (; st < sc.nst && sc.r[st] == 5; ++st, Ns *= 5) GSM_STAGE(5);
-    for (; st < sc.nst && sc.r[st] == 3; ++st, Ns *= 3) GSM_STAGE(3);
+    for (; st < nend && sc.r[st] == 8; ++st, Ns *= 8) GSM_STAGE(8);
+    for (; st < nend && sc.r[st] == 4; ++st, Ns *= 4) GSM_STAGE(4);
+    for (; st < nend && sc.r[st] == 2; ++st, Ns *= 2) GSM_STAGE(2);
+    for (; st < nend && sc.r[st] == 5; ++st, Ns *= 5) GSM_STAGE(5);
+    for (; st < nend && sc.r[st] == 3; ++st, Ns *= 3) GSM_STAGE(3);
 #undef GSM_STAGE
+}
+
+// Whether fft_fused_mid8 applies: the schedule starts and ends with radix 8
+// (M = 8^k, k >= 2).
+__host__ __device__ __forceinline__ bool fusable8(const Sched &sc)
+{
+    return sc.nst >= 2 && sc.r[0] == 8 && sc.r[sc.nst - 1] == 8;
+}
+
+// The last forward stage, a pointwise multiplication by mult(k) and the first
+// inverse stage of a line whose schedule starts and ends with radix 8, in
+// registers.  The forward stage's butterfly b (Ns = M/8 = nb, so j = b)
+// leaves its outputs at the natural indices b + t M/8, which are exactly the
+// inputs of the inverse's (untwiddled) butterfly b; that one writes to 8b + t.
+// Saves two shared-memory round trips and a barrier over running the two
+// transforms and the multiplication apart.  Follow with
+// fft_line<Pol, false, ...>(..., st_begin = 1).
+template <class Pol, int NB, class MultF>
+__device__ __forceinline__ void fft_fused_mid8(typename Pol::scplx *s, const Sched &sc,
+                                               const typename Pol::tw_t *__restrict__ tw, const Group &g,
+                                               const double *__restrict__ gt, MultF mult)
+{
+    using R = typename Pol::real;
+    const int M = sc.M, nb = M / 8;
+    cx<R> v[NB][8];
+#pragma unroll
+    for (int i = 0; i < NB; ++i) {
+        const int b = g.t + i * g.T;
+        if (b < nb) {
+#pragma unroll
+            for (int t = 0; t < 8; ++t) v[i][t] = Pol::ld(s[pidx<Pol>(b + t * nb)]);
+            bool done = false;
+            if constexpr (std::is_same<Pol, F64>::value) {
+                if (gt != nullptr) {
+                    size_t goff = 0;
+                    for (size_t q = 8; q < (size_t)nb; q *= 8) goff += q * kG8Slots;
+                    bfly8_fma<true, 8>(v[i], gt + goff + (size_t)b * kG8Slots);
+                    done = true;
+                }
+            }
+            if (!done) {
+#pragma unroll
+                for (int t = 1; t < 8; ++t) v[i][t] = cmul(v[i][t], Pol::tw(tw[b * t]));   // twiddle step 1
+                bfly<R, 8, true, 0>(v[i]);
+            }
+#pragma unroll
+            for (int t = 0; t < 8; ++t) v[i][t] = cscale(v[i][t], mult(b + t * nb));
+            bfly<R, 8, false, 0>(v[i]);
+        }
+    }
+    group_sync(g);
+#pragma unroll
+    for (int i = 0; i < NB; ++i) {
+        const int b = g.t + i * g.T;
+        if (b < nb) {
+#pragma unroll
+            for (int t = 0; t < 8; ++t) s[pidx<Pol>(8 * b + t)] = Pol::st(v[i][t]);
+        }
+    }
+    group_sync(g);
 }
 
 }  // namespace gsm

@@ -174,30 +174,34 @@ __device__ __forceinline__ void body_conv(S_t<Pol> *__restrict__ W, const typena
         s[pidx<Pol>(z)] = v;
     }
     group_sync(g);
-    fft_line<Pol, true, EMAX, true, false>(s, sc, tw, g, g8_table<Pol>(tw, M));
+    // multiplier of frequency k: the whole half spectrum is stored (full), or
+    // the octant, read at min(k, M - k) (the multiplier is even)
+    const typename Pol::mult_t *mrow;
     if (full) {
-        const typename Pol::mult_t *mrow = mult + (size_t)line * M;
-        for (int k = g.t; k < M; k += g.T) {
-            const int p = pidx<Pol>(k);
-            s[p] = Pol::st(cscale(Pol::ld(s[p]), Pol::mult(mrow[k])));
-        }
+        mrow = mult + (size_t)line * M;
+    } else if (is3d) {
+        const int kx = line / My, ky = line - kx * My;
+        mrow = mult + ((size_t)kx * ny1 + min(ky, My - ky)) * (n + 1);
     } else {
-        size_t row;
-        if (is3d) {
-            const int kx = line / My, ky = line - kx * My;
-            row = ((size_t)kx * ny1 + min(ky, My - ky)) * (n + 1);
-        } else {
-            row = (size_t)line * (n + 1);
-        }
-        const typename Pol::mult_t *mrow = mult + row;
-        for (int k = g.t; k < M; k += g.T) {
-            const R m = Pol::mult(mrow[min(k, M - k)]);
-            const int p = pidx<Pol>(k);
-            s[p] = Pol::st(cscale(Pol::ld(s[p]), m));
-        }
+        mrow = mult + (size_t)line * (n + 1);
     }
-    group_sync(g);
-    fft_line<Pol, false, EMAX, false, true>(s, sc, tw, g, g8_table<Pol>(tw, M));
+    auto mult_of = [&](int k) -> R { return Pol::mult(mrow[full ? k : min(k, M - k)]); };
+    const double *gt = g8_table<Pol>(tw, M);
+    if (fusable8(sc)) {
+        // forward up to its last stage; last forward stage, multiplication and
+        // first inverse stage in registers; the rest of the inverse
+        fft_line<Pol, true, EMAX, true, false>(s, sc, tw, g, gt, 0, sc.nst - 1);
+        fft_fused_mid8<Pol, (EMAX + 7) / 8>(s, sc, tw, g, gt, mult_of);
+        fft_line<Pol, false, EMAX, false, true>(s, sc, tw, g, gt, 1);
+    } else {
+        fft_line<Pol, true, EMAX, true, false>(s, sc, tw, g, gt);
+        for (int k = g.t; k < M; k += g.T) {
+            const int p = pidx<Pol>(k);
+            s[p] = Pol::st(cscale(Pol::ld(s[p]), mult_of(k)));
+        }
+        group_sync(g);
+        fft_line<Pol, false, EMAX, false, true>(s, sc, tw, g, gt);
+    }
     for (int z = g.t; z < n; z += g.T) w[z] = s[pidx<Pol>(z)];
 }
 
