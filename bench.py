@@ -424,6 +424,18 @@ def _time_apply(torch, fn, steps, flush, stream):
     return float(np.mean([a.elapsed_time(b) for a, b in ev]))
 
 
+def _cpu_leg(run, points: int, sample: str):
+    """A config's CPU-baseline leg: the oracle, as it stands, on the host cores.
+    `run` does one oracle evaluation (its set-up already done); it is timed, and
+    its output also serves as the line's parity reference."""
+    import oracle
+    t0 = time.perf_counter()
+    out = run()
+    dt = time.perf_counter() - t0
+    return out, {"value": points / dt / 1e6, "unit": UNIT, "cores": oracle.max_threads(), "kind": "oracle",
+                 "sample": sample, "seconds": dt}
+
+
 def run_suite(a):
     import torch
 
@@ -466,8 +478,10 @@ def run_suite(a):
     rho = wl.coulomb3d_gaussian(32, 8.0, 1.0)
     X, Y, Z = wl.mesh((32, 32, 32), 8.0)
     ue = coulomb3d_gaussian(np.sqrt(X * X + Y * Y + Z * Z), 1.0)
-    uo = oracle.apply("coulomb3d", rho, 8.0)[0]
+    prep = oracle.Prepared("coulomb3d", 32, 8.0)
+    uo, cpu = _cpu_leg(lambda: prep.run(rho), 32 ** 3, "the whole 32^3 config, apply only")
     line = precisions_line("1", "coulomb3d", rho, 8.0, (32, 32, 32), uo, ue)
+    line["cpu_baseline"] = cpu
     line["oracle_rel_err_vs_closed_form"] = relmax(uo, ue)
     emit(line)
 
@@ -475,10 +489,10 @@ def run_suite(a):
     for n in (128, 256):
         for name, rho in (("2a anisotropic", wl.coulomb3d_anisotropic(n, 12.0, 4.0)),
                           ("2b mixture8", wl.coulomb3d_mixture(n, 12.0))):
-            t0 = time.perf_counter()
-            uo = oracle.Prepared("coulomb3d", n, 12.0).run(rho)
+            prep = oracle.Prepared("coulomb3d", n, 12.0)
+            uo, cpu = _cpu_leg(lambda: prep.run(rho), n ** 3, f"the whole {n}^3 config, apply only")
             line = precisions_line(name, "coulomb3d", rho, 12.0, (n, n, n), uo)
-            line["oracle_s"] = time.perf_counter() - t0
+            line["cpu_baseline"] = cpu
             emit(line)
 
     # config 3: 2D Poisson and Coulomb on [-16,16]^2, 1024^2 and 4096^2, 6 isotropic Gaussians
@@ -492,10 +506,10 @@ def run_suite(a):
                 r = np.sqrt((X - c[0]) ** 2 + (Y - c[1]) ** 2)
                 f = poisson2d_gaussian if kernel == "poisson2d" else coulomb2d_gaussian
                 closed += amp * f(r, sw[0])
-            t0 = time.perf_counter()
-            uo = oracle.Prepared(kernel, n, 16.0).run(rho)
+            prep = oracle.Prepared(kernel, n, 16.0)
+            uo, cpu = _cpu_leg(lambda: prep.run(rho), n * n, f"the whole {n}^2 config, apply only")
             line = precisions_line("3", kernel, rho, 16.0, (n, n), uo, closed)
-            line["oracle_s"] = time.perf_counter() - t0
+            line["cpu_baseline"] = cpu
             line["oracle_rel_err_vs_closed_form"] = relmax(uo, closed)
             emit(line)
 
@@ -518,19 +532,24 @@ def run_suite(a):
         batch = gsm.Batch(plans, rhos, outs, stream=stream)
         ms_graph = _time_apply(torch, lambda: batch.launch(stream=stream), steps, flush, stream)
         same_graph = all(torch.equal(x, y) for x, y in zip(outs, loop_out))
-        # oracle spot check on three instances
-        errs = []
+        # CPU-baseline leg on three of the instances, also the parity sample
+        errs, cpu_s, cpu_pts = [], 0.0, 0
         for i in (0, len(specs) // 2, len(specs) - 1):
             n, prm = specs[i]
-            uo = oracle.Prepared("coulomb3d", n, 10.0, S=plans[i].info()["S"], taylor_mode=1).run(
-                wl.mixture((n, n, n), 10.0, prm))
+            prep = oracle.Prepared("coulomb3d", n, 10.0, S=plans[i].info()["S"], taylor_mode=1)
+            rho_i = wl.mixture((n, n, n), 10.0, prm)
+            uo, cpu_i = _cpu_leg(lambda: prep.run(rho_i), n ** 3, "")
+            cpu_s += cpu_i["seconds"]
+            cpu_pts += n ** 3
             errs.append(relmax(outs[i].double().cpu().numpy(), uo))
+        cpu = dict(cpu_i, value=cpu_pts / cpu_s / 1e6, seconds=cpu_s,
+                   sample="instances 0, 24 and 47 of the 48, apply only")
         emit({"config": "4 batch48", "precision": prec, "instances": len(specs),
               "sizes": [n for n, _ in specs], "points": npts,
               "loop": {"ms": ms_loop, "Mpts_s": npts / ms_loop / 1e3},
               "grouped": {"ms": ms_grouped, "Mpts_s": npts / ms_grouped / 1e3, "bitwise_equal_loop": same},
               "graph": {"ms": ms_graph, "Mpts_s": npts / ms_graph / 1e3, "bitwise_equal_loop": same_graph},
-              "rel_err_vs_oracle_sampled": errs})
+              "rel_err_vs_oracle_sampled": errs, "cpu_baseline": cpu})
         batch.destroy()
         for p in plans:
             p.destroy()
@@ -555,7 +574,8 @@ def run_suite(a):
             E, g = fwd_bwd()
         torch.cuda.synchronize()
         ms = _time_apply(torch, fwd_bwd, steps, flush, stream)
-        E_o, g_o, _ = oracle.hartree(kernel, psi_h, L, taylor_mode=1, S=plan.info()["S"])
+        (E_o, g_o, _), cpu = _cpu_leg(lambda: oracle.hartree(kernel, psi_h, L, taylor_mode=1, S=plan.info()["S"]),
+                                      n ** 3, f"energy and gradient of the whole {n}^3 config, plan included")
         gh = g.cpu().numpy()
         # central differences of the GPU energy, h = 1e-6, real and imaginary parts
         rng = np.random.default_rng(5)
@@ -578,7 +598,8 @@ def run_suite(a):
               "ms_energy_and_gradient": ms, "Mpts_s": n ** 3 / ms / 1e3,
               "energy": float(E.detach()), "rel_err_energy_vs_oracle": abs(float(E.detach()) - E_o) / abs(E_o),
               "rel_err_grad_vs_oracle": float(np.max(np.abs(gh - g_o)) / np.max(np.abs(g_o))),
-              "fd_max_abs_err_over_max_grad": fd_err / float(np.max(np.abs(g_o))), "fd_points": 2 * len(idxs)})
+              "fd_max_abs_err_over_max_grad": fd_err / float(np.max(np.abs(g_o))), "fd_points": 2 * len(idxs),
+              "cpu_baseline": cpu})
         plan.destroy()
 
 
