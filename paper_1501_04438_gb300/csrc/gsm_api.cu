@@ -43,6 +43,9 @@ static void free_plan(Plan *p)
     cudaFree(p->d_work2);
     cudaFree(p->d_stage_in);
     cudaFree(p->d_stage_out);
+    for (cudaEvent_t e : p->copy_ev)
+        if (e) cudaEventDestroy(e);
+    if (p->copy_stream) cudaStreamDestroy(p->copy_stream);
     cudaFree(p->d_scratch);
     p->magic = 0;
     delete p;
@@ -459,10 +462,56 @@ gsm_status_t gsm_apply_host(gsm_plan_t h, const void *rho_host, void *u_host, vo
         GSM_CUDA_TRY(cudaMalloc(&p->d_stage_in, bytes));
         GSM_CUDA_TRY(cudaMalloc(&p->d_stage_out, bytes));
     }
-    GSM_CUDA_TRY(cudaMemcpyAsync(p->d_stage_in, rho_host, bytes, cudaMemcpyHostToDevice, st));
-    gsm_status_t s = launch_apply(p, p->d_stage_in, p->d_stage_out, st);
-    if (s != GSM_OK) return s;
-    GSM_CUDA_TRY(cudaMemcpyAsync(u_host, p->d_stage_out, bytes, cudaMemcpyDeviceToHost, st));
+    if (p->d != 3) {
+        GSM_CUDA_TRY(cudaMemcpyAsync(p->d_stage_in, rho_host, bytes, cudaMemcpyHostToDevice, st));
+        gsm_status_t s = launch_apply(p, p->d_stage_in, p->d_stage_out, st);
+        if (s != GSM_OK) return s;
+        GSM_CUDA_TRY(cudaMemcpyAsync(u_host, p->d_stage_out, bytes, cudaMemcpyDeviceToHost, st));
+        GSM_CUDA_TRY(cudaStreamSynchronize(st));
+        return GSM_OK;
+    }
+    // 3D: the x passes work slab by slab, so the host-to-device copy of z-chunk c
+    // overlaps the x forward pass of chunk c - 1, and the device-to-host copy of
+    // chunk c the x inverse pass of chunk c + 1 (copies on the plan's own stream,
+    // ordered against `st` by events)
+    if (!p->copy_stream) {
+        GSM_CUDA_TRY(cudaStreamCreateWithFlags(&p->copy_stream, cudaStreamNonBlocking));
+        for (cudaEvent_t &e : p->copy_ev) GSM_CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    }
+    cudaStream_t cs = p->copy_stream;
+    const int nz = p->n[2];
+    const int K = nz < kHostChunks ? nz : kHostChunks;
+    const size_t slab = (size_t)p->n[0] * p->n[1] * io_bytes(p);
+    const unsigned char *hin = static_cast<const unsigned char *>(rho_host);
+    unsigned char *hout = static_cast<unsigned char *>(u_host);
+    unsigned char *din = static_cast<unsigned char *>(p->d_stage_in);
+    unsigned char *dout = static_cast<unsigned char *>(p->d_stage_out);
+    cudaEvent_t *ev_in = p->copy_ev, *ev_out = p->copy_ev + kHostChunks, ev_start = p->copy_ev[2 * kHostChunks],
+                ev_done = p->copy_ev[2 * kHostChunks + 1];
+    GSM_CUDA_TRY(cudaEventRecord(ev_start, st));          // work queued before on `st` comes first
+    GSM_CUDA_TRY(cudaStreamWaitEvent(cs, ev_start, 0));
+    for (int c = 0; c < K; ++c) {
+        const int z0 = (int)((long)nz * c / K), z1 = (int)((long)nz * (c + 1) / K);
+        GSM_CUDA_TRY(cudaMemcpyAsync(din + z0 * slab, hin + z0 * slab, (z1 - z0) * slab, cudaMemcpyHostToDevice, cs));
+        GSM_CUDA_TRY(cudaEventRecord(ev_in[c], cs));
+        GSM_CUDA_TRY(cudaStreamWaitEvent(st, ev_in[c], 0));
+        gsm_status_t s = launch_x_slabs(p, false, z0, z1, din, nullptr, st);
+        if (s != GSM_OK) return s;
+    }
+    for (int pass = 1; pass <= 3; ++pass) {
+        gsm_status_t s = launch_pass(p, pass, nullptr, nullptr, st);
+        if (s != GSM_OK) return s;
+    }
+    for (int c = 0; c < K; ++c) {
+        const int z0 = (int)((long)nz * c / K), z1 = (int)((long)nz * (c + 1) / K);
+        gsm_status_t s = launch_x_slabs(p, true, z0, z1, nullptr, dout, st);
+        if (s != GSM_OK) return s;
+        GSM_CUDA_TRY(cudaEventRecord(ev_out[c], st));
+        GSM_CUDA_TRY(cudaStreamWaitEvent(cs, ev_out[c], 0));
+        GSM_CUDA_TRY(cudaMemcpyAsync(hout + z0 * slab, dout + z0 * slab, (z1 - z0) * slab, cudaMemcpyDeviceToHost, cs));
+    }
+    GSM_CUDA_TRY(cudaEventRecord(ev_done, cs));
+    GSM_CUDA_TRY(cudaStreamWaitEvent(st, ev_done, 0));     // later work on `st` sees u
     GSM_CUDA_TRY(cudaStreamSynchronize(st));
     return GSM_OK;
 }

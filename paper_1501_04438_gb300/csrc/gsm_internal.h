@@ -58,6 +58,8 @@ struct Plan {
     size_t mult_elems_pass = 0;    // entries of the pass-precision table
     bool mult_full = false;        // pass table covers the half spectrum (general dipolar)
     void *d_stage_in = nullptr, *d_stage_out = nullptr;   // gsm_apply_host staging
+    cudaStream_t copy_stream = nullptr;                    // gsm_apply_host copies (3D)
+    cudaEvent_t copy_ev[2 * 8 + 2] = {};                   // chunk events of that pipeline
     double *d_scratch = nullptr;                           // energy partial sums
     size_t scratch_elems = 0;
 
@@ -87,6 +89,12 @@ gsm_status_t build_plan_data(Plan *p, cudaStream_t st, const StoredPlanData *sto
 gsm_status_t configure_passes(Plan *p);
 gsm_status_t launch_apply(const Plan *p, const void *rho, void *u, cudaStream_t st);
 gsm_status_t launch_pass(const Plan *p, int pass, const void *rho, void *u, cudaStream_t st);
+// 3D only: the x forward pass (inverse = false, reads rho) or the x inverse
+// pass (inverse = true, writes u) on the z-slabs [z0, z1); rho and u point
+// at the whole arrays
+gsm_status_t launch_x_slabs(const Plan *p, bool inverse, int z0, int z1, const void *rho, void *u,
+                            cudaStream_t st);
+constexpr int kHostChunks = 8;       // z-chunks of the pipelined host apply
 gsm_status_t autotune_plan(Plan *p, cudaStream_t st, std::string *report);
 // set the launch shape of one pass (nl lines per CTA, emax elements per thread)
 gsm_status_t set_pass_shape(Plan *p, int pass, int nl, int emax);

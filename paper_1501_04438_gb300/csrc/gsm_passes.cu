@@ -979,6 +979,49 @@ gsm_status_t launch_apply(const Plan *p, const void *rho, void *u, cudaStream_t 
     }
 }
 
+template <class Pol>
+gsm_status_t x_slabs_t(const Plan *p, bool inverse, int z0, int z1, const void *rho_v, void *u_v,
+                       cudaStream_t st)
+{
+    using io = typename Pol::io_t;
+    using tw = typename Pol::tw_t;
+    const int nx = p->n[0], ny = p->n[1], hx = nx + 1;
+    const size_t in_off = (size_t)z0 * ny * nx, w_off = (size_t)z0 * hx * ny;
+    S_t<Pol> *W1 = static_cast<S_t<Pol> *>(p->d_work1) + w_off;
+    const tw *twx = static_cast<const tw *>(p->d_tw[0]);
+    if (z1 <= z0) return GSM_OK;
+    if (!inverse) {
+        const PassCfg &c = p->cfg_xf;
+        dim3 g((ny + 2 * c.nl - 1) / (2 * c.nl), z1 - z0);
+        const io *rho = static_cast<const io *>(rho_v) + in_off;
+        with_emax(c, [&](auto E) {
+            k_xf<Pol, E()><<<g, c.nthr, c.smem, st>>>(rho, W1, nx, ny, hx, p->sched[0], c.nl, c.gthr, twx);
+        });
+    } else {
+        const PassCfg &c = p->cfg_xi;
+        dim3 g((ny + 2 * c.nl - 1) / (2 * c.nl), z1 - z0);
+        io *u = static_cast<io *>(u_v) + in_off;
+        with_emax(c, [&](auto E) {
+            k_xi<Pol, E()><<<g, c.nthr, c.smem, st>>>(W1, u, nx, ny, hx, p->sched[0], c.nl, c.gthr, twx);
+        });
+    }
+    GSM_CUDA_TRY(cudaGetLastError());
+    return GSM_OK;
+}
+
+gsm_status_t launch_x_slabs(const Plan *p, bool inverse, int z0, int z1, const void *rho, void *u, cudaStream_t st)
+{
+    if (p->d != 3 || z0 < 0 || z1 > p->n[2]) {
+        set_error("x slabs: 3D plans and 0 <= z0 <= z1 <= nz only");
+        return GSM_ERR_INVALID_ARG;
+    }
+    switch (p->opt.precision) {
+    case GSM_FP64: return x_slabs_t<F64>(p, inverse, z0, z1, rho, u, st);
+    case GSM_FP32: return x_slabs_t<F32>(p, inverse, z0, z1, rho, u, st);
+    default: return x_slabs_t<DF64>(p, inverse, z0, z1, rho, u, st);
+    }
+}
+
 gsm_status_t launch_pass(const Plan *p, int pass, const void *rho, void *u, cudaStream_t st)
 {
     switch (p->opt.precision) {

@@ -209,13 +209,23 @@ def test_invalid_arguments_raise_status(gsm):
         gsm.Plan("ds2d", 1.0, (16, 16, 16))      # the binding checks the dimension
 
 
-def test_apply_host_equals_device(gsm):
+@pytest.mark.parametrize("precision", ["fp64", "fp32x2", "fp32"])
+def test_apply_host_equals_device(gsm, precision):
+    """The host apply (3D: copies pipelined with the x passes in z-chunks) gives
+    the device apply's bits, for chunkings with ragged, single-slab and many
+    slabs per chunk, repeated calls, and 2D."""
     torch = _torch()
-    rho = wl.coulomb3d_mixture(40, 12.0)
-    plan = gsm.Plan("coulomb3d", 12.0, 40)
-    uh = plan.apply_host(rho)
-    ud = plan.apply(torch.tensor(rho, device="cuda")).cpu().numpy()
-    assert np.array_equal(uh, ud)
+    dt = torch.float32 if precision == "fp32" else torch.float64
+    npd = np.float32 if precision == "fp32" else np.float64
+    for kernel, n in (("coulomb3d", (40, 40, 40)), ("coulomb3d", (16, 12, 20)), ("dipolar3d", (12, 10, 8)),
+                      ("poisson2d", (48, 30))):
+        rho = np.random.default_rng(17).standard_normal(n[::-1]).astype(npd)
+        plan = gsm.Plan(kernel, 5.0, n, precision=precision)
+        for _ in range(2):
+            uh = plan.apply_host(rho)
+            ud = plan.apply(torch.tensor(rho, dtype=dt, device="cuda")).cpu().numpy()
+            torch.cuda.synchronize()
+            assert np.array_equal(uh, ud), (kernel, n)
 
 
 def test_batched_equals_single(gsm):
