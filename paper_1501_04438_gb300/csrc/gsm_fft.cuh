@@ -347,36 +347,46 @@ __device__ __forceinline__ void fft_stage(typename Pol::scplx *s, int M, int Ns,
     group_sync(g);
 }
 
-// ---------------------------------------------------------------- FMA-form radix 8 (FP64)
-// Doubles of the FMA-form constants for a schedule: 16 per index j of every
-// radix-8 stage after the first (Ns = 8, 64, ...).
-inline size_t g8_table_doubles(const Sched &sc)
+// ---------------------------------------------------------------- FMA-form stages (FP64)
+// FMA-form constants exist for the twiddled stages of radix 8, 4 and 2 (they
+// come first in every schedule, so their Ns are powers of two): gslots(R)
+// doubles per index j, stage after stage in schedule order.
+__host__ __device__ __forceinline__ bool gtabled(int R) { return R == 8 || R == 4 || R == 2; }
+__host__ __device__ __forceinline__ int gslots(int R) { return R == 8 ? 16 : (R == 4 ? 8 : 4); }
+
+// Offset (in doubles) of the constants of stage st.
+__host__ __device__ inline size_t gtable_offset(const Sched &sc, int st)
 {
-    size_t tot = 0, Ns = 1;
-    for (int st = 0; st < sc.nst && sc.r[st] == 8; ++st, Ns *= 8)
-        if (Ns > 1) tot += Ns * 16;
-    return tot;
+    size_t off = 0, Ns = 1;
+    for (int i = 0; i < st && i < sc.nst; ++i) {
+        if (Ns > 1 && gtabled(sc.r[i])) off += Ns * (size_t)gslots(sc.r[i]);
+        Ns *= (size_t)sc.r[i];
+    }
+    return off;
 }
 
-// A twiddled radix-8 stage in which every multiplication is fused into an
-// addition: the "tangent" form of the twiddle factors (E. N. Linzer and
-// E. Feig, IEEE Trans. Signal Process. 41 (1993); S. Goedecker, SIAM J. Sci.
-// Comput. 18 (1997)).  Each twiddle W_t = w^(jt) is written
+// Doubles of all FMA-form constants of a schedule.
+inline size_t g8_table_doubles(const Sched &sc) { return gtable_offset(sc, sc.nst); }
+
+// Twiddled stages in which every multiplication is fused into an addition:
+// the "tangent" form of the twiddle factors (E. N. Linzer and E. Feig, IEEE
+// Trans. Signal Process. 41 (1993); S. Goedecker, SIAM J. Sci. Comput. 18
+// (1997)).  Each twiddle W_t = w^(jt) is written
 //   W_t = f_t i^(k_t) (1 + i tau_t),  |tau_t| <= 1,  f_t = cos(phi_t) >= 1/sqrt2,
 // with i^(k_t) the nearest quarter turn.  X_t = i^(k_t)(1 + i tau_t) x_t costs
 // two FMAs (the quarter turn is a swap and sign flips, done on the integer
-// side); the real scales f_t are carried as ratios through the three layers of
-// the radix-8 butterfly (t vs t+4, then the two radix-4 layers), each layer a
-// pair of FMAs per complex value, and cancel at the end because f_0 = 1.
-// 66 FP64 instructions per butterfly instead of 80 (14 complex multiplications'
-// worth of DMUL/DFMA, then the additions).  The constants of stage Ns, index j,
-// are 16 doubles (one 128-byte line) at gt[16 j]:
-//   0..6  tau_t sigma_t (t = 1..7; sigma_t = -1 for odd k_t, which folds the
-//         swap's sign into the tangent)
-//   7..10 r_t = f_(t+4) / f_t (t = 0..3)
-//   11 f_2, 12 f_3 / f_1, 13 f_1, 14 f_1 / sqrt2
-//   15    k_t mod 4 in bits 2(t-1), 2(t-1)+1 (an integer in the double's bits)
-// for the forward direction; the inverse uses conj(W_t) = f_t i^(-k_t)(1 - i tau_t).
+// side); the real scales f_t are carried as ratios through the butterfly's
+// layers, each a pair of FMAs per complex value, and cancel at the end because
+// f_0 = 1.  Radix 8: 66 FP64 instructions per butterfly instead of 80;
+// radix 4: 22 instead of 28; radix 2: 6 instead of 8.  Constants per index j
+// (forward direction; the inverse uses conj(W_t) = f_t i^(-k_t)(1 - i tau_t)):
+//   radix 8 (16 doubles, one 128-byte line): 0..6 tau_t sigma_t (t = 1..7;
+//     sigma_t = -1 for odd k_t, which folds the swap's sign into the tangent),
+//     7..10 r_t = f_(t+4) / f_t (t = 0..3), 11 f_2, 12 f_3 / f_1, 13 f_1,
+//     14 f_1 / sqrt2, 15 the codes k_t mod 4 in bits 2(t-1), 2(t-1)+1 (an
+//     integer in the double's bits);
+//   radix 4 (8 doubles): tau_t sigma_t (t = 1..3), f_2, f_3 / f_1, f_1, codes, -;
+//   radix 2 (4 doubles): tau_1 sigma_1, f_1, code, -.
 constexpr int kG8Slots = 16;
 
 __device__ __forceinline__ double flip_sign(double x, unsigned neg)
@@ -462,23 +472,59 @@ __device__ __forceinline__ void bfly8_fma(cx<double> *v, const double *__restric
     }
 }
 
-// Twiddled radix-8 Stockham stage (Ns > 1) in FMA form; HALF = 2: only the
-// outputs t < 4 (the crop).  Same data movement as fft_stage.
-template <bool FWD, int NB, int HALF>
-__device__ __forceinline__ void fft_stage8_fma(double2 *s, int M, int Ns, const double *__restrict__ gt,
-                                               const Group &g)
+// Twiddled radix-4 butterfly in FMA form, in place (Y_0..Y_3 in natural
+// order; HALFOUT: Y_0, Y_1 only).  Constants at c: tau_t sigma_t (t = 1..3),
+// f_2, f_3 / f_1, f_1, the quarter-turn codes, one unused slot.
+template <bool FWD, bool HALFOUT>
+__device__ __forceinline__ void bfly4_fma(cx<double> *v, const double *__restrict__ c)
 {
-    constexpr int NOUT = HALF == 2 ? 4 : 8;
-    const int nb = M / 8;
-    cx<double> v[NB][8];
+    const int codes = __double2loint(__ldg(c + 6));
+#pragma unroll
+    for (int t = 1; t < 4; ++t) {
+        int k = (codes >> (2 * (t - 1))) & 3;
+        if (!FWD) k = (4 - k) & 3;
+        const double tt = __ldg(c + t - 1);
+        v[t] = tangent_rot(v[t], k, FWD ? tt : -tt);
+    }
+    dft4_scaled<FWD, HALFOUT>(v[0], v[1], v[2], v[3], __ldg(c + 3), __ldg(c + 4), __ldg(c + 5));
+}
+
+// Twiddled radix-2 butterfly in FMA form: Y_0,1 = x_0 +- f_1 X_1.  Constants
+// at c: tau_1 sigma_1, f_1, the quarter-turn code, one unused slot.
+template <bool FWD, bool HALFOUT>
+__device__ __forceinline__ void bfly2_fma(cx<double> *v, const double *__restrict__ c)
+{
+    int k = __double2loint(__ldg(c + 2)) & 3;
+    if (!FWD) k = (4 - k) & 3;
+    const double tt = __ldg(c);
+    const cx<double> X = tangent_rot(v[1], k, FWD ? tt : -tt);
+    const double f = __ldg(c + 1);
+    const cx<double> x0 = v[0];
+    v[0] = {fma(f, X.re, x0.re), fma(f, X.im, x0.im)};
+    if (!HALFOUT) v[1] = {fma(-f, X.re, x0.re), fma(-f, X.im, x0.im)};
+}
+
+// Twiddled Stockham stage of radix RAD (8, 4 or 2; Ns > 1, a power of two) in
+// FMA form; HALF = 2: only the outputs t < RAD/2 (the crop).  Same data
+// movement as fft_stage; gt points at this stage's constants.
+template <int RAD, bool FWD, int NB, int HALF>
+__device__ __forceinline__ void fft_stage_fma(double2 *s, int M, int Ns, const double *__restrict__ gt,
+                                              const Group &g)
+{
+    constexpr int NOUT = HALF == 2 ? RAD / 2 : RAD;
+    constexpr int SL = RAD == 8 ? 16 : (RAD == 4 ? 8 : 4);
+    const int nb = M / RAD;
+    cx<double> v[NB][RAD];
 #pragma unroll
     for (int i = 0; i < NB; ++i) {
         const int b = g.t + i * g.T;
         if (b < nb) {
 #pragma unroll
-            for (int t = 0; t < 8; ++t) v[i][t] = F64::ld(s[pidx<F64>(b + t * nb)]);
-            const int j = b & (Ns - 1);   // Ns is a power of 8
-            bfly8_fma<FWD, NOUT>(v[i], gt + (size_t)j * kG8Slots);
+            for (int t = 0; t < RAD; ++t) v[i][t] = F64::ld(s[pidx<F64>(b + t * nb)]);
+            const double *c = gt + (size_t)(b & (Ns - 1)) * SL;
+            if constexpr (RAD == 8) bfly8_fma<FWD, NOUT>(v[i], c);
+            else if constexpr (RAD == 4) bfly4_fma<FWD, HALF == 2>(v[i], c);
+            else bfly2_fma<FWD, HALF == 2>(v[i], c);
         }
     }
     group_sync(g);
@@ -487,7 +533,7 @@ __device__ __forceinline__ void fft_stage8_fma(double2 *s, int M, int Ns, const 
         const int b = g.t + i * g.T;
         if (b < nb) {
             const int j = b & (Ns - 1);
-            const int d0 = (b - j) * 8 + j;
+            const int d0 = (b - j) * RAD + j;
 #pragma unroll
             for (int t = 0; t < NOUT; ++t) s[pidx<F64>(d0 + t * Ns)] = F64::st(v[i][t]);
         }
@@ -506,9 +552,10 @@ __device__ __forceinline__ void fft_stage8_fma(double2 *s, int M, int Ns, const 
 // output is needed (the last stage is pruned when its radix is even; the
 // second half of the line is then left undefined).  Both apply to policies
 // with kPrune only; for the others the full stages run.
-// gt (FP64 only, may be NULL): the constants of the FMA-form radix-8 stages
-// (fft_stage8_fma), stage Ns = 8^s at gt + 16 (8 + 64 + ... + 8^(s-1)); with
-// NULL every stage takes the twiddle table tw.
+// gt (FP64 only, may be NULL): the constants of the FMA-form stages
+// (fft_stage_fma), laid out as gtable_offset describes; with NULL every stage
+// takes the twiddle table tw.  Stages [st_begin, st_end) run (st_end < 0: to
+// the last).
 template <class Pol, bool FWD, int EMAX, bool ZPAD_ = false, bool CROP_ = false>
 __device__ __forceinline__ void fft_line(typename Pol::scplx *s, const Sched &sc,
                                          const typename Pol::tw_t *__restrict__ tw, const Group &g,
@@ -532,24 +579,41 @@ __device__ __forceinline__ void fft_line(typename Pol::scplx *s, const Sched &sc
             fft_stage<Pol, RAD, FWD, NB, 0>(s, M, Ns, tw, g);                                  \
     } while (0)
     if constexpr (std::is_same<Pol, F64>::value) {
-        // radix-8 stages come first in the schedule: Ns = 1, 8, 64, ...  The
-        // first (no twiddles) is peeled off so that the loop holds only the
-        // FMA-form stage (a loop mixing several large stage bodies costs the
-        // register allocator dearly).
-        if (gt != nullptr && sc.nst > 0 && sc.r[0] == 8) {
-            constexpr int NB8 = (EMAX + 7) / 8;
+        // stages of radix 8, 4, 2 come first in the schedule (Ns powers of two).
+        // The untwiddled first stage is peeled off so that each loop holds only
+        // one FMA-form stage body (a loop mixing several large stage bodies
+        // costs the register allocator dearly).
+        if (gt != nullptr && sc.nst > 0 && gtabled(sc.r[0])) {
             if (st == 0 && st < nend) {
-                if (ZPAD) fft_stage<Pol, 8, FWD, NB8, 1>(s, M, 1, tw, g);
-                else fft_stage<Pol, 8, FWD, NB8, 0>(s, M, 1, tw, g);
+                const int r0 = sc.r[0];
+                if (r0 == 8) {
+                    if (ZPAD) fft_stage<Pol, 8, FWD, (EMAX + 7) / 8, 1>(s, M, 1, tw, g);
+                    else fft_stage<Pol, 8, FWD, (EMAX + 7) / 8, 0>(s, M, 1, tw, g);
+                } else if (r0 == 4) {
+                    if (ZPAD) fft_stage<Pol, 4, FWD, (EMAX + 3) / 4, 1>(s, M, 1, tw, g);
+                    else fft_stage<Pol, 4, FWD, (EMAX + 3) / 4, 0>(s, M, 1, tw, g);
+                } else {
+                    if (ZPAD) fft_stage<Pol, 2, FWD, (EMAX + 1) / 2, 1>(s, M, 1, tw, g);
+                    else fft_stage<Pol, 2, FWD, (EMAX + 1) / 2, 0>(s, M, 1, tw, g);
+                }
                 st = 1;
-                Ns = 8;
+                Ns = r0;
             }
-            size_t goff = 0;   // constants of stage Ns start after those of 8, 64, ..., Ns/8
-            for (size_t q = 8; q < (size_t)Ns; q *= 8) goff += q * kG8Slots;
+            size_t goff = gtable_offset(sc, st);
             for (; st < nend && sc.r[st] == 8; ++st, Ns *= 8) {
-                if (CROP && st == last) fft_stage8_fma<FWD, NB8, 2>(s, M, Ns, gt + goff, g);
-                else fft_stage8_fma<FWD, NB8, 0>(s, M, Ns, gt + goff, g);
-                goff += (size_t)Ns * kG8Slots;
+                if (CROP && st == last) fft_stage_fma<8, FWD, (EMAX + 7) / 8, 2>(s, M, Ns, gt + goff, g);
+                else fft_stage_fma<8, FWD, (EMAX + 7) / 8, 0>(s, M, Ns, gt + goff, g);
+                goff += (size_t)Ns * 16;
+            }
+            for (; st < nend && sc.r[st] == 4; ++st, Ns *= 4) {
+                if (CROP && st == last) fft_stage_fma<4, FWD, (EMAX + 3) / 4, 2>(s, M, Ns, gt + goff, g);
+                else fft_stage_fma<4, FWD, (EMAX + 3) / 4, 0>(s, M, Ns, gt + goff, g);
+                goff += (size_t)Ns * 8;
+            }
+            for (; st < nend && sc.r[st] == 2; ++st, Ns *= 2) {
+                if (CROP && st == last) fft_stage_fma<2, FWD, (EMAX + 1) / 2, 2>(s, M, Ns, gt + goff, g);
+                else fft_stage_fma<2, FWD, (EMAX + 1) / 2, 0>(s, M, Ns, gt + goff, g);
+                goff += (size_t)Ns * 4;
             }
         }
     }
@@ -593,9 +657,7 @@ __device__ __forceinline__ void fft_fused_mid8(typename Pol::scplx *s, const Sch
             bool done = false;
             if constexpr (std::is_same<Pol, F64>::value) {
                 if (gt != nullptr) {
-                    size_t goff = 0;
-                    for (size_t q = 8; q < (size_t)nb; q *= 8) goff += q * kG8Slots;
-                    bfly8_fma<true, 8>(v[i], gt + goff + (size_t)b * kG8Slots);
+                    bfly8_fma<true, 8>(v[i], gt + gtable_offset(sc, sc.nst - 1) + (size_t)b * kG8Slots);
                     done = true;
                 }
             }

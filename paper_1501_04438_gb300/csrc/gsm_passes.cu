@@ -397,56 +397,86 @@ __global__ void __launch_bounds__(32 * kBatchMaxLines) k_batch(const __grid_cons
 }
 
 // ------------------------------------------------------------------ tables
-// Constants of the FMA-form radix-8 stages (layout in gsm_fft.cuh, before
-// fft_stage8_fma) for the radix-8 stages s = 1..n8-1 of a schedule, Ns = 8^s,
-// one thread per (stage, j).  Forward twiddle W_t = exp(-2 pi i j t / (8 Ns)):
-// with q = j t, K = round(q / 2Ns) and m = q - 2 Ns K (|m| <= Ns),
-// W_t = i^(-K) exp(-i pi m / (4 Ns)), so k_t = -K mod 4, f_t = cos(pi m / 4Ns),
-// tau_t = -tan(pi m / 4Ns).
-__global__ void k_g8table(int n8, double *out)
+// Constants of the FMA-form stages (layout before kG8Slots in gsm_fft.cuh),
+// one thread per (stage, j).  For stage radix R with Ns, forward twiddle
+// W_t = exp(-2 pi i q / D), q = j t, D = R Ns: with K = round(4 q / D) and
+// m = q - K D/4 (|m| <= D/8), W_t = i^(-K) exp(-2 pi i m / D), so k_t = -K mod 4,
+// f_t = cos(2 pi m / D), tau_t = -tan(2 pi m / D).
+struct GStage {
+    int R;
+    long Ns, off;   // off: first double of the stage's constants
+};
+struct GTableDesc {
+    int n;
+    GStage s[kMaxStages];
+};
+
+__global__ void k_gtable(GTableDesc d, double *out)
 {
-    long idx = blockIdx.x * (long)blockDim.x + threadIdx.x;
-    long Ns = 8, base = 0;
-    int s = 1;
-    for (; s < n8 && idx >= base + Ns; ++s) {
-        base += Ns;
-        Ns *= 8;
-    }
-    if (s >= n8) return;
-    const long j = idx - base;
+    const long idx = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    long base = 0;
+    int st = 0;
+    for (; st < d.n && idx >= base + d.s[st].Ns; ++st) base += d.s[st].Ns;
+    if (st >= d.n) return;
+    const int R = d.s[st].R;
+    const long Ns = d.s[st].Ns, j = idx - base, D = R * Ns;
     double f[8], tau[8];
     int codes = 0;
     f[0] = 1.0;
     tau[0] = 0.0;
-    for (int t = 1; t < 8; ++t) {
+    for (int t = 1; t < R; ++t) {
         const long q = j * t;
-        const long K = (q + Ns) / (2 * Ns);
-        const long m = q - 2 * Ns * K;
+        const long K = (4 * q + D / 2) / D;
+        const long m = q - K * (D / 4);
         const int k = (int)((4 - (K & 3)) & 3);
         double sn, cs;
-        sincospi((double)m / (double)(4 * Ns), &sn, &cs);
+        sincospi(2.0 * (double)m / (double)D, &sn, &cs);
         f[t] = cs;
         tau[t] = (k & 1) ? sn / cs : -sn / cs;   // tau sigma_t, sigma_t = -1 for odd k
         codes |= k << (2 * (t - 1));
     }
-    double *c = out + (base + j) * 16;
-    for (int t = 1; t < 8; ++t) c[t - 1] = tau[t];
-    for (int t = 0; t < 4; ++t) c[7 + t] = f[t + 4] / f[t];
-    c[11] = f[2];
-    c[12] = f[3] / f[1];
-    c[13] = f[1];
-    c[14] = f[1] * 0.707106781186547524400844362104849039;
-    c[15] = __hiloint2double(0, codes);
+    double *c = out + d.s[st].off + j * gslots(R);
+    if (R == 8) {
+        for (int t = 1; t < 8; ++t) c[t - 1] = tau[t];
+        for (int t = 0; t < 4; ++t) c[7 + t] = f[t + 4] / f[t];
+        c[11] = f[2];
+        c[12] = f[3] / f[1];
+        c[13] = f[1];
+        c[14] = f[1] * 0.707106781186547524400844362104849039;
+        c[15] = __hiloint2double(0, codes);
+    } else if (R == 4) {
+        for (int t = 1; t < 4; ++t) c[t - 1] = tau[t];
+        c[3] = f[2];
+        c[4] = f[3] / f[1];
+        c[5] = f[1];
+        c[6] = __hiloint2double(0, codes);
+        c[7] = 0.0;
+    } else {
+        c[0] = tau[1];
+        c[1] = f[1];
+        c[2] = __hiloint2double(0, codes);
+        c[3] = 0.0;
+    }
 }
 
 // Fills the FMA-form constants of schedule sc at `dst` (just after the M
 // twiddles of an FP64 table, so 16-byte aligned).
 void launch_g8table(const Sched &sc, double2 *dst, cudaStream_t st)
 {
-    int n8 = 0;
-    while (n8 < sc.nst && sc.r[n8] == 8) ++n8;
-    const long entries = (long)(g8_table_doubles(sc) / kG8Slots);
-    if (entries > 0) k_g8table<<<(entries + 127) / 128, 128, 0, st>>>(n8, reinterpret_cast<double *>(dst));
+    GTableDesc d;
+    d.n = 0;
+    long Ns = 1, entries = 0;
+    for (int i = 0; i < sc.nst; ++i) {
+        if (Ns > 1 && gtabled(sc.r[i])) {
+            d.s[d.n].R = sc.r[i];
+            d.s[d.n].Ns = Ns;
+            d.s[d.n].off = (long)gtable_offset(sc, i);
+            ++d.n;
+            entries += Ns;
+        }
+        Ns *= sc.r[i];
+    }
+    if (entries > 0) k_gtable<<<(entries + 127) / 128, 128, 0, st>>>(d, reinterpret_cast<double *>(dst));
 }
 
 // w[m] = exp(-2 pi i m / M) from sincospi in FP64, then rounded or split.
