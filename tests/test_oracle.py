@@ -18,7 +18,8 @@ from paper_1501_04438_gb300 import workloads as wl
 from closed_forms import (coulomb2d_gaussian, coulomb3d_gaussian, coulomb_gaussian_axes_points,
                           dipolar3d_gaussian, ds2d_gaussian, poisson2d_gaussian, power_gaussian)
 
-GOLDEN = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_tables.json")))
+with open(os.path.join(os.path.dirname(__file__), "golden", "paper_tables.json")) as _f:
+    GOLDEN = json.load(_f)
 
 
 def relmax(a, b):
