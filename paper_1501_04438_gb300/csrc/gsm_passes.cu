@@ -359,7 +359,10 @@ struct BatchArgs {
 };
 
 template <class Pol, int PASS, int D>
-__global__ void __launch_bounds__(32 * kBatchMaxLines) k_batch(const __grid_constant__ BatchArgs a)
+// Resident CTAs per SM asked of the compiler: FP64 and double-float 2 (a
+// 128-register cap), FP32 3 (85 registers)
+__global__ void __launch_bounds__(32 * kBatchMaxLines, std::is_same<Pol, F32>::value ? 3 : 2)
+    k_batch(const __grid_constant__ BatchArgs a)
 {
     using io = typename Pol::io_t;
     using tw = typename Pol::tw_t;
