@@ -189,7 +189,12 @@ gsm_status_t gsm_plan_autotune(gsm_plan_t p, void *cuda_stream, char *report, si
 /*
  * Same as gsm_apply with HOST arrays: copies rho to the device, applies, copies
  * u back, and synchronises the stream before returning.  Staging buffers are
- * allocated on the first call and owned by the plan.
+ * allocated on the first call and owned by the plan.  3D plans overlap the
+ * copies with the x passes: the copies run in 8 z-chunks on a stream the plan
+ * creates on the first call, ordered against `cuda_stream` by events (work
+ * queued before on `cuda_stream` completes first).  Copies overlap only from
+ * page-locked (pinned) host memory; pageable arrays are copied synchronously
+ * by the runtime, with the same result.  One host apply per plan at a time.
  */
 gsm_status_t gsm_apply_host(gsm_plan_t p, const void *rho_host, void *u_host, void *cuda_stream);
 
