@@ -106,3 +106,22 @@ def test_missing_library_fails_loudly(tmp_path):
             _abi.load(str(tmp_path / "nope.so"))
     finally:
         _abi._lib = saved
+
+
+def _build_c_client(libpath, out):
+    """Compile and link tests/c/gsm_c_client.c (C99) against include/gsm.h and
+    libgsm.so; returns the gcc result."""
+    cuda = os.environ.get("CUDA_HOME", "/usr/local/cuda")
+    libdir = os.path.dirname(libpath)
+    cmd = ["gcc", "-std=c99", "-Wall", "-Werror", "-O1", os.path.join(ROOT, "tests", "c", "gsm_c_client.c"),
+           "-I", os.path.join(ROOT, "include"), "-I", os.path.join(cuda, "include"), "-o", out,
+           "-L", libdir, "-lgsm", "-Wl,-rpath," + libdir, "-L", os.path.join(cuda, "lib64"), "-lcudart",
+           "-Wl,-rpath," + os.path.join(cuda, "lib64"), "-lm"]
+    return subprocess.run(cmd, capture_output=True, text=True)
+
+
+def test_c_client_builds_against_header_and_library(libpath, tmp_path):
+    """The header is valid C99 and a C program links against the library
+    (no GPU needed to build)."""
+    r = _build_c_client(libpath, str(tmp_path / "client"))
+    assert r.returncode == 0, r.stderr
