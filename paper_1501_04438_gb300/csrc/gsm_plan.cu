@@ -13,6 +13,9 @@
 
 #include <algorithm>
 #include <cmath>
+#include <map>
+#include <mutex>
+#include <tuple>
 #include <vector>
 
 #include "gsm_internal.h"
@@ -515,6 +518,47 @@ __global__ void k_multiplier_dip_full(DipFull dp, const double *__restrict__ mC,
 }  // namespace
 
 // ---------------------------------------------------------------- host side
+// Results of the Gaussian-sum scan (the chosen S and its error), kept for the
+// process: plans of other grid sizes with the same kernel, delta, interval,
+// accuracy target (and beta) reuse them.  The scan is deterministic, so a hit
+// gives what the scan would.
+namespace {
+struct GsKey {
+    int device, kind, S_request;
+    double delta, rmax, eps, beta;
+    bool operator<(const GsKey &o) const
+    {
+        return std::tie(device, kind, S_request, delta, rmax, eps, beta) <
+               std::tie(o.device, o.kind, o.S_request, o.delta, o.rmax, o.eps, o.beta);
+    }
+};
+std::mutex g_gs_mutex;
+std::map<GsKey, std::pair<int, double>> g_gs_cache;
+
+GsKey gs_key(const GsSpec &gs, int S_request, double eps)
+{
+    int dev = 0;
+    cudaGetDevice(&dev);
+    return GsKey{dev, gs.kind, S_request, gs.delta, gs.rmax, eps, gs.beta};
+}
+
+bool gs_cache_lookup(const GsSpec &gs, int S_request, double eps, int *S, double *err)
+{
+    std::lock_guard<std::mutex> lock(g_gs_mutex);
+    auto it = g_gs_cache.find(gs_key(gs, S_request, eps));
+    if (it == g_gs_cache.end()) return false;
+    *S = it->second.first;
+    *err = it->second.second;
+    return true;
+}
+
+void gs_cache_insert(const GsSpec &gs, int S_request, double eps, int S, double err)
+{
+    std::lock_guard<std::mutex> lock(g_gs_mutex);
+    g_gs_cache[gs_key(gs, S_request, eps)] = {S, err};
+}
+}  // namespace
+
 gsm_status_t build_plan_data(Plan *p, cudaStream_t st, const StoredPlanData *stored)
 {
     const int d = p->d;
@@ -551,7 +595,10 @@ gsm_status_t build_plan_data(Plan *p, cudaStream_t st, const StoredPlanData *sto
             set_error("stored plan: Gaussian-sum size does not match its kernel");
             return GSM_ERR_INVALID_ARG;
         }
+    } else if (gs_cache_lookup(gs, p->opt.S, p->eps, &S, &err)) {
+        // the same scan ran for an earlier plan in this process
     } else {
+        const int S_request = S;
         double *d_err = nullptr;
         const int S_first = 4;
         const int count = kSmax - S_first + 1;
@@ -588,6 +635,7 @@ gsm_status_t build_plan_data(Plan *p, cudaStream_t st, const StoredPlanData *sto
             set_error("no Gaussian sum with S <= 500 meets the requested accuracy");
             return GSM_ERR_ACCURACY;
         }
+        gs_cache_insert(gs, S_request, p->eps, S, err);
     }
     p->S = S;
     p->gs_err = err;

@@ -542,3 +542,19 @@ def test_power_closed_form(gsm):
         r = np.sqrt(sum(c * c for c in C))
         u, _ = run(gsm, kernel, np.exp(-r * r / 1.44), 8.0, beta=beta)
         assert relmax(u, power_gaussian(r, 1.2, beta, d)) < tol, kernel
+
+
+def test_gaussian_sum_scan_cache(gsm):
+    """Plans with the same kernel, delta, box shape and accuracy share the scan's
+    result; it equals the terms of a plan that forces the same S, and another
+    accuracy target gives another S."""
+    a = gsm.Plan("coulomb3d", 3.0, (16, 16, 16))
+    b = gsm.Plan("coulomb3d", 7.0, (24, 20, 32))          # cube of another size: same sum
+    c = gsm.Plan("coulomb3d", 7.0, (24, 20, 32), S=a.info()["S"])
+    d = gsm.Plan("coulomb3d", 7.0, (24, 20, 32), gs_eps=1e-10)
+    wa, ta = a.gs_terms()
+    for p in (b, c):
+        w, t = p.gs_terms()
+        assert p.info()["S"] == a.info()["S"] and p.info()["gs_err"] == a.info()["gs_err"]
+        assert np.array_equal(w, wa) and np.array_equal(t, ta)
+    assert d.info()["S"] < a.info()["S"]
