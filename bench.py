@@ -405,7 +405,12 @@ def main():
                 ms = float(np.mean(sm_))
                 uv = vu.double().cpu().numpy()
                 ref = u_oracle if u_oracle is not None else u_gpu
+                vcb = 8 if vp == "fp32" else 16
+                _, vb = apply_model(n, vcb)
+                vb5 = vb + 4 * vcb * (n + 1) * n * n
                 variants[vp] = {"value": n ** 3 / (ms / 1e3) / 1e6, "unit": UNIT, "ms_per_step": ms,
+                                "hbm_frac": vb / (ms / 1e3) / 1e9 / hbm_peak,
+                                "hbm_frac_5pass": vb5 / (ms / 1e3) / 1e9 / hbm_peak,
                                 "rel_err": relmax(uv, ref),
                                 "rel_err_vs": "oracle" if u_oracle is not None else "gpu fp64",
                                 "passes_ms": {PASS_NAMES_3D[p]: float(np.mean(pm_[p])) for p in range(npass)}}
