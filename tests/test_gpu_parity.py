@@ -558,3 +558,33 @@ def test_gaussian_sum_scan_cache(gsm):
         assert p.info()["S"] == a.info()["S"] and p.info()["gs_err"] == a.info()["gs_err"]
         assert np.array_equal(w, wa) and np.array_equal(t, ta)
     assert d.info()["S"] < a.info()["S"]
+
+
+def test_large_cube_512_closed_form(gsm):
+    """512^3 on [-16,16]^3 (h = 1/16, padded length 1024 = 8 8 8 2): too large
+    for the oracle, so sampled points against the erf closed form (Eq. DensGaus
+    with sigma = 1.2), at the resolved floor, and FP32x2 against FP64."""
+    import sys, os
+    sys.path.insert(0, os.path.dirname(__file__))
+    from closed_forms import coulomb3d_gaussian
+    torch = _torch()
+    n, L, sig = 512, 16.0, 1.2
+    ax = torch.tensor(wl.grid_1d(n, L), device="cuda")
+    Z, Y, X = torch.meshgrid(ax, ax, ax, indexing="ij")
+    rho = torch.exp(-(X * X + Y * Y + Z * Z) / sig ** 2)
+    del X, Y, Z
+    plan = gsm.Plan("coulomb3d", L, n)
+    u = plan.apply(rho)
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(51)
+    idx = rng.integers(0, n, (300, 3))
+    idx[:10] = n // 2 - 1 + rng.integers(0, 3, (10, 3))          # near the centre
+    g = wl.grid_1d(n, L)
+    r = np.sqrt(g[idx[:, 0]] ** 2 + g[idx[:, 1]] ** 2 + g[idx[:, 2]] ** 2)
+    got = u[idx[:, 0], idx[:, 1], idx[:, 2]].cpu().numpy()
+    ref = coulomb3d_gaussian(r, sig)
+    assert np.max(np.abs(got - ref)) / np.max(np.abs(ref)) < 1e-13
+    p2 = gsm.Plan("coulomb3d", L, n, precision="fp32x2")
+    u2 = p2.apply(rho)
+    torch.cuda.synchronize()
+    assert float((u2 - u).abs().max() / u.abs().max()) < 1e-12
