@@ -450,7 +450,47 @@ def _cpu_leg(run, points: int, sample: str):
                  "sample": sample, "seconds": dt}
 
 
+def run_suite_sharded(a, rank: int, world: int, local: int):
+    """Config 4 over `world` GPUs: the 48 independent applies split by the LPT
+    rule (partition_batch), each rank applying its share with the grouped
+    launch; no collective on the data path.  Time = max over ranks."""
+    import torch
+    import torch.distributed as dist
+
+    import paper_1501_04438_gb300 as gsm
+    from paper_1501_04438_gb300 import workloads as wl
+
+    torch.cuda.set_device(local)
+    dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(device=dev)
+    flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)
+    specs = wl.batch_specs()
+    mine = gsm.partition_batch([n for n, _ in specs], world)[rank]
+    for prec in ("fp64", "fp32"):
+        dt = torch.float32 if prec == "fp32" else torch.float64
+        plans = [gsm.Plan("coulomb3d", 10.0, specs[i][0], precision=prec, stream=stream) for i in mine]
+        rhos = [torch.tensor(wl.mixture((specs[i][0],) * 3, 10.0, specs[i][1]), dtype=dt, device=dev) for i in mine]
+        outs = [torch.empty_like(r) for r in rhos]
+        dist.barrier()
+        ms = _time_apply(torch, lambda: gsm.apply_batched(plans, rhos, outs, stream=stream), max(3, a.steps),
+                         flush, stream)
+        ms = max_over_ranks(ms, dev)
+        npts = sum(n ** 3 for n, _ in specs)
+        if rank == 0:
+            print(json.dumps({"config": "4 batch48 sharded", "precision": prec, "n_gpus": world,
+                              "partition": "LPT on prod(2n) log2 prod(2n)", "ms": ms,
+                              "Mpts_s": npts / ms / 1e3, "scaling": "strong"}), flush=True)
+        for p in plans:
+            p.destroy()
+    dist.barrier()
+    dist.destroy_process_group()
+
+
 def run_suite(a):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if world > 1:
+        return run_suite_sharded(a, int(os.environ.get("RANK", "0")), world, int(os.environ.get("LOCAL_RANK", "0")))
     import torch
 
     import oracle

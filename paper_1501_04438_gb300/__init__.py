@@ -22,7 +22,8 @@ import numpy as np
 from . import _abi
 from ._abi import GSMError, KERNEL_DIM, KERNELS, PRECISIONS
 
-__all__ = ["Plan", "Batch", "apply", "apply_batched", "GSMApply", "hartree_energy", "fft_lines", "GSMError",
+__all__ = ["Plan", "Batch", "apply", "apply_batched", "partition_batch", "apply_cost", "GSMApply", "hartree_energy",
+           "fft_lines", "GSMError",
            "KERNELS", "PRECISIONS", "library_path"]
 
 
@@ -288,6 +289,33 @@ def apply_batched(plans, rhos, outs=None, stream=None):
     U = (ctypes.c_void_p * count)(*[o.data_ptr() for o in outs])
     _abi.check(_abi.load().gsm_apply_batched(count, H, R, U, _stream_ptr(stream)))
     return outs
+
+
+def apply_cost(n) -> float:
+    """Relative cost of one apply on grid n (an int or a tuple): the padded FFT
+    work, prod(2 n_a) * log2(prod(2 n_a))."""
+    dims = (n,) * 3 if isinstance(n, int) else tuple(n)
+    pts = float(np.prod([2 * v for v in dims]))
+    return pts * float(np.log2(pts))
+
+
+def partition_batch(sizes, world: int):
+    """Split a batch of independent applies over `world` ranks (GPUs) by the
+    longest-processing-time rule: instances in decreasing apply_cost, each to
+    the rank with the least cost so far (ties to the lower rank).  Returns one
+    sorted list of instance indices per rank; no rank's total exceeds the
+    optimum by more than a factor 4/3 - 1/(3 world) (Graham's bound).  The
+    instances share nothing, so a sharded batch needs no collective."""
+    if world < 1:
+        raise ValueError("world must be >= 1")
+    order = sorted(range(len(sizes)), key=lambda i: (-apply_cost(sizes[i]), i))
+    load = [0.0] * world
+    parts = [[] for _ in range(world)]
+    for i in order:
+        r = min(range(world), key=lambda k: (load[k], k))
+        parts[r].append(i)
+        load[r] += apply_cost(sizes[i])
+    return [sorted(p) for p in parts]
 
 
 class Batch:
