@@ -104,6 +104,9 @@ typedef struct {
                                    must be smaller than every box[a] / max box */
     double beta;                /* exponent of GSM_POWER_3D / GSM_POWER_2D, 0 < beta < d
                                    (default 1) */
+    int host_zero_copy;         /* gsm_apply_host with page-locked host arrays: 1 (default)
+                                   the passes read rho and write u in host memory over
+                                   the host link; 0: staged copies */
 } gsm_options_t;
 
 /* Read-only facts about a plan. */
@@ -187,9 +190,13 @@ gsm_status_t gsm_apply_pass(gsm_plan_t p, int pass, const void *rho, void *u, vo
 gsm_status_t gsm_plan_autotune(gsm_plan_t p, void *cuda_stream, char *report, size_t report_len);
 
 /*
- * Same as gsm_apply with HOST arrays: copies rho to the device, applies, copies
- * u back, and synchronises the stream before returning.  Staging buffers are
- * allocated on the first call and owned by the plan.  3D plans overlap the
+ * Same as gsm_apply with HOST arrays, synchronising the stream before it
+ * returns.  When both arrays are page-locked (cudaHostAlloc, cudaHostRegister,
+ * torch pin_memory) and options.host_zero_copy is set, the first pass reads rho
+ * and the last writes u directly in host memory through their mapped device
+ * addresses: no copies.  Otherwise rho is copied to the device, applied, and u
+ * copied back; staging buffers are allocated on the first such call and owned
+ * by the plan.  In that case 3D plans overlap the
  * copies with the x passes: the copies run in 8 z-chunks on a stream the plan
  * creates on the first call, ordered against `cuda_stream` by events (work
  * queued before on `cuda_stream` completes first).  Copies overlap only from

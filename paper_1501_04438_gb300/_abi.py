@@ -26,7 +26,7 @@ EXPORTS = ["gsm_default_options", "gsm_plan", "gsm_apply", "gsm_apply_pass", "gs
 class Options(ctypes.Structure):
     _fields_ = [("delta", ctypes.c_double), ("S", ctypes.c_int), ("precision", ctypes.c_int),
                 ("dip_n", ctypes.c_double * 3), ("dip_m", ctypes.c_double * 3), ("debug", ctypes.c_int),
-                ("box", ctypes.c_double * 3), ("beta", ctypes.c_double)]
+                ("box", ctypes.c_double * 3), ("beta", ctypes.c_double), ("host_zero_copy", ctypes.c_int)]
 
 
 class PlanInfo(ctypes.Structure):

@@ -77,6 +77,7 @@ void gsm_default_options(gsm_options_t *opt)
     opt->dip_m[2] = 1.0;
     opt->debug = 0;
     opt->beta = 1.0;
+    opt->host_zero_copy = 1;
 }
 
 const char *gsm_status_string(gsm_status_t s)
@@ -458,6 +459,22 @@ gsm_status_t gsm_apply_host(gsm_plan_t h, const void *rho_host, void *u_host, vo
     }
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
     const size_t bytes = grid_points(p) * io_bytes(p);
+    // Page-locked host arrays are mapped into the device's address space: the
+    // x passes then read rho and write u in host memory themselves, over the
+    // coherent host link, with no separate copies.  Anything else (pageable
+    // memory) goes through the staging buffers below.
+    cudaPointerAttributes ai, ao;
+    const bool in_mapped = cudaPointerGetAttributes(&ai, rho_host) == cudaSuccess && ai.type == cudaMemoryTypeHost &&
+                           ai.devicePointer != nullptr;
+    const bool out_mapped = cudaPointerGetAttributes(&ao, u_host) == cudaSuccess && ao.type == cudaMemoryTypeHost &&
+                            ao.devicePointer != nullptr;
+    cudaGetLastError();   // an unregistered pointer may leave an error behind on older runtimes
+    if (in_mapped && out_mapped && p->opt.host_zero_copy != 0) {
+        gsm_status_t s = launch_apply(p, ai.devicePointer, ao.devicePointer, st);
+        if (s != GSM_OK) return s;
+        GSM_CUDA_TRY(cudaStreamSynchronize(st));
+        return GSM_OK;
+    }
     if (!p->d_stage_in) {
         GSM_CUDA_TRY(cudaMalloc(&p->d_stage_in, bytes));
         GSM_CUDA_TRY(cudaMalloc(&p->d_stage_out, bytes));

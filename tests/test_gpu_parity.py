@@ -211,21 +211,28 @@ def test_invalid_arguments_raise_status(gsm):
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32x2", "fp32"])
 def test_apply_host_equals_device(gsm, precision):
-    """The host apply (3D: copies pipelined with the x passes in z-chunks) gives
-    the device apply's bits, for chunkings with ragged, single-slab and many
-    slabs per chunk, repeated calls, and 2D."""
+    """The host apply gives the device apply's bits: pageable arrays (staged
+    copies, in 3D pipelined with the x passes in z-chunks: ragged, single-slab
+    and many slabs per chunk), page-locked arrays read and written in place
+    (zero copy) or staged, repeated calls, and 2D."""
     torch = _torch()
     dt = torch.float32 if precision == "fp32" else torch.float64
     npd = np.float32 if precision == "fp32" else np.float64
     for kernel, n in (("coulomb3d", (40, 40, 40)), ("coulomb3d", (16, 12, 20)), ("dipolar3d", (12, 10, 8)),
                       ("poisson2d", (48, 30))):
         rho = np.random.default_rng(17).standard_normal(n[::-1]).astype(npd)
-        plan = gsm.Plan(kernel, 5.0, n, precision=precision)
-        for _ in range(2):
-            uh = plan.apply_host(rho)
-            ud = plan.apply(torch.tensor(rho, dtype=dt, device="cuda")).cpu().numpy()
-            torch.cuda.synchronize()
-            assert np.array_equal(uh, ud), (kernel, n)
+        ud = None
+        for zero_copy in (True, False):
+            plan = gsm.Plan(kernel, 5.0, n, precision=precision, host_zero_copy=zero_copy)
+            if ud is None:
+                ud = plan.apply(torch.tensor(rho, dtype=dt, device="cuda")).cpu().numpy()
+                torch.cuda.synchronize()
+            for _ in range(2):
+                assert np.array_equal(plan.apply_host(rho), ud), (kernel, n)      # pageable: staged copies
+                pin_in = torch.tensor(rho, dtype=dt).pin_memory()
+                pin_out = torch.empty_like(pin_in).pin_memory()
+                plan.apply_host(pin_in.numpy(), pin_out.numpy())                  # page-locked
+                assert np.array_equal(pin_out.numpy(), ud), (kernel, n, zero_copy)
 
 
 def test_batched_equals_single(gsm):
