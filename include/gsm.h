@@ -96,7 +96,9 @@ typedef struct {
     double dip_n[3];            /* dipolar unit vectors n, m (default e_z, e_z); any */
     double dip_m[3];            /* directions (both along one axis: octant multiplier,
                                    otherwise a half-spectrum multiplier table) */
-    int debug;                  /* reserved, 0 */
+    int debug;                  /* 0; bit 0 set: FP32 plans use the shared-memory FFT engine
+                                   for the conv pass even where the register-resident
+                                   kernel applies (conv length 512) */
     double box[3];              /* rectangular box (Sec. 2.5, Eq. tensor_ani): if all
                                    d entries are > 0, axis a spans [-box[a], box[a]]
                                    and L is ignored; all 0 (default): [-L, L]^d.  The

@@ -66,11 +66,13 @@ class Plan:
                 0 < beta < d
     host_zero_copy : apply_host with page-locked arrays reads and writes host
                 memory from the passes (True) or stages copies (False)
+    debug     : bit 0: FP32 conv through the shared-memory FFT engine even where
+                the register-resident kernel applies (for comparisons)
     """
 
     def __init__(self, kernel: str, L: float, n, gs_eps: float = 0.0, precision: str = "fp64",
                  delta: float = 1e-3, S: int = 0, dip_n=(0.0, 0.0, 1.0), dip_m=(0.0, 0.0, 1.0),
-                 stream=None, box=None, beta: float = 1.0, host_zero_copy: bool = True):
+                 stream=None, box=None, beta: float = 1.0, host_zero_copy: bool = True, debug: int = 0):
         lib = _abi.load()
         if kernel not in KERNELS:
             raise ValueError(f"unknown kernel {kernel!r}")
@@ -89,6 +91,7 @@ class Plan:
         opt.precision = PRECISIONS[precision]
         opt.beta = float(beta)
         opt.host_zero_copy = 1 if host_zero_copy else 0
+        opt.debug = int(debug)
         for i in range(3):
             opt.dip_n[i] = float(dip_n[i])
             opt.dip_m[i] = float(dip_m[i])

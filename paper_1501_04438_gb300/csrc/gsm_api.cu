@@ -196,6 +196,7 @@ static gsm_status_t create_plan(gsm_plan_t *out, gsm_kernel_t kind, int d, doubl
     p->L = L;
     for (int a = 0; a < 3; ++a) p->eta[a] = eta[a];
     p->opt = o;
+    p->rr_conv = (o.debug & 1) == 0;
     p->dip_axis = dip_axis;
     const bool log_kernel = kind == GSM_POISSON_2D || kind == GSM_DAVEY_STEWARTSON_2D;
     p->eps = gs_eps > 0.0 ? gs_eps : (log_kernel ? 1e-13 : 2e-15);

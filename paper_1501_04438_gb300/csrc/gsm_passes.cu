@@ -693,6 +693,12 @@ void launch_pass_t(const Plan *p, int pass, const void *rho_v, void *u_v, cudaSt
         });
     } else if (p->d == 2) {
         const PassCfg &c = p->cfg_conv;
+        if constexpr (std::is_same<Pol, F32>::value) {
+            if (p->M[1] == 512 && p->rr_conv) {
+                launch_conv_rr512_f32(W1, mult, hx, 0, 1, ny + 1, p->mult_full, twy, st);
+                return;
+            }
+        }
         with_emax(c, [&](auto E) {
             k_conv<Pol, E()><<<(hx + c.nl - 1) / c.nl, c.nthr, c.smem, st>>>(W1, mult, hx, ny, 0, 1, ny + 1,
                                                                           p->sched[1], c.nl, c.gthr, twy,
@@ -710,6 +716,12 @@ void launch_pass_t(const Plan *p, int pass, const void *rho_v, void *u_v, cudaSt
         } else if (pass == 2) {
             const PassCfg &c = p->cfg_conv;
             const int nlines = hx * My;
+            if constexpr (std::is_same<Pol, F32>::value) {
+                if (p->M[2] == 512 && p->rr_conv) {
+                    launch_conv_rr512_f32(W2, mult, nlines, 1, My, ny + 1, p->mult_full, twz, st);
+                    return;
+                }
+            }
             with_emax(c, [&](auto E) {
                 k_conv<Pol, E()><<<(nlines + c.nl - 1) / c.nl, c.nthr, c.smem, st>>>(
                     W2, mult, nlines, nz, 1, My, ny + 1, p->sched[2], c.nl, c.gthr, twz, p->mult_full ? 1 : 0);

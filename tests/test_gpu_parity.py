@@ -595,3 +595,26 @@ def test_large_cube_512_closed_form(gsm):
     u2 = p2.apply(rho)
     torch.cuda.synchronize()
     assert float((u2 - u).abs().max() / u.abs().max()) < 1e-12
+
+
+@pytest.mark.parametrize("kernel,n,L,kw", [
+    ("coulomb3d", (256, 256, 256), 12.0, {}),
+    ("coulomb3d", (20, 24, 256), 6.0, {}),
+    ("dipolar3d", (16, 12, 256), 6.0, dict(dip_n=(0.6, 0.0, 0.8), dip_m=(0.0, 0.8, 0.6))),
+    ("poisson2d", (40, 256), 8.0, {}),
+], ids=["cube256", "lines256", "dipolar_full256", "2d256"])
+def test_fp32_register_resident_conv(gsm, kernel, n, L, kw):
+    """FP32 plans with conv length 512 use the register-resident conv kernel: against
+    the oracle at the FP32 tolerance, and against the shared-memory engine (debug
+    bit 0) to the same order, including the half-spectrum multiplier (general
+    dipolar directions) and 2D."""
+    torch = _torch()
+    if n == (256, 256, 256):
+        rho = wl.coulomb3d_mixture(256, L)
+    else:
+        rho = np.random.default_rng(61).standard_normal(n[::-1])
+    u, plan = run(gsm, kernel, rho, L, "fp32", **kw)
+    u_eng, _ = run(gsm, kernel, rho, L, "fp32", debug=1, **kw)
+    uo, _ = oracle.apply(kernel, rho, L, taylor_mode=1, S=plan.info()["S"], **kw)
+    assert relmax(u, uo) < TOL["fp32"], relmax(u, uo)
+    assert relmax(u, u_eng) < TOL["fp32"], relmax(u, u_eng)
