@@ -97,8 +97,8 @@ typedef struct {
     double dip_m[3];            /* directions (both along one axis: octant multiplier,
                                    otherwise a half-spectrum multiplier table) */
     int debug;                  /* 0; bit 0 set: FP32 plans use the shared-memory FFT engine
-                                   for the conv pass even where the register-resident
-                                   kernel applies (conv length 512) */
+                                   for the y and conv passes even where the register-
+                                   resident kernels apply (padded length 512) */
     double box[3];              /* rectangular box (Sec. 2.5, Eq. tensor_ani): if all
                                    d entries are > 0, axis a spans [-box[a], box[a]]
                                    and L is ignored; all 0 (default): [-L, L]^d.  The

@@ -158,8 +158,64 @@ __device__ __forceinline__ void dft16(cx<float> *v)
 constexpr int kRrLinesPerCta = 16;           // 16 lines x 16 threads = 256 threads
 constexpr int kRrRow = 17;                   // row pitch of the transpose buffer (bank spread)
 constexpr int kRrLineElems = 32 * kRrRow;    // one line's transpose buffer
+constexpr size_t kRrSmem = sizeof(float2) * kRrLinesPerCta * kRrLineElems;
 
-// One line of padded length 512 (n = 256 stored values) per 16 threads.
+// The 512-point transforms of one line by its 16 threads, in pieces (S is the
+// line's transpose buffer; each thread reads and writes only its own rows
+// k1 = t and t + 16, so row work needs no barrier):
+//   fwd512_cols: on entry v[m] = x[t + 16 m], m < 16 (the rest is zero
+//     padding); DFT32 over m, twiddle w512^(t k1), to S (column t), barrier.
+//   fwd512_row: r[k2] = Y[k1 + 32 k2] for row k1 (a 16-point DFT of the row).
+//   inv512_row: r holds Y[k1 + 32 k2]; inverse DFT16, twiddle, to S (row k1).
+//   inv512_cols: barrier, column t from S, inverse DFT32 keeping the outputs
+//     b < 16: v[b] = z[t + 16 b].
+__device__ __forceinline__ void fwd512_cols(cx<float> *v, float2 *S, int t, const float2 *__restrict__ tw)
+{
+    dft32<true, true, false>(v);
+#pragma unroll
+    for (int k1 = 1; k1 < 32; ++k1) {
+        const float2 q = tw[t * k1];
+        v[k1] = cmul(v[k1], cx<float>{q.x, q.y});
+    }
+#pragma unroll
+    for (int k1 = 0; k1 < 32; ++k1) S[k1 * kRrRow + t] = make_float2(v[k1].re, v[k1].im);
+    __syncwarp();
+}
+
+__device__ __forceinline__ void fwd512_row(cx<float> *r, const float2 *S, int k1)
+{
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+        const float2 x = S[k1 * kRrRow + i];
+        r[i] = {x.x, x.y};
+    }
+    dft16<true>(r);
+}
+
+__device__ __forceinline__ void inv512_row(cx<float> *r, float2 *S, int k1, const float2 *__restrict__ tw)
+{
+    dft16<false>(r);
+#pragma unroll
+    for (int a = 1; a < 16; ++a) {
+        const float2 q = tw[a * k1];
+        r[a] = cmulc(r[a], cx<float>{q.x, q.y});
+    }
+#pragma unroll
+    for (int a = 0; a < 16; ++a) S[k1 * kRrRow + a] = make_float2(r[a].re, r[a].im);
+}
+
+__device__ __forceinline__ void inv512_cols(cx<float> *v, const float2 *S, int t)
+{
+    __syncwarp();
+#pragma unroll
+    for (int k1 = 0; k1 < 32; ++k1) {
+        const float2 x = S[k1 * kRrRow + t];
+        v[k1] = {x.x, x.y};
+    }
+    dft32<false, false, true>(v);
+}
+
+// Conv pass: one line of padded length 512 (n = 256 stored values) per 16 threads.
 // Multiplier of frequency k: mrow[k] (full) or mrow[min(k, 512 - k)].
 __global__ void __launch_bounds__(16 * kRrLinesPerCta, 2)
     k_conv_rr512(float2 *__restrict__ W, const float *__restrict__ mult, int nlines, int is3d, int My, int ny1,
@@ -182,69 +238,122 @@ __global__ void __launch_bounds__(16 * kRrLinesPerCta, 2)
     } else {
         mrow = mult + (size_t)ln * 257;
     }
-
-    // forward, step 1: DFT32 over m of x[t + 16 m] (m < 16 stored), twiddle w512^(t k1)
     cx<float> v[32];
 #pragma unroll
     for (int m = 0; m < 16; ++m) {
         const float2 x = active ? w[t + 16 * m] : make_float2(0.f, 0.f);
         v[m] = {x.x, x.y};
     }
-    dft32<true, true, false>(v);
-#pragma unroll
-    for (int k1 = 1; k1 < 32; ++k1) {
-        const float2 q = tw[t * k1];
-        v[k1] = cmul(v[k1], cx<float>{q.x, q.y});
-    }
-#pragma unroll
-    for (int k1 = 0; k1 < 32; ++k1) S[k1 * kRrRow + t] = make_float2(v[k1].re, v[k1].im);
-    __syncwarp();
-
-    // forward, step 2: rows k1 = t and t + 16, DFT16 over the 16 threads' values;
-    // multiplier; inverse step 2: DFT16 over k2, twiddle conj w512^(a k1)
+    fwd512_cols(v, S, t, tw);
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
         const int k1 = t + 16 * h;
         cx<float> *r = v + 16 * h;
-#pragma unroll
-        for (int i = 0; i < 16; ++i) {
-            const float2 x = S[k1 * kRrRow + i];
-            r[i] = {x.x, x.y};
-        }
-        dft16<true>(r);
+        fwd512_row(r, S, k1);
 #pragma unroll
         for (int k2 = 0; k2 < 16; ++k2) {
             const int k = k1 + 32 * k2;
             const float m = active ? mrow[full ? k : min(k, 512 - k)] : 0.f;
             r[k2] = {r[k2].re * m, r[k2].im * m};
         }
-        dft16<false>(r);
-#pragma unroll
-        for (int a = 1; a < 16; ++a) {
-            const float2 q = tw[a * k1];
-            r[a] = cmulc(r[a], cx<float>{q.x, q.y});
-        }
+        inv512_row(r, S, k1, tw);
     }
-    __syncwarp();
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-        const int k1 = t + 16 * h;
-#pragma unroll
-        for (int a = 0; a < 16; ++a) S[k1 * kRrRow + a] = make_float2(v[16 * h + a].re, v[16 * h + a].im);
-    }
-    __syncwarp();
-
-    // inverse, step 1: thread a takes column a, inverse DFT32 over k1, outputs b < 16
-#pragma unroll
-    for (int k1 = 0; k1 < 32; ++k1) {
-        const float2 x = S[k1 * kRrRow + t];
-        v[k1] = {x.x, x.y};
-    }
-    dft32<false, false, true>(v);
+    inv512_cols(v, S, t);
     if (active) {
 #pragma unroll
         for (int b = 0; b < 16; ++b) w[t + 16 * b] = make_float2(v[b].re, v[b].im);
     }
+}
+
+// 3D y-forward pass, ny = 256 (My = 512): W1[z][kx][y] -> W2[kx][ky][z].  CTA
+// (bx, kx) takes z = 16 bx .. 16 bx + 15; the outputs go through shared memory
+// (row ky of 16 z values, pitch 17) so that each ky row is written as 128
+// contiguous bytes.  The staging buffer is the transpose buffers' space.
+__global__ void __launch_bounds__(16 * kRrLinesPerCta, 2)
+    k_yf_rr512(const float2 *__restrict__ W1, float2 *__restrict__ W2, int nz, int hx, const float2 *__restrict__ tw)
+{
+    extern __shared__ float2 sbuf[];
+    const int t = threadIdx.x & 15;
+    const int l = threadIdx.x >> 4;
+    const int kx = blockIdx.y;
+    const int z0 = blockIdx.x * kRrLinesPerCta;
+    const int z = z0 + l;
+    const bool active = z < nz;
+    float2 *S = sbuf + l * kRrLineElems;
+    const float2 *in = W1 + ((size_t)(active ? z : 0) * hx + kx) * 256;
+    cx<float> v[32];
+#pragma unroll
+    for (int m = 0; m < 16; ++m) {
+        const float2 x = active ? in[t + 16 * m] : make_float2(0.f, 0.f);
+        v[m] = {x.x, x.y};
+    }
+    fwd512_cols(v, S, t, tw);
+    fwd512_row(v, S, t);
+    fwd512_row(v + 16, S, t + 16);
+    __syncthreads();                      // every line done with its transpose buffer
+#pragma unroll
+    for (int h = 0; h < 2; ++h)
+#pragma unroll
+        for (int k2 = 0; k2 < 16; ++k2) {
+            const int k = t + 16 * h + 32 * k2;
+            sbuf[k * kRrRow + l] = make_float2(v[16 * h + k2].re, v[16 * h + k2].im);
+        }
+    __syncthreads();
+    float2 *out = W2 + (size_t)kx * 512 * nz;
+    for (int i = threadIdx.x; i < 512 * 16; i += blockDim.x) {
+        const int ky = i >> 4, zz = z0 + (i & 15);
+        if (zz < nz) out[(size_t)ky * nz + zz] = sbuf[ky * kRrRow + (i & 15)];
+    }
+}
+
+// 3D y-inverse pass, ny = 256: W2[kx][ky][z] -> W1[z][kx][y] (crop to y < 256).
+__global__ void __launch_bounds__(16 * kRrLinesPerCta, 2)
+    k_yi_rr512(const float2 *__restrict__ W2, float2 *__restrict__ W1, int nz, int hx, const float2 *__restrict__ tw)
+{
+    extern __shared__ float2 sbuf[];
+    const int t = threadIdx.x & 15;
+    const int l = threadIdx.x >> 4;
+    const int kx = blockIdx.y;
+    const int z0 = blockIdx.x * kRrLinesPerCta;
+    const int z = z0 + l;
+    const float2 *in = W2 + (size_t)kx * 512 * nz;
+    for (int i = threadIdx.x; i < 512 * 16; i += blockDim.x) {
+        const int ky = i >> 4, zz = z0 + (i & 15);
+        sbuf[ky * kRrRow + (i & 15)] = zz < nz ? in[(size_t)ky * nz + zz] : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+    cx<float> v[32];
+#pragma unroll
+    for (int h = 0; h < 2; ++h)
+#pragma unroll
+        for (int k2 = 0; k2 < 16; ++k2) {
+            const float2 x = sbuf[(t + 16 * h + 32 * k2) * kRrRow + l];
+            v[16 * h + k2] = {x.x, x.y};
+        }
+    __syncthreads();                      // the buffer becomes the lines' transpose buffers
+    float2 *S = sbuf + l * kRrLineElems;
+    inv512_row(v, S, t, tw);
+    inv512_row(v + 16, S, t + 16, tw);
+    inv512_cols(v, S, t);
+    if (z < nz) {
+        float2 *out = W1 + ((size_t)z * hx + kx) * 256;
+#pragma unroll
+        for (int b = 0; b < 16; ++b) out[t + 16 * b] = make_float2(v[b].re, v[b].im);
+    }
+}
+
+// Raise the kernel's dynamic shared-memory limit to kRrSmem once per device;
+// `raised` is the kernel's own flag array (the kernels share a function type).
+template <class K>
+cudaError_t raise_rr(K kernel, bool *raised)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev >= 0 && dev < 64 && raised[dev]) return cudaSuccess;
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRrSmem);
+    if (e == cudaSuccess && dev >= 0 && dev < 64) raised[dev] = true;
+    return e;
 }
 
 }  // namespace
@@ -253,20 +362,34 @@ __global__ void __launch_bounds__(16 * kRrLinesPerCta, 2)
 gsm_status_t launch_conv_rr512_f32(void *W, const void *mult, int nlines, int is3d, int My, int ny1, bool full,
                                    const void *tw, cudaStream_t st)
 {
+    static bool raised[64] = {};
+    GSM_CUDA_TRY(raise_rr(k_conv_rr512, raised));
     const int blocks = (nlines + kRrLinesPerCta - 1) / kRrLinesPerCta;
-    const size_t smem = sizeof(float2) * kRrLinesPerCta * kRrLineElems;
-    static bool raised[64] = {};   // per device; setting it twice is harmless
-    int dev = 0;
-    GSM_CUDA_TRY(cudaGetDevice(&dev));
-    if (dev < 0 || dev >= 64 || !raised[dev]) {
-        GSM_CUDA_TRY(cudaFuncSetAttribute(k_conv_rr512, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        if (dev >= 0 && dev < 64) raised[dev] = true;
+    k_conv_rr512<<<blocks, 16 * kRrLinesPerCta, kRrSmem, st>>>(static_cast<float2 *>(W),
+                                                               static_cast<const float *>(mult), nlines, is3d, My,
+                                                               ny1, full ? 1 : 0, static_cast<const float2 *>(tw));
+    return GSM_OK;   // a launch error stays pending for the caller's check
+}
+
+// y passes of a 3D FP32 plan with ny = 256: forward (W1 -> W2) or inverse (W2 -> W1).
+gsm_status_t launch_y_rr512_f32(bool inverse, const void *in, void *out, int nz, int hx, const void *tw,
+                                cudaStream_t st)
+{
+    dim3 g((nz + kRrLinesPerCta - 1) / kRrLinesPerCta, hx);
+    if (!inverse) {
+        static bool raised_f[64] = {};
+        GSM_CUDA_TRY(raise_rr(k_yf_rr512, raised_f));
+        k_yf_rr512<<<g, 16 * kRrLinesPerCta, kRrSmem, st>>>(static_cast<const float2 *>(in),
+                                                            static_cast<float2 *>(out), nz, hx,
+                                                            static_cast<const float2 *>(tw));
+    } else {
+        static bool raised_i[64] = {};
+        GSM_CUDA_TRY(raise_rr(k_yi_rr512, raised_i));
+        k_yi_rr512<<<g, 16 * kRrLinesPerCta, kRrSmem, st>>>(static_cast<const float2 *>(in),
+                                                            static_cast<float2 *>(out), nz, hx,
+                                                            static_cast<const float2 *>(tw));
     }
-    k_conv_rr512<<<blocks, 16 * kRrLinesPerCta, smem, st>>>(static_cast<float2 *>(W), static_cast<const float *>(mult),
-                                                         nlines, is3d, My, ny1, full ? 1 : 0,
-                                                         static_cast<const float2 *>(tw));
-    GSM_CUDA_TRY(cudaGetLastError());
-    return GSM_OK;
+    return GSM_OK;   // a launch error stays pending for the caller's check
 }
 
 }  // namespace gsm

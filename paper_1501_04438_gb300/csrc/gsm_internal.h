@@ -57,7 +57,7 @@ struct Plan {
     size_t mult_elems = 0;         // octant entries (FP64 tables)
     size_t mult_elems_pass = 0;    // entries of the pass-precision table
     bool mult_full = false;        // pass table covers the half spectrum (general dipolar)
-    bool rr_conv = true;           // FP32, conv length 512: the register-resident conv kernel
+    bool rr_conv = true;           // FP32, padded length 512: the register-resident y and conv kernels
     void *d_stage_in = nullptr, *d_stage_out = nullptr;   // gsm_apply_host staging
     cudaStream_t copy_stream = nullptr;                    // gsm_apply_host copies (3D)
     cudaEvent_t copy_ev[2 * 8 + 2] = {};                   // chunk events of that pipeline
@@ -99,6 +99,9 @@ constexpr int kHostChunks = 8;       // z-chunks of the pipelined host apply
 // conv pass of FP32 plans with padded conv length 512, register-resident (gsm_conv_rr.cu)
 gsm_status_t launch_conv_rr512_f32(void *W, const void *mult, int nlines, int is3d, int My, int ny1, bool full,
                                    const void *tw, cudaStream_t st);
+// y passes of 3D FP32 plans with ny = 256 (forward W1 -> W2, inverse W2 -> W1), register-resident
+gsm_status_t launch_y_rr512_f32(bool inverse, const void *in, void *out, int nz, int hx, const void *tw,
+                                cudaStream_t st);
 gsm_status_t autotune_plan(Plan *p, cudaStream_t st, std::string *report);
 // set the launch shape of one pass (nl lines per CTA, emax elements per thread)
 gsm_status_t set_pass_shape(Plan *p, int pass, int nl, int emax);

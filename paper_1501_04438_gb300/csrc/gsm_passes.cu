@@ -708,6 +708,12 @@ void launch_pass_t(const Plan *p, int pass, const void *rho_v, void *u_v, cudaSt
         const tw *twz = static_cast<const tw *>(p->d_tw[2]);
         const int My = p->M[1];
         if (pass == 1) {
+            if constexpr (std::is_same<Pol, F32>::value) {
+                if (p->M[1] == 512 && p->rr_conv) {
+                    launch_y_rr512_f32(false, W1, W2, nz, hx, twy, st);
+                    return;
+                }
+            }
             const PassCfg &c = p->cfg_yf;
             dim3 g((nz + c.nl - 1) / c.nl, hx);
             with_emax(c, [&](auto E) {
@@ -727,6 +733,12 @@ void launch_pass_t(const Plan *p, int pass, const void *rho_v, void *u_v, cudaSt
                     W2, mult, nlines, nz, 1, My, ny + 1, p->sched[2], c.nl, c.gthr, twz, p->mult_full ? 1 : 0);
             });
         } else {
+            if constexpr (std::is_same<Pol, F32>::value) {
+                if (p->M[1] == 512 && p->rr_conv) {
+                    launch_y_rr512_f32(true, W2, W1, nz, hx, twy, st);
+                    return;
+                }
+            }
             const PassCfg &c = p->cfg_yi;
             dim3 g((nz + c.nl - 1) / c.nl, hx);
             with_emax(c, [&](auto E) {

@@ -602,9 +602,12 @@ def test_large_cube_512_closed_form(gsm):
     ("coulomb3d", (20, 24, 256), 6.0, {}),
     ("dipolar3d", (16, 12, 256), 6.0, dict(dip_n=(0.6, 0.0, 0.8), dip_m=(0.0, 0.8, 0.6))),
     ("poisson2d", (40, 256), 8.0, {}),
-], ids=["cube256", "lines256", "dipolar_full256", "2d256"])
+    ("coulomb3d", (24, 256, 40), 6.0, {}),
+    ("coulomb3d", (16, 256, 256), 6.0, {}),
+], ids=["cube256", "lines256", "dipolar_full256", "2d256", "y256", "y256z256"])
 def test_fp32_register_resident_conv(gsm, kernel, n, L, kw):
-    """FP32 plans with conv length 512 use the register-resident conv kernel: against
+    """FP32 plans with padded length 512 in y or in the conv direction use the
+    register-resident kernels (nz = 40: a ragged last CTA of z-lines): against
     the oracle at the FP32 tolerance, and against the shared-memory engine (debug
     bit 0) to the same order, including the half-spectrum multiplier (general
     dipolar directions) and 2D."""
