@@ -97,8 +97,8 @@ typedef struct {
     double dip_m[3];            /* directions (both along one axis: octant multiplier,
                                    otherwise a half-spectrum multiplier table) */
     int debug;                  /* 0; bit 0 set: FP32 plans use the shared-memory FFT engine
-                                   for the y and conv passes even where the register-
-                                   resident kernels apply (padded length 512) */
+                                   in every pass even where the register-resident kernels
+                                   apply (padded length 512) */
     double box[3];              /* rectangular box (Sec. 2.5, Eq. tensor_ani): if all
                                    d entries are > 0, axis a spans [-box[a], box[a]]
                                    and L is ignored; all 0 (default): [-L, L]^d.  The
@@ -213,7 +213,9 @@ gsm_status_t gsm_apply_host(gsm_plan_t p, const void *rho_host, void *u_host, vo
  * but must be distinct handles.  Plans whose padded lengths are all <= 512
  * are grouped by precision and dimension: each pass is ONE launch over up to
  * 48 instances of different sizes (one warp per FFT line, one CTA shape for
- * all sizes); other plans are applied one by one.  The results are the same
+ * all sizes); other plans, and FP32 plans with a padded length of exactly 512
+ * (which use register-resident kernels of their own), are applied one by one.
+ * The results are the same
  * bits as gsm_apply's.  Errors as in gsm_apply; nothing is launched if any
  * argument is invalid.  (No counterpart in the paper, which treats one
  * density at a time.)

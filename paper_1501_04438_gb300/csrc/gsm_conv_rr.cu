@@ -342,16 +342,126 @@ __global__ void __launch_bounds__(16 * kRrLinesPerCta, 2)
     }
 }
 
+// x passes, nx = 256 (Mx = 512): 8 complex lines (16 real rows) per CTA of 128
+// threads.  Shared memory: the lines' transpose buffers, then the staging
+// buffer of the transposed side W1[z][kx][y] (257 rows kx of 16 y, pitch 17).
+constexpr int kRrXLines = 8;
+constexpr int kRrXPitch = 17;
+constexpr size_t kRrXSmem = sizeof(float2) * (kRrXLines * kRrLineElems + 257 * kRrXPitch);
+
+// x forward: rows y, y + 1 of rho form one complex line Z; after the transform
+// 2 A[k] = Z[k] + conj Z[-k], 2 B[k] = -i (Z[k] - conj Z[-k]) for k = 0..256
+// (the factor 2 is removed by the multiplier), written to W1[z][k][y].
+__global__ void __launch_bounds__(16 * kRrXLines, 3)
+    k_xf_rr512(const float *__restrict__ rho, float2 *__restrict__ W1, int ny, const float2 *__restrict__ tw)
+{
+    extern __shared__ float2 sbuf[];
+    const int t = threadIdx.x & 15;
+    const int l = threadIdx.x >> 4;
+    const int z = blockIdx.y;
+    const int y0 = blockIdx.x * 2 * kRrXLines;
+    const int ya = y0 + 2 * l;
+    float2 *S = sbuf + l * kRrLineElems;
+    float2 *T = sbuf + kRrXLines * kRrLineElems;
+    const float *slab = rho + (size_t)z * ny * 256;
+    cx<float> v[32];
+#pragma unroll
+    for (int m = 0; m < 16; ++m) {
+        const float a = ya < ny ? slab[(size_t)ya * 256 + t + 16 * m] : 0.f;
+        const float b = ya + 1 < ny ? slab[(size_t)(ya + 1) * 256 + t + 16 * m] : 0.f;
+        v[m] = {a, b};
+    }
+    fwd512_cols(v, S, t, tw);
+    fwd512_row(v, S, t);
+    fwd512_row(v + 16, S, t + 16);
+    __syncwarp();                          // rows read: the buffer takes Z in natural order
+#pragma unroll
+    for (int h = 0; h < 2; ++h)
+#pragma unroll
+        for (int k2 = 0; k2 < 16; ++k2) S[t + 16 * h + 32 * k2] = make_float2(v[16 * h + k2].re, v[16 * h + k2].im);
+    __syncwarp();
+    for (int k = t; k <= 256; k += 16) {
+        const float2 zk = S[k], zm = S[(512 - k) & 511];
+        const cx<float> p = {zk.x, zk.y}, q = {zm.x, -zm.y};   // Z[k], conj Z[-k]
+        const cx<float> A = cadd(p, q), B = cmul_negi(csub(p, q));
+        T[k * kRrXPitch + 2 * l] = make_float2(A.re, A.im);
+        T[k * kRrXPitch + 2 * l + 1] = make_float2(B.re, B.im);
+    }
+    __syncthreads();
+    float2 *out = W1 + (size_t)z * 257 * ny;
+    for (int i = threadIdx.x; i < 257 * 16; i += blockDim.x) {
+        const int k = i >> 4, r = i & 15;
+        if (y0 + r < ny) out[(size_t)k * ny + y0 + r] = T[k * kRrXPitch + r];
+    }
+}
+
+// x inverse: Z[k] = A + i B, Z[512 - k] = conj A + i conj B (A, B real at k = 0
+// and 256), inverse transform, real part to row y and imaginary part to row y + 1.
+__global__ void __launch_bounds__(16 * kRrXLines, 3)
+    k_xi_rr512(const float2 *__restrict__ W1, float *__restrict__ u, int ny, const float2 *__restrict__ tw)
+{
+    extern __shared__ float2 sbuf[];
+    const int t = threadIdx.x & 15;
+    const int l = threadIdx.x >> 4;
+    const int z = blockIdx.y;
+    const int y0 = blockIdx.x * 2 * kRrXLines;
+    const int ya = y0 + 2 * l;
+    float2 *S = sbuf + l * kRrLineElems;
+    float2 *T = sbuf + kRrXLines * kRrLineElems;
+    const float2 *in = W1 + (size_t)z * 257 * ny;
+    for (int i = threadIdx.x; i < 257 * 16; i += blockDim.x) {
+        const int k = i >> 4, r = i & 15;
+        T[k * kRrXPitch + r] = y0 + r < ny ? in[(size_t)k * ny + y0 + r] : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+    for (int k = t; k <= 256; k += 16) {
+        const float2 a = T[k * kRrXPitch + 2 * l], b = T[k * kRrXPitch + 2 * l + 1];
+        cx<float> A = {a.x, a.y}, B = {b.x, b.y};
+        if (k == 0 || k == 256) {
+            A.im = 0.f;
+            B.im = 0.f;
+        }
+        const cx<float> zk = cadd(A, cmul_posi(B));
+        S[k] = make_float2(zk.re, zk.im);
+        if (k > 0 && k < 256) {
+            const cx<float> zm = cadd(cconj(A), cmul_posi(cconj(B)));
+            S[512 - k] = make_float2(zm.re, zm.im);
+        }
+    }
+    __syncwarp();
+    cx<float> v[32];
+#pragma unroll
+    for (int h = 0; h < 2; ++h)
+#pragma unroll
+        for (int k2 = 0; k2 < 16; ++k2) {
+            const float2 x = S[t + 16 * h + 32 * k2];
+            v[16 * h + k2] = {x.x, x.y};
+        }
+    __syncwarp();                          // natural order read: the buffer takes the rows
+    inv512_row(v, S, t, tw);
+    inv512_row(v + 16, S, t + 16, tw);
+    inv512_cols(v, S, t);
+    float *slab = u + (size_t)z * ny * 256;
+    if (ya < ny) {
+#pragma unroll
+        for (int b = 0; b < 16; ++b) slab[(size_t)ya * 256 + t + 16 * b] = v[b].re;
+    }
+    if (ya + 1 < ny) {
+#pragma unroll
+        for (int b = 0; b < 16; ++b) slab[(size_t)(ya + 1) * 256 + t + 16 * b] = v[b].im;
+    }
+}
+
 // Raise the kernel's dynamic shared-memory limit to kRrSmem once per device;
 // `raised` is the kernel's own flag array (the kernels share a function type).
 template <class K>
-cudaError_t raise_rr(K kernel, bool *raised)
+cudaError_t raise_rr(K kernel, bool *raised, size_t smem = kRrSmem)
 {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev >= 0 && dev < 64 && raised[dev]) return cudaSuccess;
-    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRrSmem);
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e == cudaSuccess && dev >= 0 && dev < 64) raised[dev] = true;
     return e;
 }
@@ -388,6 +498,26 @@ gsm_status_t launch_y_rr512_f32(bool inverse, const void *in, void *out, int nz,
         k_yi_rr512<<<g, 16 * kRrLinesPerCta, kRrSmem, st>>>(static_cast<const float2 *>(in),
                                                             static_cast<float2 *>(out), nz, hx,
                                                             static_cast<const float2 *>(tw));
+    }
+    return GSM_OK;   // a launch error stays pending for the caller's check
+}
+
+// x passes of an FP32 plan with nx = 256 on the z-slabs [0, nz): forward
+// (rho -> W1) or inverse (W1 -> u); the pointers are those of slab 0.
+gsm_status_t launch_x_rr512_f32(bool inverse, const void *in, void *out, int ny, int nz, const void *tw,
+                                cudaStream_t st)
+{
+    dim3 g((ny + 2 * kRrXLines - 1) / (2 * kRrXLines), nz);
+    if (!inverse) {
+        static bool raised_f[64] = {};
+        GSM_CUDA_TRY(raise_rr(k_xf_rr512, raised_f, kRrXSmem));
+        k_xf_rr512<<<g, 16 * kRrXLines, kRrXSmem, st>>>(static_cast<const float *>(in), static_cast<float2 *>(out),
+                                                        ny, static_cast<const float2 *>(tw));
+    } else {
+        static bool raised_i[64] = {};
+        GSM_CUDA_TRY(raise_rr(k_xi_rr512, raised_i, kRrXSmem));
+        k_xi_rr512<<<g, 16 * kRrXLines, kRrXSmem, st>>>(static_cast<const float2 *>(in), static_cast<float *>(out),
+                                                        ny, static_cast<const float2 *>(tw));
     }
     return GSM_OK;   // a launch error stays pending for the caller's check
 }

@@ -57,7 +57,7 @@ struct Plan {
     size_t mult_elems = 0;         // octant entries (FP64 tables)
     size_t mult_elems_pass = 0;    // entries of the pass-precision table
     bool mult_full = false;        // pass table covers the half spectrum (general dipolar)
-    bool rr_conv = true;           // FP32, padded length 512: the register-resident y and conv kernels
+    bool rr_conv = true;           // FP32, padded length 512: the register-resident x, y, conv kernels
     void *d_stage_in = nullptr, *d_stage_out = nullptr;   // gsm_apply_host staging
     cudaStream_t copy_stream = nullptr;                    // gsm_apply_host copies (3D)
     cudaEvent_t copy_ev[2 * 8 + 2] = {};                   // chunk events of that pipeline
@@ -101,6 +101,9 @@ gsm_status_t launch_conv_rr512_f32(void *W, const void *mult, int nlines, int is
                                    const void *tw, cudaStream_t st);
 // y passes of 3D FP32 plans with ny = 256 (forward W1 -> W2, inverse W2 -> W1), register-resident
 gsm_status_t launch_y_rr512_f32(bool inverse, const void *in, void *out, int nz, int hx, const void *tw,
+                                cudaStream_t st);
+// x passes of FP32 plans with nx = 256 on nz slabs (forward rho -> W1, inverse W1 -> u)
+gsm_status_t launch_x_rr512_f32(bool inverse, const void *in, void *out, int ny, int nz, const void *tw,
                                 cudaStream_t st);
 gsm_status_t autotune_plan(Plan *p, cudaStream_t st, std::string *report);
 // set the launch shape of one pass (nl lines per CTA, emax elements per thread)

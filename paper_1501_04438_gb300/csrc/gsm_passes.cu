@@ -679,6 +679,13 @@ void launch_pass_t(const Plan *p, int pass, const void *rho_v, void *u_v, cudaSt
     const tw *twx = static_cast<const tw *>(p->d_tw[0]);
     const tw *twy = static_cast<const tw *>(p->d_tw[1]);
     const int last = p->d == 3 ? 4 : 2;
+    if constexpr (std::is_same<Pol, F32>::value) {
+        if ((pass == 0 || pass == last) && p->M[0] == 512 && p->rr_conv) {
+            if (pass == 0) launch_x_rr512_f32(false, rho, W1, ny, nz, twx, st);
+            else launch_x_rr512_f32(true, W1, u, ny, nz, twx, st);
+            return;
+        }
+    }
     if (pass == 0) {
         const PassCfg &c = p->cfg_xf;
         dim3 g((ny + 2 * c.nl - 1) / (2 * c.nl), nz);
@@ -1047,6 +1054,14 @@ gsm_status_t x_slabs_t(const Plan *p, bool inverse, int z0, int z1, const void *
     S_t<Pol> *W1 = static_cast<S_t<Pol> *>(p->d_work1) + w_off;
     const tw *twx = static_cast<const tw *>(p->d_tw[0]);
     if (z1 <= z0) return GSM_OK;
+    if constexpr (std::is_same<Pol, F32>::value) {
+        if (p->M[0] == 512 && p->rr_conv) {
+            if (!inverse) launch_x_rr512_f32(false, static_cast<const io *>(rho_v) + in_off, W1, ny, z1 - z0, twx, st);
+            else launch_x_rr512_f32(true, W1, static_cast<io *>(u_v) + in_off, ny, z1 - z0, twx, st);
+            GSM_CUDA_TRY(cudaGetLastError());
+            return GSM_OK;
+        }
+    }
     if (!inverse) {
         const PassCfg &c = p->cfg_xf;
         dim3 g((ny + 2 * c.nl - 1) / (2 * c.nl), z1 - z0);
@@ -1251,8 +1266,12 @@ namespace {
 
 bool batch_eligible(const Plan *p)
 {
-    for (int a = 0; a < p->d; ++a)
+    for (int a = 0; a < p->d; ++a) {
         if (p->M[a] > kBatchMaxM) return false;
+        // FP32 plans that use the register-resident kernels apply alone, so that
+        // a batch gives the same bits as gsm_apply
+        if (p->opt.precision == GSM_FP32 && p->rr_conv && p->M[a] == 512) return false;
+    }
     return true;
 }
 

@@ -604,10 +604,12 @@ def test_large_cube_512_closed_form(gsm):
     ("poisson2d", (40, 256), 8.0, {}),
     ("coulomb3d", (24, 256, 40), 6.0, {}),
     ("coulomb3d", (16, 256, 256), 6.0, {}),
-], ids=["cube256", "lines256", "dipolar_full256", "2d256", "y256", "y256z256"])
+    ("coulomb3d", (256, 30, 20), 6.0, {}),
+    ("coulomb2d", (256, 40), 6.0, {}),
+], ids=["cube256", "lines256", "dipolar_full256", "2d256", "y256", "y256z256", "x256", "2dx256"])
 def test_fp32_register_resident_conv(gsm, kernel, n, L, kw):
-    """FP32 plans with padded length 512 in y or in the conv direction use the
-    register-resident kernels (nz = 40: a ragged last CTA of z-lines): against
+    """FP32 plans with padded length 512 in x, y or the conv direction use the
+    register-resident kernels (ragged last CTAs: nz = 40, ny = 30): against
     the oracle at the FP32 tolerance, and against the shared-memory engine (debug
     bit 0) to the same order, including the half-spectrum multiplier (general
     dipolar directions) and 2D."""
@@ -621,3 +623,18 @@ def test_fp32_register_resident_conv(gsm, kernel, n, L, kw):
     uo, _ = oracle.apply(kernel, rho, L, taylor_mode=1, S=plan.info()["S"], **kw)
     assert relmax(u, uo) < TOL["fp32"], relmax(u, uo)
     assert relmax(u, u_eng) < TOL["fp32"], relmax(u, u_eng)
+
+
+def test_fp32_batch_with_register_resident_plans_equals_single(gsm):
+    """FP32 plans with a padded length of 512 apply alone inside a batch, so the
+    batch keeps the bits of the single applies."""
+    torch = _torch()
+    shapes = [(256, 24, 20), (32, 32, 32), (20, 256, 16), (24, 20, 256)]
+    plans = [gsm.Plan("coulomb3d", 4.0, n, precision="fp32") for n in shapes]
+    rhos = [torch.tensor(np.random.default_rng(70 + i).standard_normal(n[::-1]), dtype=torch.float32, device="cuda")
+            for i, n in enumerate(shapes)]
+    singles = [p.apply(r).clone() for p, r in zip(plans, rhos)]
+    outs = gsm.apply_batched(plans, rhos)
+    torch.cuda.synchronize()
+    for a, b in zip(outs, singles):
+        assert torch.equal(a, b)
