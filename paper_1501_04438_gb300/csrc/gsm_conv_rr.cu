@@ -317,7 +317,8 @@ __global__ void __launch_bounds__(16 * kRrLinesPerCta, 2)
     const int z0 = blockIdx.x * kRrLinesPerCta;
     const int z = z0 + l;
     const float2 *in = W2 + (size_t)kx * 512 * nz;
-    for (int i = threadIdx.x; i < 512 * 16; i += blockDim.x) {
+#pragma unroll 8
+    for (int i = threadIdx.x; i < 512 * 16; i += blockDim.x) {   // unrolled: loads in flight
         const int ky = i >> 4, zz = z0 + (i & 15);
         sbuf[ky * kRrRow + (i & 15)] = zz < nz ? in[(size_t)ky * nz + zz] : make_float2(0.f, 0.f);
     }
@@ -409,7 +410,8 @@ __global__ void __launch_bounds__(16 * kRrXLines, 3)
     float2 *S = sbuf + l * kRrLineElems;
     float2 *T = sbuf + kRrXLines * kRrLineElems;
     const float2 *in = W1 + (size_t)z * 257 * ny;
-    for (int i = threadIdx.x; i < 257 * 16; i += blockDim.x) {
+#pragma unroll 8
+    for (int i = threadIdx.x; i < 257 * 16; i += blockDim.x) {   // unrolled: loads in flight
         const int k = i >> 4, r = i & 15;
         T[k * kRrXPitch + r] = y0 + r < ny ? in[(size_t)k * ny + y0 + r] : make_float2(0.f, 0.f);
     }
