@@ -350,16 +350,30 @@ __device__ __forceinline__ void fft_stage(typename Pol::scplx *s, int M, int Ns,
 // ---------------------------------------------------------------- FMA-form stages (FP64)
 // FMA-form constants exist for the twiddled stages of radix 8, 4 and 2 (they
 // come first in every schedule, so their Ns are powers of two): gslots(R)
-// doubles per index j, stage after stage in schedule order.
+// slots for each index j < Ns, rounded up to whole blocks of kGBlk indices,
+// stage after stage in schedule order.
 __host__ __device__ __forceinline__ bool gtabled(int R) { return R == 8 || R == 4 || R == 2; }
 __host__ __device__ __forceinline__ int gslots(int R) { return R == 8 ? 16 : (R == 4 ? 8 : 4); }
+constexpr int kGBlk = 32;
+
+// Doubles of the constants of one stage of radix R after stages of product Ns.
+__host__ __device__ __forceinline__ size_t gblock(int R, size_t Ns)
+{
+    return (Ns + kGBlk - 1) / kGBlk * kGBlk * (size_t)gslots(R);
+}
+
+// First slot of index j within a stage's constants.
+__host__ __device__ __forceinline__ size_t gindex(int R, size_t j)
+{
+    return (j / kGBlk) * (size_t)(gslots(R) * kGBlk) + j % kGBlk;
+}
 
 // Offset (in doubles) of the constants of stage st.
 __host__ __device__ inline size_t gtable_offset(const Sched &sc, int st)
 {
     size_t off = 0, Ns = 1;
     for (int i = 0; i < st && i < sc.nst; ++i) {
-        if (Ns > 1 && gtabled(sc.r[i])) off += Ns * (size_t)gslots(sc.r[i]);
+        if (Ns > 1 && gtabled(sc.r[i])) off += gblock(sc.r[i], Ns);
         Ns *= (size_t)sc.r[i];
     }
     return off;
@@ -378,16 +392,22 @@ inline size_t g8_table_doubles(const Sched &sc) { return gtable_offset(sc, sc.ns
 // side); the real scales f_t are carried as ratios through the butterfly's
 // layers, each a pair of FMAs per complex value, and cancel at the end because
 // f_0 = 1.  Radix 8: 66 FP64 instructions per butterfly instead of 80;
-// radix 4: 22 instead of 28; radix 2: 6 instead of 8.  Constants per index j
+// radix 4: 22 instead of 28; radix 2: 6 instead of 8.  A stage's constants
+// are slot-major in blocks of kGBlk = 32 indices: slot q of index j is at
+// ((j / 32) * slots + q) * 32 + j % 32, so the threads of a warp, which hold
+// consecutive j, read each slot from 256 consecutive bytes (two 128-byte
+// lines per warp instead of one line per thread), and a thread reaches its
+// slots at fixed offsets from one pointer.  Slots
 // (forward direction; the inverse uses conj(W_t) = f_t i^(-k_t)(1 - i tau_t)):
-//   radix 8 (16 doubles, one 128-byte line): 0..6 tau_t sigma_t (t = 1..7;
+//   radix 8 (16 slots): 0..6 tau_t sigma_t (t = 1..7;
 //     sigma_t = -1 for odd k_t, which folds the swap's sign into the tangent),
 //     7..10 r_t = f_(t+4) / f_t (t = 0..3), 11 f_2, 12 f_3 / f_1, 13 f_1,
 //     14 f_1 / sqrt2, 15 the codes k_t mod 4 in bits 2(t-1), 2(t-1)+1 (an
 //     integer in the double's bits);
-//   radix 4 (8 doubles): tau_t sigma_t (t = 1..3), f_2, f_3 / f_1, f_1, codes, -;
-//   radix 2 (4 doubles): tau_1 sigma_1, f_1, code, -.
-constexpr int kG8Slots = 16;
+//   radix 4 (8 slots): tau_t sigma_t (t = 1..3), f_2, f_3 / f_1, f_1, codes, -;
+//   radix 2 (4 slots): tau_1 sigma_1, f_1, code, -.
+// Slot q of the constants at c (index j's first slot).
+__device__ __forceinline__ double gslot(const double *__restrict__ c, int q) { return __ldg(c + q * kGBlk); }
 
 __device__ __forceinline__ double flip_sign(double x, unsigned neg)
 {
@@ -428,18 +448,18 @@ __device__ __forceinline__ void dft4_scaled(cx<double> &z0, cx<double> &z1, cx<d
 template <bool FWD, int NOUT>
 __device__ __forceinline__ void bfly8_fma(cx<double> *v, const double *__restrict__ c)
 {
-    const int codes = __double2loint(__ldg(c + 15));
+    const int codes = __double2loint(gslot(c, 15));
 #pragma unroll
     for (int t = 1; t < 8; ++t) {
         int k = (codes >> (2 * (t - 1))) & 3;
         if (!FWD) k = (4 - k) & 3;
-        const double tt = __ldg(c + t - 1);
+        const double tt = gslot(c, t - 1);
         v[t] = tangent_rot(v[t], k, FWD ? tt : -tt);
     }
     // layer 1: v_t <- E_t = X_t + r_t X_(t+4) (scale f_t), v_(t+4) <- O_t = X_t - r_t X_(t+4)
 #pragma unroll
     for (int t = 0; t < 4; ++t) {
-        const double r = __ldg(c + 7 + t);
+        const double r = gslot(c, 7 + t);
         const cx<double> x = v[t], y = v[t + 4];
         v[t] = {fma(r, y.re, x.re), fma(r, y.im, x.im)};
         v[t + 4] = {fma(-r, y.re, x.re), fma(-r, y.im, x.im)};
@@ -457,9 +477,9 @@ __device__ __forceinline__ void bfly8_fma(cx<double> *v, const double *__restric
             v[7] = {-b.re - b.im, b.re - b.im};       // (-1 + i) b
         }
     }
-    const double f2 = __ldg(c + 11), f31 = __ldg(c + 12);
-    dft4_scaled<FWD, NOUT == 4>(v[0], v[1], v[2], v[3], f2, f31, __ldg(c + 13));   // Y_0, Y_2, Y_4, Y_6
-    dft4_scaled<FWD, NOUT == 4>(v[4], v[5], v[6], v[7], f2, f31, __ldg(c + 14));   // Y_1, Y_3, Y_5, Y_7
+    const double f2 = gslot(c, 11), f31 = gslot(c, 12);
+    dft4_scaled<FWD, NOUT == 4>(v[0], v[1], v[2], v[3], f2, f31, gslot(c, 13));   // Y_0, Y_2, Y_4, Y_6
+    dft4_scaled<FWD, NOUT == 4>(v[4], v[5], v[6], v[7], f2, f31, gslot(c, 14));   // Y_1, Y_3, Y_5, Y_7
     // interleave (register renaming only)
     const cx<double> e1 = v[1], e2 = v[2], e3 = v[3], o0 = v[4], o1 = v[5], o2 = v[6];
     v[1] = o0;
@@ -473,32 +493,32 @@ __device__ __forceinline__ void bfly8_fma(cx<double> *v, const double *__restric
 }
 
 // Twiddled radix-4 butterfly in FMA form, in place (Y_0..Y_3 in natural
-// order; HALFOUT: Y_0, Y_1 only).  Constants at c: tau_t sigma_t (t = 1..3),
+// order; HALFOUT: Y_0, Y_1 only).  Constant slots at c: tau_t sigma_t (t = 1..3),
 // f_2, f_3 / f_1, f_1, the quarter-turn codes, one unused slot.
 template <bool FWD, bool HALFOUT>
 __device__ __forceinline__ void bfly4_fma(cx<double> *v, const double *__restrict__ c)
 {
-    const int codes = __double2loint(__ldg(c + 6));
+    const int codes = __double2loint(gslot(c, 6));
 #pragma unroll
     for (int t = 1; t < 4; ++t) {
         int k = (codes >> (2 * (t - 1))) & 3;
         if (!FWD) k = (4 - k) & 3;
-        const double tt = __ldg(c + t - 1);
+        const double tt = gslot(c, t - 1);
         v[t] = tangent_rot(v[t], k, FWD ? tt : -tt);
     }
-    dft4_scaled<FWD, HALFOUT>(v[0], v[1], v[2], v[3], __ldg(c + 3), __ldg(c + 4), __ldg(c + 5));
+    dft4_scaled<FWD, HALFOUT>(v[0], v[1], v[2], v[3], gslot(c, 3), gslot(c, 4), gslot(c, 5));
 }
 
-// Twiddled radix-2 butterfly in FMA form: Y_0,1 = x_0 +- f_1 X_1.  Constants
-// at c: tau_1 sigma_1, f_1, the quarter-turn code, one unused slot.
+// Twiddled radix-2 butterfly in FMA form: Y_0,1 = x_0 +- f_1 X_1.  Constant
+// slots at c: tau_1 sigma_1, f_1, the quarter-turn code, one unused slot.
 template <bool FWD, bool HALFOUT>
 __device__ __forceinline__ void bfly2_fma(cx<double> *v, const double *__restrict__ c)
 {
-    int k = __double2loint(__ldg(c + 2)) & 3;
+    int k = __double2loint(gslot(c, 2)) & 3;
     if (!FWD) k = (4 - k) & 3;
-    const double tt = __ldg(c);
+    const double tt = gslot(c, 0);
     const cx<double> X = tangent_rot(v[1], k, FWD ? tt : -tt);
-    const double f = __ldg(c + 1);
+    const double f = gslot(c, 1);
     const cx<double> x0 = v[0];
     v[0] = {fma(f, X.re, x0.re), fma(f, X.im, x0.im)};
     if (!HALFOUT) v[1] = {fma(-f, X.re, x0.re), fma(-f, X.im, x0.im)};
@@ -512,7 +532,6 @@ __device__ __forceinline__ void fft_stage_fma(double2 *s, int M, int Ns, const d
                                               const Group &g)
 {
     constexpr int NOUT = HALF == 2 ? RAD / 2 : RAD;
-    constexpr int SL = RAD == 8 ? 16 : (RAD == 4 ? 8 : 4);
     const int nb = M / RAD;
     cx<double> v[NB][RAD];
 #pragma unroll
@@ -521,7 +540,7 @@ __device__ __forceinline__ void fft_stage_fma(double2 *s, int M, int Ns, const d
         if (b < nb) {
 #pragma unroll
             for (int t = 0; t < RAD; ++t) v[i][t] = F64::ld(s[pidx<F64>(b + t * nb)]);
-            const double *c = gt + (size_t)(b & (Ns - 1)) * SL;
+            const double *c = gt + gindex(RAD, b & (Ns - 1));
             if constexpr (RAD == 8) bfly8_fma<FWD, NOUT>(v[i], c);
             else if constexpr (RAD == 4) bfly4_fma<FWD, HALF == 2>(v[i], c);
             else bfly2_fma<FWD, HALF == 2>(v[i], c);
@@ -603,17 +622,17 @@ __device__ __forceinline__ void fft_line(typename Pol::scplx *s, const Sched &sc
             for (; st < nend && sc.r[st] == 8; ++st, Ns *= 8) {
                 if (CROP && st == last) fft_stage_fma<8, FWD, (EMAX + 7) / 8, 2>(s, M, Ns, gt + goff, g);
                 else fft_stage_fma<8, FWD, (EMAX + 7) / 8, 0>(s, M, Ns, gt + goff, g);
-                goff += (size_t)Ns * 16;
+                goff += gblock(8, Ns);
             }
             for (; st < nend && sc.r[st] == 4; ++st, Ns *= 4) {
                 if (CROP && st == last) fft_stage_fma<4, FWD, (EMAX + 3) / 4, 2>(s, M, Ns, gt + goff, g);
                 else fft_stage_fma<4, FWD, (EMAX + 3) / 4, 0>(s, M, Ns, gt + goff, g);
-                goff += (size_t)Ns * 8;
+                goff += gblock(4, Ns);
             }
             for (; st < nend && sc.r[st] == 2; ++st, Ns *= 2) {
                 if (CROP && st == last) fft_stage_fma<2, FWD, (EMAX + 1) / 2, 2>(s, M, Ns, gt + goff, g);
                 else fft_stage_fma<2, FWD, (EMAX + 1) / 2, 0>(s, M, Ns, gt + goff, g);
-                goff += (size_t)Ns * 4;
+                goff += gblock(2, Ns);
             }
         }
     }
@@ -657,7 +676,7 @@ __device__ __forceinline__ void fft_fused_mid8(typename Pol::scplx *s, const Sch
             bool done = false;
             if constexpr (std::is_same<Pol, F64>::value) {
                 if (gt != nullptr) {
-                    bfly8_fma<true, 8>(v[i], gt + gtable_offset(sc, sc.nst - 1) + (size_t)b * kG8Slots);
+                    bfly8_fma<true, 8>(v[i], gt + gtable_offset(sc, sc.nst - 1) + gindex(8, b));
                     done = true;
                 }
             }

@@ -400,7 +400,7 @@ __global__ void __launch_bounds__(32 * kBatchMaxLines, std::is_same<Pol, F32>::v
 }
 
 // ------------------------------------------------------------------ tables
-// Constants of the FMA-form stages (layout before kG8Slots in gsm_fft.cuh),
+// Constants of the FMA-form stages (slot-major blocks, see gindex in gsm_fft.cuh),
 // one thread per (stage, j).  For stage radix R with Ns, forward twiddle
 // W_t = exp(-2 pi i q / D), q = j t, D = R Ns: with K = round(4 q / D) and
 // m = q - K D/4 (|m| <= D/8), W_t = i^(-K) exp(-2 pi i m / D), so k_t = -K mod 4,
@@ -438,27 +438,28 @@ __global__ void k_gtable(GTableDesc d, double *out)
         tau[t] = (k & 1) ? sn / cs : -sn / cs;   // tau sigma_t, sigma_t = -1 for odd k
         codes |= k << (2 * (t - 1));
     }
-    double *c = out + d.s[st].off + j * gslots(R);
+    double *cj = out + d.s[st].off + gindex(R, j);
+    auto c = [&](int q) -> double & { return cj[q * kGBlk]; };
     if (R == 8) {
-        for (int t = 1; t < 8; ++t) c[t - 1] = tau[t];
-        for (int t = 0; t < 4; ++t) c[7 + t] = f[t + 4] / f[t];
-        c[11] = f[2];
-        c[12] = f[3] / f[1];
-        c[13] = f[1];
-        c[14] = f[1] * 0.707106781186547524400844362104849039;
-        c[15] = __hiloint2double(0, codes);
+        for (int t = 1; t < 8; ++t) c(t - 1) = tau[t];
+        for (int t = 0; t < 4; ++t) c(7 + t) = f[t + 4] / f[t];
+        c(11) = f[2];
+        c(12) = f[3] / f[1];
+        c(13) = f[1];
+        c(14) = f[1] * 0.707106781186547524400844362104849039;
+        c(15) = __hiloint2double(0, codes);
     } else if (R == 4) {
-        for (int t = 1; t < 4; ++t) c[t - 1] = tau[t];
-        c[3] = f[2];
-        c[4] = f[3] / f[1];
-        c[5] = f[1];
-        c[6] = __hiloint2double(0, codes);
-        c[7] = 0.0;
+        for (int t = 1; t < 4; ++t) c(t - 1) = tau[t];
+        c(3) = f[2];
+        c(4) = f[3] / f[1];
+        c(5) = f[1];
+        c(6) = __hiloint2double(0, codes);
+        c(7) = 0.0;
     } else {
-        c[0] = tau[1];
-        c[1] = f[1];
-        c[2] = __hiloint2double(0, codes);
-        c[3] = 0.0;
+        c(0) = tau[1];
+        c(1) = f[1];
+        c(2) = __hiloint2double(0, codes);
+        c(3) = 0.0;
     }
 }
 
