@@ -3,13 +3,21 @@
 //   F64  : IEEE double.
 //   F32  : IEEE single.
 //   DF64 : double-float ("FP32x2"): a value is hi + lo with two floats,
-//          |lo| <= ulp(hi)/2, about 48 significand bits, computed with FP32
-//          instructions only.  Additions use the error-free two-sum of
-//          Knuth and the fast two-sum of Dekker; products use the FMA-based
-//          exact product (Dekker 1971, "A floating-point technique for extending
-//          the available precision"; Hida, Li, Bailey 2001, double-double).
-//          The additions are the "sloppy" variant: its error is bounded
-//          relative to |a| + |b|, which is what normwise FFT error bounds use.
+//          about 48 significand bits, computed with FP32 instructions only.
+//          Additions use the error-free two-sum of Knuth; products use the
+//          FMA-based exact product (Dekker 1971, "A floating-point technique
+//          for extending the available precision"; Hida, Li, Bailey 2001,
+//          double-double).  Tables (twiddles, multiplier) are split from FP64
+//          into normalised pairs, |lo| <= ulp(hi)/2; the results of sums and
+//          products within a stage are left unnormalised ("pair arithmetic",
+//          M. Lange and S. M. Rump, ACM TOMS 46 (2020)): the closing fast
+//          two-sum of double-word arithmetic is omitted, so |lo| may exceed
+//          ulp(hi)/2, until the value is stored (DF64::st renormalises).
+//          The error of each operation stays bounded relative
+//          to |a| + |b| (sums) or |a||b| (products with a normalised factor:
+//          every product of the passes has a table value, twiddle or
+//          multiplier, as one factor), which is what normwise FFT error
+//          bounds use.
 //
 // Every kernel is written once against this interface:
 //   real  R          scalar type
@@ -55,20 +63,11 @@ __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
     float bb = __fsub_rn(s, a);
     e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
 }
-// s + e == a + b exactly when |a| >= |b| (Dekker fast two-sum).
-__device__ __forceinline__ void quick_two_sum(float a, float b, float &s, float &e)
-{
-    s = __fadd_rn(a, b);
-    e = __fsub_rn(b, __fsub_rn(s, a));
-}
 __device__ __forceinline__ df radd(df a, df b)
 {
     float s, e;
     two_sum(a.hi, b.hi, s, e);
-    e = __fadd_rn(e, __fadd_rn(a.lo, b.lo));
-    df r;
-    quick_two_sum(s, e, r.hi, r.lo);
-    return r;
+    return df{s, __fadd_rn(e, __fadd_rn(a.lo, b.lo))};
 }
 __device__ __forceinline__ df rneg(df a) { return df{-a.hi, -a.lo}; }
 __device__ __forceinline__ df rsub(df a, df b) { return radd(a, rneg(b)); }
@@ -79,9 +78,7 @@ __device__ __forceinline__ df rmul(df a, df b)
     float e = __fmaf_rn(a.hi, b.hi, -p);
     e = __fmaf_rn(a.hi, b.lo, e);
     e = __fmaf_rn(a.lo, b.hi, e);
-    df r;
-    quick_two_sum(p, e, r.hi, r.lo);
-    return r;
+    return df{p, e};
 }
 // split a double constant into hi + lo floats (folds at compile time)
 __host__ __device__ __forceinline__ df df_from_double(double k)
@@ -184,7 +181,16 @@ struct DF64 {
     static constexpr int kPadShift = 3;
     static constexpr bool kPrune = false;
     __device__ static __forceinline__ cx<real> ld(const scplx &v) { return {df{v.x, v.y}, df{v.z, v.w}}; }
-    __device__ static __forceinline__ scplx st(cx<real> a) { return make_float4(a.re.hi, a.re.lo, a.im.hi, a.im.lo); }
+    // stored values are renormalised (two-sum: exact whatever the order of
+    // |hi| and |lo|), so the unnormalised parts of the pair arithmetic only
+    // live within one stage
+    __device__ static __forceinline__ scplx st(cx<real> a)
+    {
+        float4 r;
+        two_sum(a.re.hi, a.re.lo, r.x, r.y);
+        two_sum(a.im.hi, a.im.lo, r.z, r.w);
+        return r;
+    }
     __device__ static __forceinline__ cx<real> tw(const tw_t &v) { return {df{v.x, v.y}, df{v.z, v.w}}; }
     __device__ static __forceinline__ real mult(mult_t m) { return df{m.x, m.y}; }
     __device__ static __forceinline__ real from_io(io_t x)
