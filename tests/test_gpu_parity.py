@@ -334,6 +334,19 @@ def test_full_size_256_cube_parity(gsm, precision):
     assert relmax(u, uo) < 1e-12
 
 
+def test_fp32x2_error_class(gsm):
+    """Double-float pairs keep FP64-class accuracy: ~48 significand bits, so a
+    chain of O(log2 M) butterflies per transform over the passes stays within
+    about 1e-13 (u = 2^-48 ~ 3.6e-15 times log2(M) times a few passes) on the
+    mixture workloads, far inside the 1e-12 parity tolerance."""
+    rho3 = wl.coulomb3d_mixture(128, 12.0)
+    u3, p3 = run(gsm, "coulomb3d", rho3, 12.0, "fp32x2")
+    assert relmax(u3, oracle.Prepared("coulomb3d", 128, 12.0, S=p3.info()["S"]).run(rho3)) < 1e-13
+    rho2 = wl.mixture2d(1024, 16.0)
+    u2, p2 = run(gsm, "poisson2d", rho2, 16.0, "fp32x2")
+    assert relmax(u2, oracle.Prepared("poisson2d", 1024, 16.0, S=p2.info()["S"]).run(rho2)) < 1e-13
+
+
 @pytest.mark.parametrize("kernel", ["poisson2d", "coulomb2d"])
 def test_full_size_4096_square_parity(gsm, kernel):
     """2D at 4096^2 (M = 8192 lines, one per CTA) against the oracle and the
