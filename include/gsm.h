@@ -316,17 +316,21 @@ gsm_status_t gsm_fft_lines(int M, int nlines, int sign, gsm_precision_t precisio
  * held by another allocator (a framework's caching pool), code on a latency-
  * critical path that must not take the allocator's locks or risk an
  * out-of-memory failure at call time, or a plug-in that is not allowed to own
- * device memory.  gsm_fft_lines_noalloc computes exactly what gsm_fft_lines
- * computes, with the same arguments, but keeps the twiddle table in a fixed
- * 128 KiB scratch array that the library declares statically in device memory:
+ * device memory.  gsm_fft_lines_noalloc takes the same arguments and gives the
+ * same bits as gsm_fft_lines (the same twiddle table and, in FP64, the same
+ * FMA-form stage constants, so the same arithmetic), but keeps those tables in
+ * a fixed 384 KiB scratch array that the library declares statically in device
+ * memory:
  *   - it calls no cudaMalloc, cudaFree or other allocating routine;
- *   - M is limited by that scratch to M <= 8192 (16-byte entries); larger M is
- *     rejected with GSM_ERR_UNSUPPORTED_SIZE;
- *   - every GPU that loads the library holds the 128 KiB until the process
+ *   - the tables of every supported length fit (the largest, M = 8192 in FP64,
+ *     take 339968 bytes); a length whose tables would not fit is rejected with
+ *     GSM_ERR_UNSUPPORTED_SIZE, as is M > 8192;
+ *   - every GPU that loads the library holds the 384 KiB until the process
  *     exits;
- *   - the first call on each device looks up the device address of the
- *     scratch (set-up, once per device, on the current device); make that
- *     first call before any stream capture;
+ *   - the first call on each device (more exactly, in each CUDA context: again
+ *     after cudaDeviceReset) looks up the device address of the scratch, with
+ *     the caller's device current; make that first call before any stream
+ *     capture;
  *   - all calls share the one scratch array: calls that can overlap on the GPU
  *     (different streams, no ordering between them) race and may return wrong
  *     results; order them on one stream or with events.  Nothing in the
@@ -334,6 +338,23 @@ gsm_status_t gsm_fft_lines(int M, int nlines, int sign, gsm_precision_t precisio
  */
 gsm_status_t gsm_fft_lines_noalloc(int M, int nlines, int sign, gsm_precision_t precision,
                                    const double *in_dev, double *out_dev, void *cuda_stream);
+
+/* --- failure-handling test hooks ----------------------------------------------
+ * No counterpart in the paper.  Every device allocation the library makes goes
+ * through one internal function that counts what is live.  These two calls let
+ * a test check that each out-of-memory path releases what it had taken,
+ * without exhausting a GPU.
+ *
+ * gsm_debug_fail_alloc(k): the k-th device allocation from now (k = 0: the
+ * next one) fails as if the device were out of memory (the call that made it
+ * returns GSM_ERR_OOM); later allocations succeed again.  k < 0 cancels a
+ * pending failure.  Process-wide, for every thread and device.  Always GSM_OK.
+ *
+ * gsm_debug_alloc_stats(count, bytes): the number and the total size of the
+ * library's live device allocations (plans, workspaces, staging buffers,
+ * temporaries), process-wide.  GSM_ERR_INVALID_ARG if a pointer is NULL. */
+gsm_status_t gsm_debug_fail_alloc(int k);
+gsm_status_t gsm_debug_alloc_stats(size_t *count, size_t *bytes);
 
 #ifdef __cplusplus
 }

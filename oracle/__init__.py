@@ -4,9 +4,9 @@ arXiv:1501.04438).
 TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
 CPU-baseline leg of ``bench.py`` may import this package.  The product (the
 CUDA library in ``paper_1501_04438_gb300``) never imports it and shares no code
-with it.  The arithmetic lives in ``oracle.c`` (plain C, double precision,
-following Algorithm 1 of the paper step by step); this module only builds that
-file and marshals arguments through ctypes.
+with it.  The arithmetic lives in ``oracle.c`` (plain C, double precision, each
+quantity computed from the equation of the paper that defines it); this module
+only builds that file and marshals arguments through ctypes.
 """
 from __future__ import annotations
 

@@ -8,22 +8,24 @@
  * product (the CUDA library) never links, loads or calls it, and the two share
  * no code: not a kernel, a header, a helper, a table or a constant generator.
  *
- * The code is slow on purpose and follows the paper's steps in the paper's
- * order (Algorithm 1), so that a reader can check it against the paper by eye:
+ * The code is slow on purpose.  It is organised around the quantities the
+ * paper defines, each computed from its own equation:
  *
  * Kernels: 1/(4 pi |x|) and 1/(2 pi |x|) (Coulomb), -ln|x|/(2 pi) (Poisson),
  * the dipolar and Davey-Stewartson potentials built on them (Sec. 2.4), and
  * |x|^-beta, 0 < beta < d (remark after Eq. sinc_quad).
  *
- *   Precomputation
- *     1. Gaussian sum (GS) of the kernel by sinc quadrature   (Sec. 3.1-3.3)
- *     2. Fourier coefficients sum_q w_q G_k^q of the kernel   (Eq. tensor)
- *   Actual computation
- *     1. rho_hat by the trapezoidal rule, through an FFT       (Eq. rho_hat)
- *     2. I_1 by Eq. I1FFT through an inverse FFT
- *     3. Laplacian of rho by FFT
- *     4. near-field correction I_{2,1} from the Taylor polynomial (Eq. I_2h)
- *     5. u = I_1 + I_{2,1}
+ *   quantities fixed by the kernel and the grid ("precomputation" in Algorithm 1)
+ *     - Gaussian sum (w_q, tau_q) of the kernel by sinc quadrature (Sec. 3.1-3.3)
+ *     - Fourier coefficients sum_q w_q G_k^q of U_GS               (Eq. tensor)
+ *     - Taylor coefficients c0, c2 of the near-field ball          (Eq. taylor)
+ *   quantities of one density ("actual computation" in Algorithm 1)
+ *     - rho_hat by the trapezoidal rule, through an FFT            (Eq. rho_hat)
+ *     - the regular part I_1, an inverse FFT of rho_hat times the
+ *       stored coefficients                                        (Eq. I1FFT)
+ *     - the spectral Laplacian of rho and the near-field part
+ *       I_{2,1} = c0 rho + c2 Lap(rho)                             (Eq. I_2h)
+ *     - u = I_1 + I_{2,1}, rescaled to the box                     (Eq. rescale)
  *
  * Every routine below is pinned by a CPU test against something other than
  * itself (closed forms, exact special cases, brute force, an independent
@@ -672,7 +674,7 @@ static int run_scalar(const struct orc_prepared_s *h, const double *rho, double 
     const double L = box_eta(p, eta), c0 = h->c0, c2 = h->c2;
     const double *khat = h->khat;
 
-    /* Step 1: zero-padded density and rho_hat_k = DFT / Nt^d (Eq. rho_hat,  */
+    /* rho_hat: zero-padded density, rho_hat_k = DFT / Nt^d (Eq. rho_hat,    */
     /* trapezoidal rule).  Grid point i sits at padded index i + off with    */
     /* off = 1 + (pad - 1) n / 2 (periodic box [-P/2, P/2), P = 2 pad).       */
     size_t NT = prod(d, Nt), N = prod(d, n);
@@ -688,7 +690,7 @@ static int run_scalar(const struct orc_prepared_s *h, const double *rho, double 
     orc_fftn(d, Nt, (double *)a, -1);
     double invN = 1.0 / (double)NT;
 
-    /* Step 2: I_1(x) = sum_k rho_hat_k (sum_q w_q G^q_k) e^{2 pi i k (x - a)/P} */
+    /* I_1(x) = sum_k rho_hat_k (sum_q w_q G^q_k) e^{2 pi i k (x - a)/P}        */
     /* (Eq. I1FFT).  taylor_mode 1 also folds c0 - c2 |kappa|^2 into the     */
     /* multiplier: the Taylor correction with a padded-grid spectral Laplacian. */
     /* Period of axis j: P_j = 2 pad eta_j.                                   */
@@ -726,7 +728,7 @@ static int run_scalar(const struct orc_prepared_s *h, const double *rho, double 
     }
     orc_fftn(d, Nt, (double *)a, +1);
 
-    /* Step 3: Laplacian of rho on the n-grid (Algorithm 1, step 3) */
+    /* Lap(rho) on the n-grid (spectral), for the literal near-field part */
     double *lap = NULL;
     if (p->taylor_mode == 0) {
         lap = malloc(sizeof(double) * N);
@@ -748,7 +750,7 @@ static int run_scalar(const struct orc_prepared_s *h, const double *rho, double 
         extra = -L * L / (2.0 * PI) * log(L) * hu * hv * mass;
     }
 
-    /* Steps 4-5: I_{2,1} ~ c0 rho + c2 Lap(rho) (Eq. I_2h), u = I_1 + I_{2,1} */
+    /* I_{2,1} ~ c0 rho + c2 Lap(rho) (Eq. I_2h) and u = I_1 + I_{2,1}        */
     for (size_t i = 0; i < N; i++) {
         int x = i % n3[0], y = (i / n3[0]) % n3[1], z = i / ((size_t)n3[0] * n3[1]);
         size_t m = (size_t)(x + off[0]) + (size_t)Nt[0] * ((y + off[1]) + (size_t)Nt[1] * (z + off[2]));

@@ -20,7 +20,7 @@ EXPORTS = ["gsm_default_options", "gsm_plan", "gsm_apply", "gsm_apply_pass", "gs
            "gsm_hartree", "gsm_plan_info", "gsm_plan_destroy", "gsm_status_string", "gsm_last_error",
            "gsm_plan_gs_terms", "gsm_plan_kernel_tensor", "gsm_plan_factors", "gsm_fft_lines",
            "gsm_fft_lines_noalloc", "gsm_batch_create", "gsm_batch_launch", "gsm_batch_destroy",
-           "gsm_plan_save", "gsm_plan_load"]
+           "gsm_plan_save", "gsm_plan_load", "gsm_debug_fail_alloc", "gsm_debug_alloc_stats"]
 
 
 class Options(ctypes.Structure):
@@ -91,6 +91,8 @@ def load(path: str = LIB_PATH):
         L.gsm_plan_factors.argtypes = [_vp, ctypes.c_int, _dp, ctypes.c_size_t]
         L.gsm_fft_lines.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp, _vp, _vp]
         L.gsm_fft_lines_noalloc.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp, _vp, _vp]
+        L.gsm_debug_fail_alloc.argtypes = [ctypes.c_int]
+        L.gsm_debug_alloc_stats.argtypes = [ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ctypes.c_size_t)]
         for name in EXPORTS:
             if name not in ("gsm_default_options", "gsm_status_string", "gsm_last_error"):
                 getattr(L, name).restype = ctypes.c_int

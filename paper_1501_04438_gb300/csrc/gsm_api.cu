@@ -2,8 +2,12 @@
 #include <math.h>
 #include <string.h>
 
+#include <atomic>
+#include <mutex>
 #include <new>
 #include <string>
+#include <unordered_map>
+#include <unordered_set>
 #include <vector>
 
 #include "gsm_internal.h"
@@ -14,39 +18,134 @@ static thread_local std::string g_last_error;
 
 void set_error(const std::string &msg) { g_last_error = msg; }
 
+// ---------------------------------------------------------------- device allocations
+// Live allocations (address -> bytes) and the injected failure: g_fail_in > 0
+// counts allocations down to the one that fails; 0 fails the next; < 0 is off.
+static std::mutex g_alloc_mutex;
+static std::unordered_map<void *, size_t> g_alloc_live;
+static size_t g_alloc_bytes = 0;
+static std::atomic<long> g_fail_in{-1};
+
+static bool injected_failure()
+{
+    long k = g_fail_in.load();
+    while (k >= 0) {
+        if (g_fail_in.compare_exchange_weak(k, k - 1)) return k == 0;
+    }
+    return false;
+}
+
+static void track(void *ptr, size_t bytes)
+{
+    std::lock_guard<std::mutex> lock(g_alloc_mutex);
+    g_alloc_live[ptr] = bytes;
+    g_alloc_bytes += bytes;
+}
+
+static bool untrack(void *ptr)
+{
+    std::lock_guard<std::mutex> lock(g_alloc_mutex);
+    auto it = g_alloc_live.find(ptr);
+    if (it == g_alloc_live.end()) return false;
+    g_alloc_bytes -= it->second;
+    g_alloc_live.erase(it);
+    return true;
+}
+
+cudaError_t dev_alloc_bytes(void **ptr, size_t bytes)
+{
+    *ptr = nullptr;
+    if (injected_failure()) return cudaErrorMemoryAllocation;
+    cudaError_t e = cudaMalloc(ptr, bytes);
+    if (e != cudaSuccess) {
+        *ptr = nullptr;
+        return e;
+    }
+    track(*ptr, bytes);
+    return cudaSuccess;
+}
+
+cudaError_t dev_alloc_async_bytes(void **ptr, size_t bytes, cudaStream_t st)
+{
+    *ptr = nullptr;
+    if (injected_failure()) return cudaErrorMemoryAllocation;
+    cudaError_t e = cudaMallocAsync(ptr, bytes, st);
+    if (e != cudaSuccess) {
+        *ptr = nullptr;
+        return e;
+    }
+    track(*ptr, bytes);
+    return cudaSuccess;
+}
+
+void dev_free(void *ptr)
+{
+    if (ptr && untrack(ptr)) cudaFree(ptr);
+}
+
+void dev_free_async(void *ptr, cudaStream_t st)
+{
+    if (ptr && untrack(ptr)) cudaFreeAsync(ptr, st);
+}
+
+// ---------------------------------------------------------------- live handles
+// A handle is valid while it is in this registry: gsm_plan / gsm_plan_load and
+// gsm_batch_create add it, the destroy calls remove it before freeing, so a
+// destroyed handle is rejected without its memory being read.
+static std::mutex g_handle_mutex;
+static std::unordered_set<const void *> g_live_plans, g_live_batches;
+
+static void register_handle(std::unordered_set<const void *> &set, const void *h)
+{
+    std::lock_guard<std::mutex> lock(g_handle_mutex);
+    set.insert(h);
+}
+
+static bool release_handle(std::unordered_set<const void *> &set, const void *h)
+{
+    std::lock_guard<std::mutex> lock(g_handle_mutex);
+    return set.erase(h) != 0;
+}
+
+static bool is_live(const std::unordered_set<const void *> &set, const void *h)
+{
+    std::lock_guard<std::mutex> lock(g_handle_mutex);
+    return h != nullptr && set.count(h) != 0;
+}
+
 static Plan *checked(gsm_plan_t h)
 {
+    if (!is_live(g_live_plans, h)) return nullptr;
     Plan *p = reinterpret_cast<Plan *>(h);
-    if (!p || p->magic != kPlanMagic) return nullptr;
-    return p;
+    return p->magic == kPlanMagic ? p : nullptr;
 }
 
 static void free_plan(Plan *p)
 {
     if (!p) return;
-    cudaFree(p->d_w);
-    cudaFree(p->d_tau);
+    dev_free(p->d_w);
+    dev_free(p->d_tau);
     for (int a = 0; a < 3; ++a) {
         bool dup = false;
         for (int b = 0; b < a; ++b) dup |= (p->d_g[b] == p->d_g[a]);
-        if (!dup) cudaFree(p->d_g[a]);
+        if (!dup) dev_free(p->d_g[a]);
     }
     for (int a = 0; a < 3; ++a) {
         bool dup = false;
         for (int b = 0; b < a; ++b) dup |= (p->d_tw[b] == p->d_tw[a]);
-        if (!dup) cudaFree(p->d_tw[a]);
+        if (!dup) dev_free(p->d_tw[a]);
     }
-    cudaFree(p->d_khat);
-    if (p->d_mult != p->d_mult64) cudaFree(p->d_mult);
-    cudaFree(p->d_mult64);
-    cudaFree(p->d_work1);
-    cudaFree(p->d_work2);
-    cudaFree(p->d_stage_in);
-    cudaFree(p->d_stage_out);
+    dev_free(p->d_khat);
+    if (p->d_mult != p->d_mult64) dev_free(p->d_mult);
+    dev_free(p->d_mult64);
+    dev_free(p->d_work1);
+    dev_free(p->d_work2);
+    dev_free(p->d_stage_in);
+    dev_free(p->d_stage_out);
     for (cudaEvent_t e : p->copy_ev)
         if (e) cudaEventDestroy(e);
     if (p->copy_stream) cudaStreamDestroy(p->copy_stream);
-    cudaFree(p->d_scratch);
+    dev_free(p->d_scratch);
     p->magic = 0;
     delete p;
 }
@@ -209,6 +308,7 @@ static gsm_status_t create_plan(gsm_plan_t *out, gsm_kernel_t kind, int d, doubl
         free_plan(p);
         return s;
     }
+    register_handle(g_live_plans, p);
     *out = reinterpret_cast<gsm_plan_t>(p);
     return GSM_OK;
 }
@@ -476,9 +576,22 @@ gsm_status_t gsm_apply_host(gsm_plan_t h, const void *rho_host, void *u_host, vo
         GSM_CUDA_TRY(cudaStreamSynchronize(st));
         return GSM_OK;
     }
-    if (!p->d_stage_in) {
-        GSM_CUDA_TRY(cudaMalloc(&p->d_stage_in, bytes));
-        GSM_CUDA_TRY(cudaMalloc(&p->d_stage_out, bytes));
+    if (!p->d_stage_in || !p->d_stage_out) {
+        // both buffers or neither: the plan keeps them only when both exist
+        void *a = nullptr, *b = nullptr;
+        cudaError_t e = dev_alloc(&a, bytes);
+        if (e == cudaSuccess) e = dev_alloc(&b, bytes);
+        if (e != cudaSuccess) {
+            dev_free(a);
+            dev_free(b);
+            cudaGetLastError();
+            set_error(std::string("host apply staging buffers: ") + cudaGetErrorString(e));
+            return e == cudaErrorMemoryAllocation ? GSM_ERR_OOM : GSM_ERR_CUDA;
+        }
+        dev_free(p->d_stage_in);
+        dev_free(p->d_stage_out);
+        p->d_stage_in = a;
+        p->d_stage_out = b;
     }
     if (p->d != 3) {
         GSM_CUDA_TRY(cudaMemcpyAsync(p->d_stage_in, rho_host, bytes, cudaMemcpyHostToDevice, st));
@@ -493,8 +606,21 @@ gsm_status_t gsm_apply_host(gsm_plan_t h, const void *rho_host, void *u_host, vo
     // chunk c the x inverse pass of chunk c + 1 (copies on the plan's own stream,
     // ordered against `st` by events)
     if (!p->copy_stream) {
-        GSM_CUDA_TRY(cudaStreamCreateWithFlags(&p->copy_stream, cudaStreamNonBlocking));
-        for (cudaEvent_t &e : p->copy_ev) GSM_CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        // the stream and all its events, or nothing
+        cudaStream_t cs_new = nullptr;
+        cudaEvent_t ev_new[2 * kHostChunks + 2] = {};
+        cudaError_t e = cudaStreamCreateWithFlags(&cs_new, cudaStreamNonBlocking);
+        for (cudaEvent_t &ev : ev_new)
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+        if (e != cudaSuccess) {
+            for (cudaEvent_t ev : ev_new)
+                if (ev) cudaEventDestroy(ev);
+            if (cs_new) cudaStreamDestroy(cs_new);
+            set_error(std::string("host apply copy stream: ") + cudaGetErrorString(e));
+            return e == cudaErrorMemoryAllocation ? GSM_ERR_OOM : GSM_ERR_CUDA;
+        }
+        p->copy_stream = cs_new;
+        for (int i = 0; i < 2 * kHostChunks + 2; ++i) p->copy_ev[i] = ev_new[i];
     }
     cudaStream_t cs = p->copy_stream;
     const int nz = p->n[2];
@@ -606,9 +732,13 @@ gsm_status_t gsm_batch_create(gsm_batch_t *out, int count, const gsm_plan_t *pla
     int best_nl = kBatchLines;
     {
         float best_ms = 1e30f;
-        cudaEvent_t e0, e1;
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
         GSM_CUDA_TRY(cudaEventCreate(&e0));
-        GSM_CUDA_TRY(cudaEventCreate(&e1));
+        cudaError_t ec = cudaEventCreate(&e1);
+        if (ec != cudaSuccess) {
+            cudaEventDestroy(e0);
+            GSM_CUDA_TRY(ec);
+        }
         for (int nl : {4, 8}) {
             s = launch_batched(count, ps.data(), rho, u, nl, ts, true);
             if (s == GSM_OK) s = launch_batched(count, ps.data(), rho, u, nl, ts, false);
@@ -666,15 +796,16 @@ gsm_status_t gsm_batch_create(gsm_batch_t *out, int count, const gsm_plan_t *pla
     b->count = count;
     b->nl = best_nl;
     b->magic = kBatchMagic;
+    register_handle(g_live_batches, b);
     *out = reinterpret_cast<gsm_batch_t>(b);
     return GSM_OK;
 }
 
 static Batch *checked_batch(gsm_batch_t h)
 {
+    if (!is_live(g_live_batches, h)) return nullptr;
     Batch *b = reinterpret_cast<Batch *>(h);
-    if (!b || b->magic != kBatchMagic) return nullptr;
-    return b;
+    return b->magic == kBatchMagic ? b : nullptr;
 }
 
 gsm_status_t gsm_batch_launch(gsm_batch_t h, void *cuda_stream)
@@ -695,6 +826,7 @@ gsm_status_t gsm_batch_destroy(gsm_batch_t h)
         set_error("bad batch handle");
         return GSM_ERR_BAD_PLAN;
     }
+    release_handle(g_live_batches, b);
     cudaDeviceSynchronize();
     cudaGraphExecDestroy(b->exec);
     cudaGraphDestroy(b->graph);
@@ -767,6 +899,7 @@ gsm_status_t gsm_plan_destroy(gsm_plan_t h)
         set_error("bad plan handle");
         return GSM_ERR_BAD_PLAN;
     }
+    release_handle(g_live_plans, p);
     cudaDeviceSynchronize();
     free_plan(p);
     return GSM_OK;
@@ -843,6 +976,24 @@ gsm_status_t gsm_fft_lines_noalloc(int M, int nlines, int sign, gsm_precision_t 
     if (nlines == 0) return GSM_OK;
     return launch_fft_lines_noalloc(M, nlines, sign, precision, in_dev, out_dev,
                                     static_cast<cudaStream_t>(cuda_stream));
+}
+
+gsm_status_t gsm_debug_fail_alloc(int k)
+{
+    g_fail_in.store(k < 0 ? -1 : (long)k);
+    return GSM_OK;
+}
+
+gsm_status_t gsm_debug_alloc_stats(size_t *count, size_t *bytes)
+{
+    if (!count || !bytes) {
+        set_error("count or bytes is NULL");
+        return GSM_ERR_INVALID_ARG;
+    }
+    std::lock_guard<std::mutex> lock(g_alloc_mutex);
+    *count = g_alloc_live.size();
+    *bytes = g_alloc_bytes;
+    return GSM_OK;
 }
 
 }  // extern "C"

@@ -71,6 +71,31 @@ struct Plan {
 // thread-local last error
 void set_error(const std::string &msg);
 
+// Every device allocation of the library goes through these functions (gsm_api.cu).
+// They keep a count of what is live and can be told to fail (gsm_debug_fail_alloc),
+// so that the clean-up on every out-of-memory path can be tested without
+// exhausting a GPU.
+cudaError_t dev_alloc_bytes(void **ptr, size_t bytes);
+cudaError_t dev_alloc_async_bytes(void **ptr, size_t bytes, cudaStream_t st);
+void dev_free(void *ptr);
+void dev_free_async(void *ptr, cudaStream_t st);
+template <class T>
+inline cudaError_t dev_alloc(T **ptr, size_t bytes)
+{
+    return dev_alloc_bytes(reinterpret_cast<void **>(ptr), bytes);
+}
+// A temporary device buffer freed when it goes out of scope (dev_free waits
+// for the device, as cudaFree does, so kernels still using it finish first).
+struct DevTemp {
+    void *p = nullptr;
+    DevTemp() = default;
+    DevTemp(const DevTemp &) = delete;
+    DevTemp &operator=(const DevTemp &) = delete;
+    ~DevTemp() { dev_free(p); }
+    template <class T>
+    T *as() const { return static_cast<T *>(p); }
+};
+
 // Precomputed results a saved plan carries (Sec. 2.2: the sum over q of
 // w_q G_k^q is stored once per discretisation and reused).  Host arrays.
 struct StoredPlanData {

@@ -26,6 +26,8 @@
 #include <vector>
 #include <type_traits>
 
+#include <cuda.h>
+
 #include "gsm_internal.h"
 
 namespace gsm {
@@ -659,8 +661,8 @@ gsm_status_t configure_t(Plan *p)
         p->work1_bytes = cb * hx * p->n[1];
         p->work2_bytes = 0;
     }
-    GSM_CUDA_TRY(cudaMalloc(&p->d_work1, p->work1_bytes));
-    if (p->work2_bytes) GSM_CUDA_TRY(cudaMalloc(&p->d_work2, p->work2_bytes));
+    GSM_CUDA_TRY(dev_alloc(&p->d_work1, p->work1_bytes));
+    if (p->work2_bytes) GSM_CUDA_TRY(dev_alloc(&p->d_work2, p->work2_bytes));
     return GSM_OK;
 }
 
@@ -855,17 +857,14 @@ gsm_status_t autotune_t(Plan *p, cudaStream_t st, std::string *report)
     using io = typename Pol::io_t;
     size_t N = 1;
     for (int a = 0; a < p->d; ++a) N *= (size_t)p->n[a];
-    void *rho = nullptr, *u = nullptr;
-    GSM_CUDA_TRY(cudaMalloc(&rho, N * sizeof(io)));
-    cudaError_t e = cudaMalloc(&u, N * sizeof(io));
-    if (e != cudaSuccess) {
-        cudaFree(rho);
-        GSM_CUDA_TRY(e);
-    }
-    cudaMemsetAsync(rho, 0, N * sizeof(io), st);
-    cudaEvent_t e0, e1;
-    cudaEventCreate(&e0);
-    cudaEventCreate(&e1);
+    DevTemp rho_buf, u_buf;
+    GSM_CUDA_TRY(dev_alloc(&rho_buf.p, N * sizeof(io)));
+    GSM_CUDA_TRY(dev_alloc(&u_buf.p, N * sizeof(io)));
+    void *rho = rho_buf.p, *u = u_buf.p;
+    GSM_CUDA_TRY(cudaMemsetAsync(rho, 0, N * sizeof(io), st));
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
     const char *cache = getenv("GSM_AUTOTUNE_CACHE");
     const int np = p->d == 3 ? 5 : 3;
     char buf[256];
@@ -924,10 +923,8 @@ gsm_status_t autotune_t(Plan *p, cudaStream_t st, std::string *report)
             }
         }
     }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
-    cudaFree(rho);
-    cudaFree(u);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
     GSM_CUDA_TRY(e);
     GSM_CUDA_TRY(cudaGetLastError());
     return GSM_OK;
@@ -943,7 +940,7 @@ gsm_status_t fft_hook_t(int M, int nlines, int sign, const double *in, double *o
     }
     void *d_tw = nullptr;
     const size_t g8 = std::is_same<Pol, F64>::value ? g8_table_doubles(sc) : 0;
-    GSM_CUDA_TRY(cudaMallocAsync(&d_tw, sizeof(typename Pol::tw_t) * M + sizeof(double) * g8, st));
+    GSM_CUDA_TRY(dev_alloc_async_bytes(&d_tw, sizeof(typename Pol::tw_t) * M + sizeof(double) * g8, st));
     k_twiddles<<<(M + 255) / 256, 256, 0, st>>>(M, Pol::kId, d_tw);
     if (g8 > 0) launch_g8table(sc, static_cast<double2 *>(d_tw) + M, st);
     const PassCfg c = choose_cfg<Pol>(M, std::max(1, 2048 / M));
@@ -963,9 +960,9 @@ gsm_status_t fft_hook_t(int M, int nlines, int sign, const double *in, double *o
                                                                             nlines, sc, c.nl, c.gthr, tw, 1);
         }
     });
+    if (e == cudaSuccess) e = cudaGetLastError();
+    dev_free_async(d_tw, st);
     GSM_CUDA_TRY(e);
-    GSM_CUDA_TRY(cudaGetLastError());
-    GSM_CUDA_TRY(cudaFreeAsync(d_tw, st));
     return GSM_OK;
 }
 
@@ -1000,7 +997,7 @@ gsm_status_t make_twiddles(Plan *p, int axis, cudaStream_t st)
         }
     const int M = p->M[axis];
     const size_t g8 = p->opt.precision == GSM_FP64 ? g8_table_doubles(p->sched[axis]) : 0;
-    GSM_CUDA_TRY(cudaMalloc(&p->d_tw[axis], cplx_bytes(p->opt.precision) * M + sizeof(double) * g8));
+    GSM_CUDA_TRY(dev_alloc(&p->d_tw[axis], cplx_bytes(p->opt.precision) * M + sizeof(double) * g8));
     k_twiddles<<<(M + 255) / 256, 256, 0, st>>>(M, p->opt.precision, p->d_tw[axis]);
     if (g8 > 0) launch_g8table(p->sched[axis], static_cast<double2 *>(p->d_tw[axis]) + M, st);
     GSM_CUDA_TRY(cudaGetLastError());
@@ -1014,7 +1011,7 @@ gsm_status_t make_pass_multiplier(Plan *p, cudaStream_t st)
         return GSM_OK;
     }
     const size_t eb = p->opt.precision == GSM_FP32 ? sizeof(float) : sizeof(float2);
-    GSM_CUDA_TRY(cudaMalloc(&p->d_mult, eb * p->mult_elems));
+    GSM_CUDA_TRY(dev_alloc(&p->d_mult, eb * p->mult_elems));
     k_mult_convert<<<(p->mult_elems + 255) / 256, 256, 0, st>>>(p->d_mult64, p->mult_elems, p->opt.precision,
                                                                   p->d_mult);
     GSM_CUDA_TRY(cudaGetLastError());
@@ -1159,7 +1156,7 @@ static gsm_status_t hartree_t(Plan *p, const T *psi, T *u, T *energy, T *grad, c
         cell *= 2.0 * p->L * p->eta[a] / p->n[a];
     }
     if (!p->d_scratch) {
-        GSM_CUDA_TRY(cudaMalloc(&p->d_scratch, sizeof(double) * kEnergyBlocks));
+        GSM_CUDA_TRY(dev_alloc(&p->d_scratch, sizeof(double) * kEnergyBlocks));
         p->scratch_elems = kEnergyBlocks;
     }
     k_psi_to_rho<T><<<kEnergyBlocks, 256, 0, st>>>(psi, u, N);
@@ -1179,35 +1176,73 @@ gsm_status_t launch_hartree(Plan *p, const void *psi, void *u, void *energy, voi
 }
 
 // ------------------------------------------------------------------ no-allocation FFT
-// Scratch of gsm_fft_lines_noalloc: the twiddle table of one transform length,
-// up to 8192 entries of 16 bytes (FP64 or double-float pairs).  A file-scope
-// __device__ array, so every GPU that loads this library holds these 128 KiB
-// until the process exits; every call shares it.
+// Scratch of gsm_fft_lines_noalloc: the tables of one transform length, the M
+// twiddles (16-byte entries in FP64 and double-float, 8-byte in FP32) followed,
+// in FP64, by the constants of the FMA-form stages, exactly as gsm_fft_lines
+// builds them in its own allocation.  The largest need is M = 8192 in FP64,
+// 131072 + 208896 = 339968 bytes.  A file-scope __device__ array, so every GPU
+// that loads this library holds these 384 KiB until the process exits; every
+// call shares it.
 namespace {
 
-constexpr size_t kStaticTwiddleBytes = 8192 * 16;
-__device__ __align__(256) unsigned char g_static_twiddles[kStaticTwiddleBytes];
+constexpr size_t kStaticScratchBytes = 384 * 1024;
+__device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
 
-constexpr int kMaxDevices = 64;
+typedef CUresult (*CtxGetCurrentFn)(CUcontext *);
+typedef CUresult (*CtxGetIdFn)(CUcontext, unsigned long long *);
+
+// Identifier of the calling thread's current context (unique for the life of
+// the process), or 0 if the driver does not give one.
+unsigned long long current_context_id()
+{
+    static CtxGetCurrentFn get_current = nullptr;
+    static CtxGetIdFn get_id = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_current = reinterpret_cast<CtxGetCurrentFn>(f);
+        f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_id = reinterpret_cast<CtxGetIdFn>(f);
+        cudaGetLastError();
+    });
+    CUcontext ctx = nullptr;
+    unsigned long long id = 0;
+    if (!get_current || !get_id || get_current(&ctx) != CUDA_SUCCESS || !ctx || get_id(ctx, &id) != CUDA_SUCCESS)
+        return 0;
+    return id;
+}
+
 std::mutex g_static_mutex;
-void *g_static_addr[kMaxDevices] = {};
+std::vector<std::pair<unsigned long long, void *>> g_static_addr;   // (context id, device address)
 
-// The host-side name g_static_twiddles is not a device address; the device
-// address is looked up once per device, with that device current.
-cudaError_t static_twiddle_address(void **out)
+// The host-side name g_static_scratch is not a device address.  The device
+// address is looked up with cudaGetSymbolAddress, with the caller's device
+// current, once per context (device, or a new primary context after
+// cudaDeviceReset), and remembered; while no context id is available (before
+// the runtime has made one current) it is looked up on every call.
+cudaError_t static_scratch_address(void **out)
 {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
-    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    const unsigned long long ctx = current_context_id();
     std::lock_guard<std::mutex> lock(g_static_mutex);
-    if (!g_static_addr[dev]) {
-        void *p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_static_twiddles);
-        if (e != cudaSuccess) return e;
-        g_static_addr[dev] = p;
-    }
-    *out = g_static_addr[dev];
+    if (ctx != 0)
+        for (const auto &kv : g_static_addr)
+            if (kv.first == ctx) {
+                *out = kv.second;
+                return cudaSuccess;
+            }
+    void *p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_static_scratch);
+    if (e != cudaSuccess) return e;
+    if (ctx != 0) g_static_addr.emplace_back(ctx, p);
+    *out = p;
     return cudaSuccess;
 }
 
@@ -1219,14 +1254,18 @@ gsm_status_t fft_hook_static_t(int M, int nlines, int sign, const double *in, do
         set_error("FFT length must be a product of 2, 3, 5 between 2 and 8192");
         return GSM_ERR_UNSUPPORTED_SIZE;
     }
-    if (sizeof(typename Pol::tw_t) * (size_t)M > kStaticTwiddleBytes) {
-        set_error("FFT length exceeds the 128 KiB static twiddle scratch (M <= 8192)");
+    const size_t g8 = std::is_same<Pol, F64>::value ? g8_table_doubles(sc) : 0;
+    const size_t need = sizeof(typename Pol::tw_t) * (size_t)M + sizeof(double) * g8;
+    if (need > kStaticScratchBytes) {
+        set_error("FFT tables exceed the 384 KiB static scratch (M <= 8192)");
         return GSM_ERR_UNSUPPORTED_SIZE;
     }
     void *d_tw = nullptr;
-    GSM_CUDA_TRY(static_twiddle_address(&d_tw));
-    // every entry the FFT reads is written here first: nothing needs clearing
+    GSM_CUDA_TRY(static_scratch_address(&d_tw));
+    // the same tables gsm_fft_lines builds, so the same arithmetic and the same
+    // bits; every entry the FFT reads is written here first: nothing needs clearing
     k_twiddles<<<(M + 255) / 256, 256, 0, st>>>(M, Pol::kId, d_tw);
+    if (g8 > 0) launch_g8table(sc, static_cast<double2 *>(d_tw) + M, st);
     const PassCfg c = choose_cfg<Pol>(M, std::max(1, 2048 / M));
     const auto *tw = static_cast<const typename Pol::tw_t *>(d_tw);
     const int blocks = (nlines + c.nl - 1) / c.nl;
@@ -1236,12 +1275,12 @@ gsm_status_t fft_hook_static_t(int M, int nlines, int sign, const double *in, do
             e = raise_smem(k_fft_hook<Pol, true, E()>, c.smem);
             if (e == cudaSuccess)
                 k_fft_hook<Pol, true, E()><<<blocks, c.nthr, c.smem, st>>>((const double2 *)in, (double2 *)out,
-                                                                           nlines, sc, c.nl, c.gthr, tw, 0);
+                                                                           nlines, sc, c.nl, c.gthr, tw, 1);
         } else {
             e = raise_smem(k_fft_hook<Pol, false, E()>, c.smem);
             if (e == cudaSuccess)
                 k_fft_hook<Pol, false, E()><<<blocks, c.nthr, c.smem, st>>>((const double2 *)in, (double2 *)out,
-                                                                            nlines, sc, c.nl, c.gthr, tw, 0);
+                                                                            nlines, sc, c.nl, c.gthr, tw, 1);
         }
     });
     GSM_CUDA_TRY(e);

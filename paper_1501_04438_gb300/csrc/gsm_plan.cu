@@ -571,8 +571,8 @@ gsm_status_t build_plan_data(Plan *p, cudaStream_t st, const StoredPlanData *sto
     const int kind_gs = p->kind == GSM_DIPOLAR_3D ? GSM_COULOMB_3D
                         : (p->kind == GSM_DAVEY_STEWARTSON_2D ? GSM_POISSON_2D : p->kind);
 
-    GSM_CUDA_TRY(cudaMalloc(&p->d_w, sizeof(double) * kGsCap));
-    GSM_CUDA_TRY(cudaMalloc(&p->d_tau, sizeof(double) * kGsCap));
+    GSM_CUDA_TRY(dev_alloc(&p->d_w, sizeof(double) * kGsCap));
+    GSM_CUDA_TRY(dev_alloc(&p->d_tau, sizeof(double) * kGsCap));
     GsSpec gs;
     gs.kind = kind_gs;
     gs.delta = delta;
@@ -599,10 +599,11 @@ gsm_status_t build_plan_data(Plan *p, cudaStream_t st, const StoredPlanData *sto
         // the same scan ran for an earlier plan in this process
     } else {
         const int S_request = S;
-        double *d_err = nullptr;
+        DevTemp err_buf;
         const int S_first = 4;
         const int count = kSmax - S_first + 1;
-        GSM_CUDA_TRY(cudaMalloc(&d_err, sizeof(double) * count));
+        GSM_CUDA_TRY(dev_alloc(&err_buf.p, sizeof(double) * count));
+        double *d_err = err_buf.as<double>();
         std::vector<double> h(count, INFINITY);
         const int windows[3][2] = {{S_first, 160}, {161, 320}, {321, kSmax}};
         bool found = false;
@@ -617,7 +618,6 @@ gsm_status_t build_plan_data(Plan *p, cudaStream_t st, const StoredPlanData *sto
                                             sizeof(double) * (b - a + 1), cudaMemcpyDeviceToHost, st);
             if (e == cudaSuccess) e = cudaStreamSynchronize(st);
             if (e != cudaSuccess) {
-                cudaFree(d_err);
                 set_error(std::string("Gaussian-sum scan: ") + cudaGetErrorString(e));
                 return GSM_ERR_CUDA;
             }
@@ -630,7 +630,6 @@ gsm_status_t build_plan_data(Plan *p, cudaStream_t st, const StoredPlanData *sto
                 }
             }
         }
-        cudaFree(d_err);
         if (!found) {
             set_error("no Gaussian sum with S <= 500 meets the requested accuracy");
             return GSM_ERR_ACCURACY;
@@ -648,9 +647,10 @@ gsm_status_t build_plan_data(Plan *p, cudaStream_t st, const StoredPlanData *sto
     }
 
     // 2. 1-D factors per axis
-    double *d_weid = nullptr;
-    GSM_CUDA_TRY(cudaMalloc(&d_weid, sizeof(double) * kWeidN));
-    k_weideman<<<1, kWeidN, 0, st>>>(d_weid);
+    DevTemp weid_buf;
+    GSM_CUDA_TRY(dev_alloc(&weid_buf.p, sizeof(double) * kWeidN));
+    const double *d_weid = weid_buf.as<double>();
+    k_weideman<<<1, kWeidN, 0, st>>>(weid_buf.as<double>());
     for (int a = 0; a < d; ++a) {
         const int nk = p->n[a] + 1;
         bool same = false;
@@ -661,7 +661,7 @@ gsm_status_t build_plan_data(Plan *p, cudaStream_t st, const StoredPlanData *sto
                 break;
             }
         if (same) continue;
-        GSM_CUDA_TRY(cudaMalloc(&p->d_g[a], sizeof(double) * p->nterms * nk));
+        GSM_CUDA_TRY(dev_alloc(&p->d_g[a], sizeof(double) * p->nterms * nk));
         const long tot = (long)p->nterms * nk;
         k_factors<<<(tot + 127) / 128, 128, 0, st>>>(p->nterms, p->d_tau, nk, p->eta[a], d_weid, p->d_g[a]);
     }
@@ -669,18 +669,16 @@ gsm_status_t build_plan_data(Plan *p, cudaStream_t st, const StoredPlanData *sto
     // 3. Taylor coefficients
     if (stored) {
         GSM_CUDA_TRY(cudaStreamSynchronize(st));
-        cudaFree(d_weid);
         p->c0 = stored->c0;
         p->c2 = stored->c2;
     } else {
-        double *d_c = nullptr;
-        GSM_CUDA_TRY(cudaMalloc(&d_c, sizeof(double) * 2));
-        k_taylor<<<1, 256, 0, st>>>(kind_gs, p->opt.beta, d, p->nterms, p->d_w, p->d_tau, delta, d_c);
+        DevTemp c_buf;
+        GSM_CUDA_TRY(dev_alloc(&c_buf.p, sizeof(double) * 2));
+        k_taylor<<<1, 256, 0, st>>>(kind_gs, p->opt.beta, d, p->nterms, p->d_w, p->d_tau, delta,
+                                    c_buf.as<double>());
         double hc[2];
-        GSM_CUDA_TRY(cudaMemcpyAsync(hc, d_c, sizeof(hc), cudaMemcpyDeviceToHost, st));
+        GSM_CUDA_TRY(cudaMemcpyAsync(hc, c_buf.p, sizeof(hc), cudaMemcpyDeviceToHost, st));
         GSM_CUDA_TRY(cudaStreamSynchronize(st));
-        cudaFree(d_c);
-        cudaFree(d_weid);
         p->c0 = hc[0];
         p->c2 = hc[1];
     }
@@ -689,8 +687,8 @@ gsm_status_t build_plan_data(Plan *p, cudaStream_t st, const StoredPlanData *sto
     size_t tot = 1;
     for (int a = 0; a < d; ++a) tot *= (size_t)(p->n[a] + 1);
     p->mult_elems = tot;
-    GSM_CUDA_TRY(cudaMalloc(&p->d_khat, sizeof(double) * tot));
-    GSM_CUDA_TRY(cudaMalloc(&p->d_mult64, sizeof(double) * tot));
+    GSM_CUDA_TRY(dev_alloc(&p->d_khat, sizeof(double) * tot));
+    GSM_CUDA_TRY(dev_alloc(&p->d_mult64, sizeof(double) * tot));
     if (stored)
         GSM_CUDA_TRY(cudaMemcpyAsync(p->d_khat, stored->khat, sizeof(double) * tot, cudaMemcpyHostToDevice, st));
     else
@@ -748,7 +746,7 @@ gsm_status_t build_plan_data(Plan *p, cudaStream_t st, const StoredPlanData *sto
         dp.prec = p->opt.precision;
         const size_t full = (size_t)(p->n[0] + 1) * p->M[1] * p->M[2];
         const size_t eb = p->opt.precision == GSM_FP32 ? sizeof(float) : sizeof(double);
-        GSM_CUDA_TRY(cudaMalloc(&p->d_mult, eb * full));
+        GSM_CUDA_TRY(dev_alloc(&p->d_mult, eb * full));
         p->mult_full = true;
         p->mult_elems_pass = full;
         k_multiplier_dip_full<<<(full + 255) / 256, 256, 0, st>>>(dp, p->d_mult64, p->d_mult);
