@@ -52,6 +52,7 @@ def args_parse():
     ap.add_argument("--ref-n", type=int, default=128, help="grid of the reference arm's bounded sample")
     ap.add_argument("--suite", action="store_true",
                     help="measure every config (one JSON line each) instead of the headline line")
+    ap.add_argument("--configs", default="1,2,3,4,5", help="with --suite: which configs to run (comma list)")
     return ap.parse_args()
 
 
@@ -522,79 +523,90 @@ def run_suite(a):
             plan.destroy()
         return out
 
-    # config 1: 3D Coulomb 32^3 on [-8,8]^3, exp(-|x|^2) (the closed-form checks are in the tests)
-    rho = wl.coulomb3d_gaussian(32, 8.0, 1.0)
-    prep = oracle.Prepared("coulomb3d", 32, 8.0)
-    uo, cpu = _cpu_leg(lambda: prep.run(rho), 32 ** 3, "the whole 32^3 config, apply only")
-    line = precisions_line("1", "coulomb3d", rho, 8.0, (32, 32, 32), uo)
-    line["cpu_baseline"] = cpu
-    emit(line)
+    want = {c.strip() for c in a.configs.split(",")}
 
-    # config 2: 3D Coulomb on [-12,12]^3, anisotropic and 8-Gaussian mixture, 128^3 and 256^3
-    for n in (128, 256):
-        for name, rho in (("2a anisotropic", wl.coulomb3d_anisotropic(n, 12.0, 4.0)),
-                          ("2b mixture8", wl.coulomb3d_mixture(n, 12.0))):
-            prep = oracle.Prepared("coulomb3d", n, 12.0)
-            uo, cpu = _cpu_leg(lambda: prep.run(rho), n ** 3, f"the whole {n}^3 config, apply only")
-            line = precisions_line(name, "coulomb3d", rho, 12.0, (n, n, n), uo)
-            line["cpu_baseline"] = cpu
-            emit(line)
+    if "1" in want:
+        # config 1: 3D Coulomb 32^3 on [-8,8]^3, exp(-|x|^2) (the closed-form checks are in the tests)
+        rho = wl.coulomb3d_gaussian(32, 8.0, 1.0)
+        prep = oracle.Prepared("coulomb3d", 32, 8.0)
+        uo, cpu = _cpu_leg(lambda: prep.run(rho), 32 ** 3, "the whole 32^3 config, apply only")
+        line = precisions_line("1", "coulomb3d", rho, 8.0, (32, 32, 32), uo)
+        line["cpu_baseline"] = cpu
+        emit(line)
 
-    # config 3: 2D Poisson and Coulomb on [-16,16]^2, 1024^2 and 4096^2, 6 isotropic Gaussians
-    params = wl.mixture2d_params()
-    for n in (1024, 4096):
-        rho = wl.mixture((n, n), 16.0, params)
-        for kernel in ("poisson2d", "coulomb2d"):
-            prep = oracle.Prepared(kernel, n, 16.0)
-            uo, cpu = _cpu_leg(lambda: prep.run(rho), n * n, f"the whole {n}^2 config, apply only")
-            line = precisions_line("3", kernel, rho, 16.0, (n, n), uo)
-            line["cpu_baseline"] = cpu
-            emit(line)
+    if "2" in want:
+        # config 2: 3D Coulomb on [-12,12]^3, anisotropic and 8-Gaussian mixture, 128^3 and 256^3
+        for n in (128, 256):
+            for name, rho in (("2a anisotropic", wl.coulomb3d_anisotropic(n, 12.0, 4.0)),
+                              ("2b mixture8", wl.coulomb3d_mixture(n, 12.0))):
+                prep = oracle.Prepared("coulomb3d", n, 12.0)
+                uo, cpu = _cpu_leg(lambda: prep.run(rho), n ** 3, f"the whole {n}^3 config, apply only")
+                line = precisions_line(name, "coulomb3d", rho, 12.0, (n, n, n), uo)
+                line["cpu_baseline"] = cpu
+                emit(line)
 
-    # config 4: 48 densities, n in {48,64,96,128,160}, [-10,10]^3, 4 Gaussians each
-    specs = wl.batch_specs()
-    for prec in ("fp64", "fp32"):
-        dt = torch.float32 if prec == "fp32" else torch.float64
-        t0 = time.perf_counter()
-        plans = [gsm.Plan("coulomb3d", 10.0, n, precision=prec, stream=stream) for n, _ in specs]
-        plan_s = time.perf_counter() - t0
-        for p in plans:
-            p.autotune(stream=stream)
-        rhos = [torch.tensor(wl.mixture((n, n, n), 10.0, prm), dtype=dt, device=dev) for n, prm in specs]
-        outs = [torch.empty_like(r) for r in rhos]
-        npts = sum(n ** 3 for n, _ in specs)
-        ms_loop = _time_apply(torch, lambda: [p.apply(r, o, stream=stream) for p, r, o in zip(plans, rhos, outs)],
-                              steps, flush, stream)
-        loop_out = [o.clone() for o in outs]
-        ms_grouped = _time_apply(torch, lambda: gsm.apply_batched(plans, rhos, outs, stream=stream), steps, flush,
-                                 stream)
-        same = all(torch.equal(x, y) for x, y in zip(outs, loop_out))
-        batch = gsm.Batch(plans, rhos, outs, stream=stream)
-        ms_graph = _time_apply(torch, lambda: batch.launch(stream=stream), steps, flush, stream)
-        same_graph = all(torch.equal(x, y) for x, y in zip(outs, loop_out))
-        # CPU-baseline leg on three of the instances, also the parity sample
-        errs, cpu_s, cpu_pts = [], 0.0, 0
-        for i in (0, len(specs) // 2, len(specs) - 1):
-            n, prm = specs[i]
-            prep = oracle.Prepared("coulomb3d", n, 10.0, taylor_mode=1)
-            rho_i = wl.mixture((n, n, n), 10.0, prm)
-            uo, cpu_i = _cpu_leg(lambda: prep.run(rho_i), n ** 3, "")
-            cpu_s += cpu_i["seconds"]
-            cpu_pts += n ** 3
-            errs.append(relmax(outs[i].double().cpu().numpy(), uo))
-        cpu = dict(cpu_i, value=cpu_pts / cpu_s / 1e6, seconds=cpu_s,
-                   sample="instances 0, 24 and 47 of the 48, apply only")
-        emit({"config": "4 batch48", "precision": prec, "instances": len(specs),
-              "sizes": [n for n, _ in specs], "points": npts,
-              "loop": {"ms": ms_loop, "Mpts_s": npts / ms_loop / 1e3},
-              "grouped": {"ms": ms_grouped, "Mpts_s": npts / ms_grouped / 1e3, "bitwise_equal_loop": same},
-              "graph": {"ms": ms_graph, "Mpts_s": npts / ms_graph / 1e3, "bitwise_equal_loop": same_graph},
-              "rel_err_vs_oracle_sampled": errs, "cpu_baseline": cpu, "plans_s": plan_s})
-        batch.destroy()
-        for p in plans:
-            p.destroy()
-        del rhos, outs, loop_out
+    if "3" in want:
+        # config 3: 2D Poisson and Coulomb on [-16,16]^2, 1024^2 and 4096^2, 6 isotropic Gaussians
+        params = wl.mixture2d_params()
+        for n in (1024, 4096):
+            rho = wl.mixture((n, n), 16.0, params)
+            for kernel in ("poisson2d", "coulomb2d"):
+                prep = oracle.Prepared(kernel, n, 16.0)
+                uo, cpu = _cpu_leg(lambda: prep.run(rho), n * n, f"the whole {n}^2 config, apply only")
+                line = precisions_line("3", kernel, rho, 16.0, (n, n), uo)
+                line["cpu_baseline"] = cpu
+                emit(line)
 
+    if "4" in want:
+        # config 4: 48 densities, n in {48,64,96,128,160}, [-10,10]^3, 4 Gaussians each
+        specs = wl.batch_specs()
+        for prec in ("fp64", "fp32"):
+            dt = torch.float32 if prec == "fp32" else torch.float64
+            t0 = time.perf_counter()
+            plans = [gsm.Plan("coulomb3d", 10.0, n, precision=prec, stream=stream) for n, _ in specs]
+            plan_s = time.perf_counter() - t0
+            for p in plans:
+                p.autotune(stream=stream)
+            rhos = [torch.tensor(wl.mixture((n, n, n), 10.0, prm), dtype=dt, device=dev) for n, prm in specs]
+            outs = [torch.empty_like(r) for r in rhos]
+            npts = sum(n ** 3 for n, _ in specs)
+            ms_loop = _time_apply(torch, lambda: [p.apply(r, o, stream=stream) for p, r, o in zip(plans, rhos, outs)],
+                                  steps, flush, stream)
+            loop_out = [o.clone() for o in outs]
+            ms_grouped = _time_apply(torch, lambda: gsm.apply_batched(plans, rhos, outs, stream=stream), steps, flush,
+                                     stream)
+            same = all(torch.equal(x, y) for x, y in zip(outs, loop_out))
+            batch = gsm.Batch(plans, rhos, outs, stream=stream)
+            ms_graph = _time_apply(torch, lambda: batch.launch(stream=stream), steps, flush, stream)
+            batch.wait(stream=stream)          # raises if a bounded wait of the last launch ran out
+            same_graph = all(torch.equal(x, y) for x, y in zip(outs, loop_out))
+            # CPU-baseline leg on three of the instances, also the parity sample
+            errs, cpu_s, cpu_pts = [], 0.0, 0
+            for i in (0, len(specs) // 2, len(specs) - 1):
+                n, prm = specs[i]
+                prep = oracle.Prepared("coulomb3d", n, 10.0, taylor_mode=1)
+                rho_i = wl.mixture((n, n, n), 10.0, prm)
+                uo, cpu_i = _cpu_leg(lambda: prep.run(rho_i), n ** 3, "")
+                cpu_s += cpu_i["seconds"]
+                cpu_pts += n ** 3
+                errs.append(relmax(outs[i].double().cpu().numpy(), uo))
+            cpu = dict(cpu_i, value=cpu_pts / cpu_s / 1e6, seconds=cpu_s,
+                       sample="instances 0, 24 and 47 of the 48, apply only")
+            emit({"config": "4 batch48", "precision": prec, "instances": len(specs),
+                  "sizes": [n for n, _ in specs], "points": npts,
+                  "loop": {"ms": ms_loop, "Mpts_s": npts / ms_loop / 1e3},
+                  "persistent": {"ms": ms_grouped, "Mpts_s": npts / ms_grouped / 1e3, "bitwise_equal_loop": same,
+                                 "call": "gsm_apply_batched: one persistent launch, status read back"},
+                  "graph": {"ms": ms_graph, "Mpts_s": npts / ms_graph / 1e3, "bitwise_equal_loop": same_graph,
+                            "call": "gsm_batch_launch: the persistent launch recorded in a CUDA graph"},
+                  "rel_err_vs_oracle_sampled": errs, "cpu_baseline": cpu, "plans_s": plan_s})
+            batch.destroy()
+            for p in plans:
+                p.destroy()
+            del rhos, outs, loop_out
+
+    if "5" not in want:
+        return
     # config 5: 192^3 on [-12,12]^3, Hartree energy and gradient, Coulomb and dipolar (n = m = e_z)
     from paper_1501_04438_gb300.autograd import hartree_energy
     n, L = 192, 12.0

@@ -209,33 +209,48 @@ gsm_status_t gsm_apply_host(gsm_plan_t p, const void *rho_host, void *u_host, vo
 
 /*
  * Apply `count` plans to their densities in one call: u[i] = U_i * rho[i].
+ * (No counterpart in the paper, which treats one density at a time.)
  * Plans may differ in size, kernel and precision (each uses its own I/O type)
- * but must be distinct handles.  Plans whose padded lengths are all <= 512
- * are grouped by precision and dimension: each pass is ONE launch over up to
- * 48 instances of different sizes (one warp per FFT line, one CTA shape for
- * all sizes); other plans, and FP32 plans with a padded length of exactly 512
- * (which use register-resident kernels of their own), are applied one by one.
- * The results are the same
- * bits as gsm_apply's.  Errors as in gsm_apply; nothing is launched if any
- * argument is invalid.  (No counterpart in the paper, which treats one
- * density at a time.)
+ * but must be distinct handles.  Plans whose padded lengths are all <= 512 go
+ * through ONE persistent kernel launch per precision and dimension (up to 48
+ * instances per launch): its CTAs take work items (pass, instance, tile) from
+ * a device queue in pass-major order and run each once the instance's
+ * previous pass is complete, so the passes of different instances overlap
+ * and no launch boundary separates them.  Other plans, and FP32 plans with a
+ * padded length of exactly 512 (which use register-resident kernels of their
+ * own), are applied one by one on the stream.  The results are the same bits
+ * as gsm_apply's.
+ * Each wait of the persistent kernel for a previous pass is bounded (10 s by
+ * default): if one runs out, the kernel stops taking work, every CTA returns,
+ * and the call reports GSM_ERR_TIMEOUT (the outputs are then not valid).  The
+ * order in which work is taken guarantees that every wait ends, so the bound
+ * is a safeguard, never reached in normal operation.
+ * The call takes its queue state (about 1 KB per instance) from the stream-
+ * ordered allocator, and synchronises `cuda_stream` before it returns, to read
+ * the kernel's status.  Errors: as gsm_apply, GSM_ERR_OOM, GSM_ERR_TIMEOUT;
+ * nothing is launched if any argument is invalid.
  */
 gsm_status_t gsm_apply_batched(int count, const gsm_plan_t *plans, const void *const *rho,
                                void *const *u, void *cuda_stream);
 
 /*
- * The same batched apply recorded once into a CUDA graph, so that every later
- * run is a single cudaGraphLaunch.  The graph holds the given rho[i] and u[i]
- * pointers and each plan's workspace: refill the same rho arrays between
- * launches; the plans must outlive the batch, and no other apply may be in
- * flight on them while the batch runs.  gsm_batch_create first runs the batch
- * on `cuda_stream` with 4 and with 8 lines per CTA, keeps the faster shape
- * (so u is written), then records the graph; it synchronises the stream.
- * gsm_batch_launch is asynchronous on its stream.
+ * The same batched apply recorded once into a CUDA graph (a memset of the
+ * queue state and the persistent launches), so that every later run is a
+ * single cudaGraphLaunch.  The graph holds the given rho[i] and u[i] pointers
+ * and each plan's workspace: refill the same rho arrays between launches; the
+ * plans must outlive the batch, and no other apply may be in flight on them
+ * while the batch runs.  gsm_batch_create first runs the batch on
+ * `cuda_stream` with 4 and with 8 lines per CTA, keeps the faster shape (so u
+ * is written), then records the graph; it synchronises the stream and owns
+ * the queue state (device memory) until gsm_batch_destroy.
+ * gsm_batch_launch is asynchronous on its stream.  gsm_batch_wait synchronises
+ * `cuda_stream` and reports the last launch's status: GSM_OK, or
+ * GSM_ERR_TIMEOUT if a bounded wait ran out (see gsm_apply_batched).
  */
 gsm_status_t gsm_batch_create(gsm_batch_t *out, int count, const gsm_plan_t *plans,
                               const void *const *rho, void *const *u, void *cuda_stream);
 gsm_status_t gsm_batch_launch(gsm_batch_t b, void *cuda_stream);
+gsm_status_t gsm_batch_wait(gsm_batch_t b, void *cuda_stream);
 gsm_status_t gsm_batch_destroy(gsm_batch_t b);
 
 /*
@@ -355,6 +370,16 @@ gsm_status_t gsm_fft_lines_noalloc(int M, int nlines, int sign, gsm_precision_t 
  * temporaries), process-wide.  GSM_ERR_INVALID_ARG if a pointer is NULL. */
 gsm_status_t gsm_debug_fail_alloc(int k);
 gsm_status_t gsm_debug_alloc_stats(size_t *count, size_t *bytes);
+
+/* Test hook of the persistent batch kernel (gsm_apply_batched,
+ * gsm_batch_create), read when a batch is launched or recorded:
+ * wait_ns > 0 bounds every wait by that many nanoseconds (<= 0: the default
+ * 10 s); hold_instance >= 0 keeps the first pass of that instance (its index
+ * among the grouped plans of the call, in order) from ever counting as
+ * complete, so that the waits of its second pass run out and the call reports
+ * GSM_ERR_TIMEOUT after wait_ns, with every CTA returning; -1 turns it off.
+ * Nothing is left waiting after the call.  Process-wide.  Always GSM_OK. */
+gsm_status_t gsm_debug_batch_wait(long long wait_ns, int hold_instance);
 
 #ifdef __cplusplus
 }

@@ -348,6 +348,12 @@ class Batch:
         _abi.check(_abi.load().gsm_batch_launch(self._h, _stream_ptr(stream)))
         return self.outs
 
+    def wait(self, stream=None):
+        """Synchronise `stream` and raise GSMError (GSM_ERR_TIMEOUT) if a bounded
+        wait of the last launch ran out (gsm_batch_wait)."""
+        _abi.check(_abi.load().gsm_batch_wait(self._h, _stream_ptr(stream)))
+        return self.outs
+
     def destroy(self):
         if getattr(self, "_h", None) is not None:
             _abi.load().gsm_batch_destroy(self._h)

@@ -20,7 +20,8 @@ EXPORTS = ["gsm_default_options", "gsm_plan", "gsm_apply", "gsm_apply_pass", "gs
            "gsm_hartree", "gsm_plan_info", "gsm_plan_destroy", "gsm_status_string", "gsm_last_error",
            "gsm_plan_gs_terms", "gsm_plan_kernel_tensor", "gsm_plan_factors", "gsm_fft_lines",
            "gsm_fft_lines_noalloc", "gsm_batch_create", "gsm_batch_launch", "gsm_batch_destroy",
-           "gsm_plan_save", "gsm_plan_load", "gsm_debug_fail_alloc", "gsm_debug_alloc_stats"]
+           "gsm_plan_save", "gsm_plan_load", "gsm_debug_fail_alloc", "gsm_debug_alloc_stats",
+           "gsm_batch_wait", "gsm_debug_batch_wait"]
 
 
 class Options(ctypes.Structure):
@@ -77,6 +78,8 @@ def load(path: str = LIB_PATH):
                                        ctypes.POINTER(_vp), _vp]
         L.gsm_batch_launch.argtypes = [_vp, _vp]
         L.gsm_batch_destroy.argtypes = [_vp]
+        L.gsm_batch_wait.argtypes = [_vp, _vp]
+        L.gsm_debug_batch_wait.argtypes = [ctypes.c_longlong, ctypes.c_int]
         L.gsm_hartree.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp]
         L.gsm_plan_info.argtypes = [_vp, ctypes.POINTER(PlanInfo)]
         L.gsm_plan_destroy.argtypes = [_vp]

@@ -693,7 +693,17 @@ gsm_status_t gsm_apply_batched(int count, const gsm_plan_t *plans, const void *c
     std::vector<const Plan *> ps;
     gsm_status_t s = check_batch_args(count, plans, rho, u, &ps);
     if (s != GSM_OK || count == 0) return s;
-    return launch_batched(count, ps.data(), rho, u, kBatchLines, static_cast<cudaStream_t>(cuda_stream), false);
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    void *state = nullptr;
+    GSM_CUDA_TRY(dev_alloc_async_bytes(&state, batch_state_bytes(count), st));
+    s = launch_batched(count, ps.data(), rho, u, kBatchLines, st, false, static_cast<unsigned *>(state));
+    if (s != GSM_OK) {
+        dev_free_async(state, st);
+        return s;
+    }
+    s = batch_status(static_cast<const unsigned *>(state), count, st);
+    dev_free_async(state, st);
+    return s;
 }
 
 }  // extern "C"
@@ -705,7 +715,8 @@ struct Batch {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     int count = 0;
-    int nl = 0;   // lines (warps) per CTA chosen by timing
+    int nl = 0;               // lines (warps) per CTA chosen by timing
+    unsigned *state = nullptr;   // work-queue state of the recorded launches
 };
 }  // namespace gsm
 
@@ -729,26 +740,31 @@ gsm_status_t gsm_batch_create(gsm_batch_t *out, int count, const gsm_plan_t *pla
     // kernels are prepared outside the capture, and the lines per CTA of the
     // grouped launches (4 or 8 warps) are chosen by timing both on the stream
     cudaStream_t ts = static_cast<cudaStream_t>(cuda_stream);
+    unsigned *state = nullptr;
+    GSM_CUDA_TRY(dev_alloc(&state, batch_state_bytes(count)));
     int best_nl = kBatchLines;
     {
         float best_ms = 1e30f;
         cudaEvent_t e0 = nullptr, e1 = nullptr;
-        GSM_CUDA_TRY(cudaEventCreate(&e0));
-        cudaError_t ec = cudaEventCreate(&e1);
+        cudaError_t ec = cudaEventCreate(&e0);
+        if (ec == cudaSuccess) ec = cudaEventCreate(&e1);
         if (ec != cudaSuccess) {
-            cudaEventDestroy(e0);
+            if (e0) cudaEventDestroy(e0);
+            dev_free(state);
             GSM_CUDA_TRY(ec);
         }
         for (int nl : {4, 8}) {
-            s = launch_batched(count, ps.data(), rho, u, nl, ts, true);
-            if (s == GSM_OK) s = launch_batched(count, ps.data(), rho, u, nl, ts, false);
+            s = launch_batched(count, ps.data(), rho, u, nl, ts, true, state);
+            if (s == GSM_OK) s = launch_batched(count, ps.data(), rho, u, nl, ts, false, state);
             cudaEventRecord(e0, ts);
-            if (s == GSM_OK) s = launch_batched(count, ps.data(), rho, u, nl, ts, false);
+            if (s == GSM_OK) s = launch_batched(count, ps.data(), rho, u, nl, ts, false, state);
             cudaEventRecord(e1, ts);
             cudaError_t e = cudaEventSynchronize(e1);
+            if (s == GSM_OK && e == cudaSuccess) s = batch_status(state, count, ts);
             if (s != GSM_OK || e != cudaSuccess) {
                 cudaEventDestroy(e0);
                 cudaEventDestroy(e1);
+                dev_free(state);
                 if (s == GSM_OK) {
                     set_error(std::string("batch timing: ") + cudaGetErrorString(e));
                     s = GSM_ERR_CUDA;
@@ -766,16 +782,22 @@ gsm_status_t gsm_batch_create(gsm_batch_t *out, int count, const gsm_plan_t *pla
         cudaEventDestroy(e1);
     }
     cudaStream_t cs;
-    GSM_CUDA_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    cudaError_t ecs = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    if (ecs != cudaSuccess) {
+        dev_free(state);
+        GSM_CUDA_TRY(ecs);
+    }
     Batch *b = new (std::nothrow) Batch();
     if (!b) {
         cudaStreamDestroy(cs);
+        dev_free(state);
         set_error("host allocation failed");
         return GSM_ERR_OOM;
     }
+    b->state = state;
     cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
-        s = launch_batched(count, ps.data(), rho, u, best_nl, cs, false);
+        s = launch_batched(count, ps.data(), rho, u, best_nl, cs, false, state);
         cudaGraph_t g = nullptr;
         cudaError_t e2 = cudaStreamEndCapture(cs, &g);
         if (s == GSM_OK && e2 != cudaSuccess) e = e2;
@@ -790,6 +812,7 @@ gsm_status_t gsm_batch_create(gsm_batch_t *out, int count, const gsm_plan_t *pla
     if (s != GSM_OK) {
         if (b->exec) cudaGraphExecDestroy(b->exec);
         if (b->graph) cudaGraphDestroy(b->graph);
+        dev_free(b->state);
         delete b;
         return s;
     }
@@ -819,6 +842,16 @@ gsm_status_t gsm_batch_launch(gsm_batch_t h, void *cuda_stream)
     return GSM_OK;
 }
 
+gsm_status_t gsm_batch_wait(gsm_batch_t h, void *cuda_stream)
+{
+    Batch *b = checked_batch(h);
+    if (!b) {
+        set_error("bad batch handle");
+        return GSM_ERR_BAD_PLAN;
+    }
+    return batch_status(b->state, b->count, static_cast<cudaStream_t>(cuda_stream));
+}
+
 gsm_status_t gsm_batch_destroy(gsm_batch_t h)
 {
     Batch *b = checked_batch(h);
@@ -830,6 +863,7 @@ gsm_status_t gsm_batch_destroy(gsm_batch_t h)
     cudaDeviceSynchronize();
     cudaGraphExecDestroy(b->exec);
     cudaGraphDestroy(b->graph);
+    dev_free(b->state);
     b->magic = 0;
     delete b;
     return GSM_OK;
@@ -981,6 +1015,12 @@ gsm_status_t gsm_fft_lines_noalloc(int M, int nlines, int sign, gsm_precision_t 
 gsm_status_t gsm_debug_fail_alloc(int k)
 {
     g_fail_in.store(k < 0 ? -1 : (long)k);
+    return GSM_OK;
+}
+
+gsm_status_t gsm_debug_batch_wait(long long wait_ns, int hold_instance)
+{
+    set_batch_wait(wait_ns > 0 ? (unsigned long long)wait_ns : 0ull, hold_instance);
     return GSM_OK;
 }
 

@@ -20,6 +20,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 #include <mutex>
 #include <new>
 #include <string>
@@ -38,6 +39,17 @@ constexpr int kMaxThreads = 512;   // CTA size cap: leaves 128 registers per thr
 
 template <class Pol>
 using S_t = typename Pol::scplx;
+
+// Read of workspace data.  CG = true (the persistent batch kernel, in which the
+// workspace is written and read again by other CTAs of the same launch): the
+// load bypasses L1 and the read-only path (ld.global.cg), so it sees what
+// other CTAs stored before they signalled completion.
+template <bool CG, class T>
+__device__ __forceinline__ T ldw(const T *p)
+{
+    if constexpr (CG) return __ldcg(p);
+    else return *p;
+}
 
 // FP64 twiddle tables hold, after the M twiddles w^m, the constants of the
 // FMA-form radix-8 stages (fft_stage8_fma); the other precisions have none.
@@ -109,7 +121,7 @@ __global__ void __launch_bounds__(kMaxThreads) k_xf(const typename Pol::io_t *__
 }
 
 // ------------------------------------------------------------------ pass yf
-template <class Pol, int EMAX>
+template <class Pol, int EMAX, bool CG = false>
 __device__ __forceinline__ void body_yf(const S_t<Pol> *__restrict__ W1, S_t<Pol> *__restrict__ W2, int ny,
                                         int nz, int hx, const Sched &sc, int nl, int gthr,
                                         const typename Pol::tw_t *__restrict__ tw, int bx, int by,
@@ -126,7 +138,7 @@ __device__ __forceinline__ void body_yf(const S_t<Pol> *__restrict__ W1, S_t<Pol
     const S_t<Pol> *in = W1 + ((size_t)z * hx + kx) * ny;
     for (int y = g.t; y < (Pol::kPrune ? ny : M); y += g.T) {   // y >= ny: zero padding
         S_t<Pol> v = Pol::st(cx<R>{Pol::zero(), Pol::zero()});
-        if (y < ny && z < nz) v = in[y];
+        if (y < ny && z < nz) v = ldw<CG>(in + y);
         s[pidx<Pol>(y)] = v;
     }
     group_sync(g);
@@ -156,7 +168,7 @@ __global__ void __launch_bounds__(kMaxThreads) k_yf(const S_t<Pol> *__restrict__
 // 3D: line = kx * My + ky, row = (kx * (ny + 1) + min(ky, My - ky)) * (nz + 1).
 // 2D: line = kx, row = kx * (ny + 1).  Entirely group-local: no CTA barrier.
 // full: the multiplier is stored for the whole half spectrum, row line * M.
-template <class Pol, int EMAX>
+template <class Pol, int EMAX, bool CG = false>
 __device__ __forceinline__ void body_conv(S_t<Pol> *__restrict__ W, const typename Pol::mult_t *__restrict__ mult,
                                           int nlines, int n, int is3d, int My, int ny1, const Sched &sc, int nl,
                                           int gthr, const typename Pol::tw_t *__restrict__ tw, int bx,
@@ -172,7 +184,7 @@ __device__ __forceinline__ void body_conv(S_t<Pol> *__restrict__ W, const typena
     S_t<Pol> *w = W + (size_t)line * n;
     for (int z = g.t; z < (Pol::kPrune ? n : M); z += g.T) {   // z >= n: zero padding
         S_t<Pol> v = Pol::st(cx<R>{Pol::zero(), Pol::zero()});
-        if (z < n) v = w[z];
+        if (z < n) v = ldw<CG>(w + z);
         s[pidx<Pol>(z)] = v;
     }
     group_sync(g);
@@ -218,7 +230,7 @@ __global__ void __launch_bounds__(kMaxThreads) k_conv(S_t<Pol> *__restrict__ W, 
 }
 
 // ------------------------------------------------------------------ pass yi
-template <class Pol, int EMAX>
+template <class Pol, int EMAX, bool CG = false>
 __device__ __forceinline__ void body_yi(const S_t<Pol> *__restrict__ W2, S_t<Pol> *__restrict__ W1, int ny,
                                         int nz, int hx, const Sched &sc, int nl, int gthr,
                                         const typename Pol::tw_t *__restrict__ tw, int bx, int by,
@@ -235,7 +247,7 @@ __device__ __forceinline__ void body_yi(const S_t<Pol> *__restrict__ W2, S_t<Pol
     for (int i = threadIdx.x; i < M * nl; i += blockDim.x) {
         const int ky = i / nl, ll = i - ky * nl;
         const int zz = z0 + ll;
-        if (zz < nz) s0[ll * LS + pidx<Pol>(ky)] = in[(size_t)ky * nz + zz];
+        if (zz < nz) s0[ll * LS + pidx<Pol>(ky)] = ldw<CG>(in + (size_t)ky * nz + zz);
     }
     __syncthreads();
     const int z = z0 + l;
@@ -256,7 +268,7 @@ __global__ void __launch_bounds__(kMaxThreads) k_yi(const S_t<Pol> *__restrict__
 }
 
 // ------------------------------------------------------------------ pass xi
-template <class Pol, int EMAX>
+template <class Pol, int EMAX, bool CG = false>
 __device__ __forceinline__ void body_xi(const S_t<Pol> *__restrict__ W1, typename Pol::io_t *__restrict__ u, int nx,
                                         int ny, int hx, const Sched &sc, int nl, int gthr,
                                         const typename Pol::tw_t *__restrict__ tw, int bx, int by,
@@ -277,8 +289,8 @@ __device__ __forceinline__ void body_xi(const S_t<Pol> *__restrict__ W1, typenam
         const int k = i / nl, ll = i - k * nl;
         const int yy = y0 + 2 * ll;
         cx<R> A = {Pol::zero(), Pol::zero()}, B = {Pol::zero(), Pol::zero()};
-        if (yy < ny) A = Pol::ld(in[(size_t)k * ny + yy]);
-        if (yy + 1 < ny) B = Pol::ld(in[(size_t)k * ny + yy + 1]);
+        if (yy < ny) A = Pol::ld(ldw<CG>(in + (size_t)k * ny + yy));
+        if (yy + 1 < ny) B = Pol::ld(ldw<CG>(in + (size_t)k * ny + yy + 1));
         if (k == 0 || k == nx) {
             A.im = Pol::zero();
             B.im = Pol::zero();
@@ -332,15 +344,27 @@ __global__ void __launch_bounds__(kMaxThreads) k_fft_hook(const double2 *__restr
     }
 }
 
-// ------------------------------------------------------------------ grouped batch
-// One launch per pass covers up to kBatchMax instances of different sizes:
-// CTA b belongs to instance i with prefix[i] <= b < prefix[i+1] and handles
-// tile b - prefix[i] of that instance's pass grid.  Every line is done by one
-// warp holding up to 16 elements per thread (M <= 512), nl lines per CTA, so
-// one CTA shape serves all sizes.
+// ------------------------------------------------------------------ persistent batch
+// One launch applies up to kBatchMax plans of different sizes (one precision,
+// one dimension).  The work is a queue of items (pass, instance, tile), a
+// tile being one CTA's share of that instance's pass grid, in pass-major
+// order: every item of pass p comes before every item of pass p + 1.  A
+// resident CTA takes the next item with an atomic counter, waits until the
+// instance's previous pass is complete (a counter of finished tiles per
+// instance and pass), runs the tile with the same pass bodies as the
+// single-plan kernels, and counts it as finished.  Items are taken in an order
+// in which each item's dependencies were taken earlier, by CTAs that are
+// already running and whose own dependencies were taken earlier still, so the
+// waits always end whatever the number of resident CTAs.  Each wait is bounded
+// all the same: when it runs out the CTA records GSM_ERR_TIMEOUT in the
+// status word and raises the abort flag, and every CTA then leaves at its next
+// wait or item.  Every line is done by one warp holding up to 16 elements per
+// thread (M <= 512), nl lines per CTA, so one CTA shape serves all sizes and
+// passes.
 constexpr int kBatchMax = 48;
 constexpr int kBatchEmax = 16;
 constexpr int kBatchMaxM = 32 * kBatchEmax;
+constexpr int kBatchPasses = 5;
 
 struct InstDesc {
     const void *rho;
@@ -350,54 +374,141 @@ struct InstDesc {
     const void *tw[3];
     int n[3], M[3];
     Sched sc[3];
-    int gx[5];   // x extent of each pass's tile grid
-    int full;    // multiplier over the whole half spectrum
+    int gx[kBatchPasses];   // x extent of each pass's tile grid
+    int full;               // multiplier over the whole half spectrum
 };
 
-struct BatchArgs {
-    int count, d, nl;
-    int prefix[kBatchMax + 1];
+// Queue state of one launch in device memory, zeroed before the launch: the
+// next item, the status word (0 or GSM_ERR_TIMEOUT), the abort flag, one
+// unused word, then the finished-tile counter of each (instance, pass).
+constexpr int kStateHeader = 4;
+constexpr int kStateWords = kStateHeader + kBatchMax * kBatchPasses;
+
+struct PersistArgs {
+    int count, d, nl, npass;
+    int total;                                  // items in the queue
+    int start[kBatchPasses + 1];                // first item of each pass
+    int tiles[kBatchPasses][kBatchMax + 1];     // within a pass: first tile of each instance
+    unsigned *state;                            // kStateWords words
+    unsigned long long wait_ns;                 // bound of every wait
+    int hold;                                   // test hook: this instance's first pass never
+                                                // counts as complete (-1: none)
     InstDesc inst[kBatchMax];
 };
 
-template <class Pol, int PASS, int D>
+__device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned *p)
+{
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ unsigned ld_relaxed_gpu(const unsigned *p)
+{
+    unsigned v;
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Thread 0 of the CTA: take the next item and wait for its dependency.
+// Returns false when the queue is empty, the batch was aborted or the wait ran
+// out; otherwise the item's pass, instance and tile.
+__device__ __forceinline__ bool take_item(const PersistArgs &a, int *pass, int *inst, int *tile)
+{
+    unsigned *next = a.state, *status = a.state + 1, *abort_flag = a.state + 2;
+    const unsigned *done = a.state + kStateHeader;
+    if (ld_relaxed_gpu(abort_flag) != 0) return false;
+    const int item = (int)atomicAdd(next, 1u);
+    if (item >= a.total) return false;
+    int p = 0;
+    while (item >= a.start[p + 1]) ++p;
+    const int r = item - a.start[p];
+    int i = 0;
+    while (r >= a.tiles[p][i + 1]) ++i;
+    *pass = p;
+    *inst = i;
+    *tile = r - a.tiles[p][i];
+    if (p == 0) return true;
+    const unsigned need = (unsigned)(a.tiles[p - 1][i + 1] - a.tiles[p - 1][i]) + (p == 1 && i == a.hold ? 1u : 0u);
+    const unsigned *cnt = done + i * kBatchPasses + (p - 1);
+    if (ld_acquire_gpu(cnt) >= need) return true;
+    const unsigned long long t0 = global_ns();
+    unsigned sleep_ns = 32;
+    while (ld_acquire_gpu(cnt) < need) {
+        if (ld_relaxed_gpu(abort_flag) != 0) return false;
+        if (global_ns() - t0 > a.wait_ns) {
+            atomicExch(status, (unsigned)GSM_ERR_TIMEOUT);
+            atomicExch(abort_flag, 1u);
+            return false;
+        }
+        __nanosleep(sleep_ns);
+        if (sleep_ns < 1024) sleep_ns *= 2;
+    }
+    return true;
+}
+
+template <class Pol, int D>
 // Resident CTAs per SM asked of the compiler: FP64 and double-float 2 (a
 // 128-register cap), FP32 3 (85 registers)
 __global__ void __launch_bounds__(32 * kBatchMaxLines, std::is_same<Pol, F32>::value ? 3 : 2)
-    k_batch(const __grid_constant__ BatchArgs a)
+    k_persist(const __grid_constant__ PersistArgs a)
 {
     using io = typename Pol::io_t;
     using tw = typename Pol::tw_t;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int b = blockIdx.x;
-    int i = 0;
-    while (i + 1 < a.count && a.prefix[i + 1] <= b) ++i;
-    const InstDesc &d = a.inst[i];
-    const int t = b - a.prefix[i];
-    const int gx = d.gx[PASS];
-    const int bx = t % gx, by = t / gx;
-    const int nx = d.n[0], ny = d.n[1], nz = D == 3 ? d.n[2] : 1, hx = nx + 1;
-    S_t<Pol> *W1 = static_cast<S_t<Pol> *>(d.W1);
-    S_t<Pol> *W2 = static_cast<S_t<Pol> *>(d.W2);
-    const auto *mult = static_cast<const typename Pol::mult_t *>(d.mult);
-    const tw *tw0 = static_cast<const tw *>(d.tw[0]);
-    const tw *tw1 = static_cast<const tw *>(d.tw[1]);
-    const tw *tw2 = static_cast<const tw *>(d.tw[2]);
-    const int nl = a.nl;
+    __shared__ int s_go, s_pass, s_inst, s_tile;
     constexpr int last = D == 3 ? 4 : 2;
-    if constexpr (PASS == 0) {
-        body_xf<Pol, kBatchEmax>(static_cast<const io *>(d.rho), W1, nx, ny, hx, d.sc[0], nl, 32, tw0, bx, by, smem_raw);
-    } else if constexpr (PASS == last) {
-        body_xi<Pol, kBatchEmax>(W1, static_cast<io *>(d.u), nx, ny, hx, d.sc[0], nl, 32, tw0, bx, by, smem_raw);
-    } else if constexpr (D == 2) {
-        body_conv<Pol, kBatchEmax>(W1, mult, hx, ny, 0, 1, ny + 1, d.sc[1], nl, 32, tw1, bx, smem_raw, d.full != 0);
-    } else if constexpr (PASS == 1) {
-        body_yf<Pol, kBatchEmax>(W1, W2, ny, nz, hx, d.sc[1], nl, 32, tw1, bx, by, smem_raw);
-    } else if constexpr (PASS == 2) {
-        body_conv<Pol, kBatchEmax>(W2, mult, hx * d.M[1], nz, 1, d.M[1], ny + 1, d.sc[2], nl, 32, tw2, bx, smem_raw,
-                                   d.full != 0);
-    } else {
-        body_yi<Pol, kBatchEmax>(W2, W1, ny, nz, hx, d.sc[1], nl, 32, tw1, bx, by, smem_raw);
+    const int nl = a.nl;
+    for (;;) {
+        if (threadIdx.x == 0) {
+            int p = 0, i = 0, t = 0;
+            s_go = take_item(a, &p, &i, &t) ? 1 : 0;
+            s_pass = p;
+            s_inst = i;
+            s_tile = t;
+        }
+        __syncthreads();
+        if (!s_go) break;
+        const int pass = s_pass, i = s_inst, t = s_tile;
+        const InstDesc &d = a.inst[i];
+        const int gx = d.gx[pass];
+        const int bx = t % gx, by = t / gx;
+        const int nx = d.n[0], ny = d.n[1], nz = D == 3 ? d.n[2] : 1, hx = nx + 1;
+        S_t<Pol> *W1 = static_cast<S_t<Pol> *>(d.W1);
+        S_t<Pol> *W2 = static_cast<S_t<Pol> *>(d.W2);
+        const auto *mult = static_cast<const typename Pol::mult_t *>(d.mult);
+        const tw *tw0 = static_cast<const tw *>(d.tw[0]);
+        const tw *tw1 = static_cast<const tw *>(d.tw[1]);
+        if (pass == 0) {
+            body_xf<Pol, kBatchEmax>(static_cast<const io *>(d.rho), W1, nx, ny, hx, d.sc[0], nl, 32, tw0, bx, by,
+                                     smem_raw);
+        } else if (pass == last) {
+            body_xi<Pol, kBatchEmax, true>(W1, static_cast<io *>(d.u), nx, ny, hx, d.sc[0], nl, 32, tw0, bx, by,
+                                           smem_raw);
+        } else if constexpr (D == 2) {
+            body_conv<Pol, kBatchEmax, true>(W1, mult, hx, ny, 0, 1, ny + 1, d.sc[1], nl, 32, tw1, bx, smem_raw,
+                                             d.full != 0);
+        } else if (pass == 1) {
+            body_yf<Pol, kBatchEmax, true>(W1, W2, ny, nz, hx, d.sc[1], nl, 32, tw1, bx, by, smem_raw);
+        } else if (pass == 2) {
+            body_conv<Pol, kBatchEmax, true>(W2, mult, hx * d.M[1], nz, 1, d.M[1], ny + 1, d.sc[2], nl, 32,
+                                             static_cast<const tw *>(d.tw[2]), bx, smem_raw, d.full != 0);
+        } else {
+            body_yi<Pol, kBatchEmax, true>(W2, W1, ny, nz, hx, d.sc[1], nl, 32, tw1, bx, by, smem_raw);
+        }
+        // every thread's stores of the tile, then one release of the count
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            __threadfence();
+            atomicAdd(a.state + kStateHeader + i * kBatchPasses + pass, 1u);
+        }
     }
 }
 
@@ -1335,11 +1446,15 @@ void pass_grid(const Plan *p, int pass, int nl, int *gx, int *gy)
     }
 }
 
+std::atomic<unsigned long long> g_batch_wait_ns{kBatchWaitDefaultNs};
+std::atomic<int> g_batch_hold{-1};
+
 template <class Pol>
-gsm_status_t launch_batch_t(BatchArgs &a, const std::vector<const Plan *> &plans, const void *const *rho,
-                            void *const *u, cudaStream_t st, bool dry)
+gsm_status_t launch_persist_t(PersistArgs &a, const std::vector<const Plan *> &plans, const void *const *rho,
+                              void *const *u, cudaStream_t st, bool dry)
 {
     const int np = a.d == 3 ? 5 : 3;
+    a.npass = np;
     size_t smem = 0;
     for (size_t i = 0; i < plans.size(); ++i) {
         const Plan *p = plans[i];
@@ -1363,43 +1478,60 @@ gsm_status_t launch_batch_t(BatchArgs &a, const std::vector<const Plan *> &plans
             d.gx[pass] = gx;
         }
     }
-    cudaError_t e = cudaSuccess;
-    auto run = [&](auto kernel, int pass) {
-        a.prefix[0] = 0;
+    // the queue: pass-major, instances in order within a pass, tiles in order
+    int item = 0;
+    for (int pass = 0; pass < np; ++pass) {
+        a.start[pass] = item;
+        a.tiles[pass][0] = 0;
         for (int i = 0; i < a.count; ++i) {
             int gx, gy;
             pass_grid(plans[i], pass, a.nl, &gx, &gy);
-            a.prefix[i + 1] = a.prefix[i] + gx * gy;
+            a.tiles[pass][i + 1] = a.tiles[pass][i] + gx * gy;
         }
-        if (e == cudaSuccess) e = raise_smem(kernel, smem);
-        if (e == cudaSuccess && !dry) kernel<<<a.prefix[a.count], a.nl * 32, smem, st>>>(a);
-    };
-    if (np == 5) {
-        run(k_batch<Pol, 0, 3>, 0);
-        run(k_batch<Pol, 1, 3>, 1);
-        run(k_batch<Pol, 2, 3>, 2);
-        run(k_batch<Pol, 3, 3>, 3);
-        run(k_batch<Pol, 4, 3>, 4);
-    } else {
-        run(k_batch<Pol, 0, 2>, 0);
-        run(k_batch<Pol, 1, 2>, 1);
-        run(k_batch<Pol, 2, 2>, 2);
+        item += a.tiles[pass][a.count];
+    }
+    for (int pass = np; pass <= kBatchPasses; ++pass) a.start[pass] = item;
+    a.total = item;
+    auto kernel = a.d == 3 ? k_persist<Pol, 3> : k_persist<Pol, 2>;
+    cudaError_t e = raise_smem(kernel, smem);
+    if (e == cudaSuccess && !dry) {
+        int occ = 0, sms = 0, dev = 0;
+        e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, a.nl * 32, smem);
+        if (e == cudaSuccess) {
+            // one CTA per resident slot: the CTAs loop over the queue
+            const int grid = std::max(1, std::min(a.total, std::max(1, occ) * sms));
+            kernel<<<grid, a.nl * 32, smem, st>>>(a);
+            e = cudaGetLastError();
+        }
     }
     GSM_CUDA_TRY(e);
-    GSM_CUDA_TRY(cudaGetLastError());
     return GSM_OK;
 }
 
 }  // namespace
 
-// Launch u[i] = U_i * rho[i]: plans with all padded lengths <= 512 are grouped
-// by (precision, dimension) into launches of up to kBatchMax instances per
-// pass; the others are applied one by one.  dry: only prepare the kernels
-// (shared-memory limits), launch nothing.
-gsm_status_t launch_batched(int count, const Plan *const *plans, const void *const *rho, void *const *u,
-                            int nl, cudaStream_t st, bool dry)
+size_t batch_state_bytes(int count) { return sizeof(unsigned) * kStateWords * (size_t)std::max(count, 1); }
+
+void set_batch_wait(unsigned long long wait_ns, int hold)
 {
+    g_batch_wait_ns.store(wait_ns == 0 ? kBatchWaitDefaultNs : wait_ns);
+    g_batch_hold.store(hold < 0 ? -1 : hold);
+}
+
+// u[i] = U_i * rho[i]: plans with all padded lengths <= 512 are grouped by
+// (precision, dimension) into persistent launches of up to kBatchMax
+// instances; the others are applied one by one.  Group g keeps its queue
+// state at state + g * kStateWords (batch_state_bytes(count) bytes in all,
+// zeroed here first).  dry: only prepare the kernels (shared-memory limits),
+// launch nothing.
+gsm_status_t launch_batched(int count, const Plan *const *plans, const void *const *rho, void *const *u,
+                            int nl, cudaStream_t st, bool dry, unsigned *state)
+{
+    if (!dry) GSM_CUDA_TRY(cudaMemsetAsync(state, 0, batch_state_bytes(count), st));
     std::vector<int> done(count, 0);
+    int group = 0;
     for (int i = 0; i < count; ++i) {
         if (done[i]) continue;
         if (!batch_eligible(plans[i])) {
@@ -1419,7 +1551,7 @@ gsm_status_t launch_batched(int count, const Plan *const *plans, const void *con
             w.push_back(u[j]);
             done[j] = 1;
         }
-        BatchArgs *a = new (std::nothrow) BatchArgs();
+        PersistArgs *a = new (std::nothrow) PersistArgs();
         if (!a) {
             set_error("host allocation failed");
             return GSM_ERR_OOM;
@@ -1427,15 +1559,34 @@ gsm_status_t launch_batched(int count, const Plan *const *plans, const void *con
         a->count = (int)grp.size();
         a->d = plans[i]->d;
         a->nl = nl;
+        a->state = state + (size_t)group * kStateWords;
+        a->wait_ns = g_batch_wait_ns.load();
+        a->hold = g_batch_hold.load();
+        ++group;
         gsm_status_t s;
         switch (plans[i]->opt.precision) {
-        case GSM_FP64: s = launch_batch_t<F64>(*a, grp, r.data(), w.data(), st, dry); break;
-        case GSM_FP32: s = launch_batch_t<F32>(*a, grp, r.data(), w.data(), st, dry); break;
-        default: s = launch_batch_t<DF64>(*a, grp, r.data(), w.data(), st, dry); break;
+        case GSM_FP64: s = launch_persist_t<F64>(*a, grp, r.data(), w.data(), st, dry); break;
+        case GSM_FP32: s = launch_persist_t<F32>(*a, grp, r.data(), w.data(), st, dry); break;
+        default: s = launch_persist_t<DF64>(*a, grp, r.data(), w.data(), st, dry); break;
         }
         delete a;
         if (s != GSM_OK) return s;
     }
+    return GSM_OK;
+}
+
+// Status of the persistent launches whose queue state is at `state`, read
+// after everything queued on `st`: GSM_ERR_TIMEOUT if a bounded wait ran out.
+gsm_status_t batch_status(const unsigned *state, int count, cudaStream_t st)
+{
+    std::vector<unsigned> h(batch_state_bytes(count) / sizeof(unsigned));
+    GSM_CUDA_TRY(cudaMemcpyAsync(h.data(), state, batch_state_bytes(count), cudaMemcpyDeviceToHost, st));
+    GSM_CUDA_TRY(cudaStreamSynchronize(st));
+    for (size_t g = 0; g * kStateWords < h.size(); ++g)
+        if (h[g * kStateWords + 1] != 0) {
+            set_error("a bounded wait of the persistent batch kernel ran out; this batch's outputs are not valid");
+            return GSM_ERR_TIMEOUT;
+        }
     return GSM_OK;
 }
 

@@ -5,8 +5,11 @@ library fail, for every k along a call, and gsm_debug_alloc_stats shows that
 each failing call returns GSM_ERR_OOM and leaves the library's live
 allocations as they were (nothing leaks), and that the call succeeds once k
 is past its last allocation.  Stale handles: a destroyed plan or batch handle
-is rejected with GSM_ERR_BAD_PLAN.  No test here makes a GPU fault, trap or
-hang.
+is rejected with GSM_ERR_BAD_PLAN.  Bounded waits: the persistent batch
+kernel, told by a test hook that one instance's first pass never completes,
+reports GSM_ERR_TIMEOUT after the bound with every CTA returned, and the next
+batch on the same context gives the right bits.  No test here makes a GPU
+fault, trap or hang, and nothing is left waiting after a call returns.
 """
 import ctypes
 
@@ -139,3 +142,33 @@ def test_destroyed_handles_are_rejected():
     assert lib.gsm_plan_destroy(h) == 7
     info = gsm._abi.PlanInfo()
     assert lib.gsm_plan_info(h, ctypes.byref(info)) == 7
+
+
+def test_batch_wait_runs_out_reported_and_recoverable():
+    import torch
+    import paper_1501_04438_gb300 as gsm
+    lib = _lib()
+    plans = [gsm.Plan("coulomb3d", 4.0, n) for n in (16, 20, 24)]
+    rhos = [torch.tensor(np.random.default_rng(n).standard_normal((n, n, n)), device="cuda") for n in (16, 20, 24)]
+    singles = [p.apply(r).clone() for p, r in zip(plans, rhos)]
+    before = _stats()
+    lib.gsm_debug_batch_wait(20_000_000, 1)     # 20 ms; instance 1's first pass never completes
+    try:
+        with pytest.raises(gsm.GSMError) as ei:
+            gsm.apply_batched(plans, rhos)
+        assert ei.value.status == 6
+        with pytest.raises(gsm.GSMError) as ei:   # creation runs the batch to time it
+            gsm.Batch(plans, rhos)
+        assert ei.value.status == 6
+    finally:
+        lib.gsm_debug_batch_wait(0, -1)
+    torch.cuda.synchronize()
+    assert _stats() == before
+    outs = gsm.apply_batched(plans, rhos)
+    for o, s1 in zip(outs, singles):
+        assert torch.equal(o, s1)
+    batch = gsm.Batch(plans, rhos)
+    batch.launch()
+    for o, s1 in zip(batch.wait(), singles):
+        assert torch.equal(o, s1)
+    batch.destroy()
