@@ -504,9 +504,13 @@ def test_hartree_gradient_central_differences():
 
 @pytest.mark.parametrize("entry", GOLDEN["ds2d"], ids=[f"n{e['n']}" for e in GOLDEN["ds2d"]])
 def test_paper_table_davey_stewartson(entry):
-    """Table Tab_DS.  Resolved rows: the printed error (3.974e-9 at 128^2) and
-    the floor; the under-resolved rows depend on how d_xx rho is formed and
-    are checked for magnitude (E of order 1e-2 or worse)."""
+    """Table Tab_DS with the source d_xx rho taken spectrally from the grid
+    values (Sec. 2.4: arithmetic on the discrete Fourier coefficients).
+    Resolved rows: the printed error (3.974e-9 at 128^2) and the floor.  The
+    under-resolved rows (h = 1/2, 1/4), where the spectral derivative of a
+    Gaussian of width 1/pi sampled at h = 1/2 is itself wrong, come out below
+    the printed values (2.2e-2 and 6.6e-4 against 1.474 and 5.72e-3): the
+    paper formed the source another way (next test)."""
     L, n = entry["L"], entry["n"]
     X, Y = wl.mesh((n, n), L)
     rho = np.pi * np.exp(-np.pi ** 2 * (X * X + Y * Y))
@@ -515,9 +519,28 @@ def test_paper_table_davey_stewartson(entry):
     if entry.get("floor"):
         assert E < entry["E"], E
     elif entry.get("underresolved"):
-        assert E > 1e-4, E
+        assert entry["E"] / 100 < E < entry["E"], E
     else:
         assert abs(E - entry["E"]) < 0.02 * entry["E"], E
+
+
+@pytest.mark.parametrize("entry", [e for e in GOLDEN["ds2d"] if not e.get("floor")],
+                         ids=[f"n{e['n']}" for e in GOLDEN["ds2d"] if not e.get("floor")])
+def test_paper_table_davey_stewartson_analytic_source(entry):
+    """Table Tab_DS to all four printed digits, under-resolved rows included,
+    when the source is d_xx rho = rho (4 pi^4 x^2 - 2 pi^2) evaluated at the
+    grid points and passed through the oracle's 2D Poisson potential
+    (-(1/2pi) ln|x| * source, Example 5): 1.474, 5.720e-3, 3.974e-9.  This
+    pins the Poisson path of the oracle (Gaussian sum of ln r, factors,
+    padded FFT convolution, Taylor correction, rescaling and the ln L term) at
+    three resolutions where the error is far above rounding."""
+    L, n = entry["L"], entry["n"]
+    X, Y = wl.mesh((n, n), L)
+    rho = np.pi * np.exp(-np.pi ** 2 * (X * X + Y * Y))
+    src = rho * (4 * np.pi ** 4 * X * X - 2 * np.pi ** 2)
+    u, _ = oracle.apply("poisson2d", src, L)
+    E = relmax(u, ds2d_gaussian(X, Y))
+    assert abs(E - entry["E"]) <= 0.0005 * entry["E"], (E, entry["E"])
 
 
 def test_davey_stewartson_folded_matches_literal_when_resolved():
