@@ -595,10 +595,10 @@ def run_suite(a):
             emit({"config": "4 batch48", "precision": prec, "instances": len(specs),
                   "sizes": [n for n, _ in specs], "points": npts,
                   "loop": {"ms": ms_loop, "Mpts_s": npts / ms_loop / 1e3},
-                  "persistent": {"ms": ms_grouped, "Mpts_s": npts / ms_grouped / 1e3, "bitwise_equal_loop": same,
-                                 "call": "gsm_apply_batched: one persistent launch, status read back"},
+                  "queue": {"ms": ms_grouped, "Mpts_s": npts / ms_grouped / 1e3, "bitwise_equal_loop": same,
+                            "call": "gsm_apply_batched: one launch with a device work queue, status read back"},
                   "graph": {"ms": ms_graph, "Mpts_s": npts / ms_graph / 1e3, "bitwise_equal_loop": same_graph,
-                            "call": "gsm_batch_launch: the persistent launch recorded in a CUDA graph"},
+                            "call": "gsm_batch_launch: the queue launch recorded in a CUDA graph"},
                   "rel_err_vs_oracle_sampled": errs, "cpu_baseline": cpu, "plans_s": plan_s})
             batch.destroy()
             for p in plans:

@@ -212,15 +212,16 @@ gsm_status_t gsm_apply_host(gsm_plan_t p, const void *rho_host, void *u_host, vo
  * (No counterpart in the paper, which treats one density at a time.)
  * Plans may differ in size, kernel and precision (each uses its own I/O type)
  * but must be distinct handles.  Plans whose padded lengths are all <= 512 go
- * through ONE persistent kernel launch per precision and dimension (up to 48
- * instances per launch): its CTAs take work items (pass, instance, tile) from
- * a device queue in pass-major order and run each once the instance's
- * previous pass is complete, so the passes of different instances overlap
- * and no launch boundary separates them.  Other plans, and FP32 plans with a
+ * through ONE kernel launch per precision and dimension (up to 48 instances
+ * per launch) with a device work queue: each CTA of the launch takes the next
+ * item (pass, instance, tile) from the queue, in pass-major order, when it
+ * starts, and runs it once the instance's previous pass is complete, so the
+ * passes of different instances overlap and no launch boundary separates
+ * them.  Other plans, and FP32 plans with a
  * padded length of exactly 512 (which use register-resident kernels of their
  * own), are applied one by one on the stream.  The results are the same bits
  * as gsm_apply's.
- * Each wait of the persistent kernel for a previous pass is bounded (10 s by
+ * Each wait of the queue kernel for a previous pass is bounded (10 s by
  * default): if one runs out, the kernel stops taking work, every CTA returns,
  * and the call reports GSM_ERR_TIMEOUT (the outputs are then not valid).  The
  * order in which work is taken guarantees that every wait ends, so the bound
@@ -235,7 +236,7 @@ gsm_status_t gsm_apply_batched(int count, const gsm_plan_t *plans, const void *c
 
 /*
  * The same batched apply recorded once into a CUDA graph (a memset of the
- * queue state and the persistent launches), so that every later run is a
+ * queue state and the queue launches), so that every later run is a
  * single cudaGraphLaunch.  The graph holds the given rho[i] and u[i] pointers
  * and each plan's workspace: refill the same rho arrays between launches; the
  * plans must outlive the batch, and no other apply may be in flight on them
@@ -371,7 +372,7 @@ gsm_status_t gsm_fft_lines_noalloc(int M, int nlines, int sign, gsm_precision_t 
 gsm_status_t gsm_debug_fail_alloc(int k);
 gsm_status_t gsm_debug_alloc_stats(size_t *count, size_t *bytes);
 
-/* Test hook of the persistent batch kernel (gsm_apply_batched,
+/* Test hook of the batch queue kernel (gsm_apply_batched,
  * gsm_batch_create), read when a batch is launched or recorded:
  * wait_ns > 0 bounds every wait by that many nanoseconds (<= 0: the default
  * 10 s); hold_instance >= 0 keeps the first pass of that instance (its index

@@ -134,7 +134,7 @@ gsm_status_t autotune_plan(Plan *p, cudaStream_t st, std::string *report);
 // set the launch shape of one pass (nl lines per CTA, emax elements per thread)
 gsm_status_t set_pass_shape(Plan *p, int pass, int nl, int emax);
 // The batched apply (gsm_passes.cu): plans with all padded lengths <= 512 go
-// through persistent launches, one per (precision, dimension) group, whose
+// through one queue launch per (precision, dimension) group, whose
 // work-queue state lives at `state` (batch_state_bytes(count) bytes of device
 // memory, zeroed by the call); the others are applied one by one.  dry: only
 // prepare the kernels.  batch_status reads the state after the stream's work:
@@ -143,12 +143,12 @@ gsm_status_t launch_batched(int count, const Plan *const *plans, const void *con
                             int nl, cudaStream_t st, bool dry, unsigned *state);
 size_t batch_state_bytes(int count);
 gsm_status_t batch_status(const unsigned *state, int count, cudaStream_t st);
-// Bound of every wait of the persistent batch kernel (0: the default) and the
+// Bound of every wait of the batch queue kernel (0: the default) and the
 // test hook that keeps one instance's first pass from ever counting as
 // complete (-1: off); read when a batch is launched or recorded.
 void set_batch_wait(unsigned long long wait_ns, int hold);
 constexpr unsigned long long kBatchWaitDefaultNs = 10000000000ull;   // 10 s
-constexpr int kBatchLines = 4;      // default lines (warps) per CTA of the persistent batch kernel
+constexpr int kBatchLines = 4;      // default lines (warps) per CTA of the batch queue kernel
 constexpr int kBatchMaxLines = 8;   // largest shape tried (bounds the CTA size)
 gsm_status_t launch_hartree(Plan *p, const void *psi, void *u, void *energy, void *grad,
                             cudaStream_t st);

@@ -40,7 +40,7 @@ constexpr int kMaxThreads = 512;   // CTA size cap: leaves 128 registers per thr
 template <class Pol>
 using S_t = typename Pol::scplx;
 
-// Read of workspace data.  CG = true (the persistent batch kernel, in which the
+// Read of workspace data.  CG = true (the batch queue kernel, in which the
 // workspace is written and read again by other CTAs of the same launch): the
 // load bypasses L1 and the read-only path (ld.global.cg), so it sees what
 // other CTAs stored before they signalled completion.
@@ -344,23 +344,27 @@ __global__ void __launch_bounds__(kMaxThreads) k_fft_hook(const double2 *__restr
     }
 }
 
-// ------------------------------------------------------------------ persistent batch
+// ------------------------------------------------------------------ batch: one launch, a device work queue
 // One launch applies up to kBatchMax plans of different sizes (one precision,
 // one dimension).  The work is a queue of items (pass, instance, tile), a
 // tile being one CTA's share of that instance's pass grid, in pass-major
-// order: every item of pass p comes before every item of pass p + 1.  A
-// resident CTA takes the next item with an atomic counter, waits until the
-// instance's previous pass is complete (a counter of finished tiles per
-// instance and pass), runs the tile with the same pass bodies as the
-// single-plan kernels, and counts it as finished.  Items are taken in an order
-// in which each item's dependencies were taken earlier, by CTAs that are
-// already running and whose own dependencies were taken earlier still, so the
-// waits always end whatever the number of resident CTAs.  Each wait is bounded
-// all the same: when it runs out the CTA records GSM_ERR_TIMEOUT in the
-// status word and raises the abort flag, and every CTA then leaves at its next
-// wait or item.  Every line is done by one warp holding up to 16 elements per
-// thread (M <= 512), nl lines per CTA, so one CTA shape serves all sizes and
-// passes.
+// order: every item of pass p comes before every item of pass p + 1.  The
+// launch has one CTA per item.  When a CTA starts, its thread 0 takes a ticket
+// from an atomic counter (so items go to CTAs in the order the CTAs start,
+// whatever their block index), waits until the instance's previous pass is
+// complete (a counter of finished tiles per instance and pass), the CTA runs
+// the tile with the same pass bodies as the single-plan kernels, and counts it
+// as finished.  Each item's dependencies were taken earlier, by CTAs that are
+// already resident and whose own dependencies were taken earlier still, so
+// the waits always end, however many CTAs are resident.  Passes of different
+// instances overlap and no launch boundary drains the GPU between passes.
+// Each wait is bounded all the same: when it runs out the CTA records
+// GSM_ERR_TIMEOUT in the status word and raises the abort flag, and every
+// later CTA returns at once.  Every line is done by one warp holding up to 16
+// elements per thread (M <= 512), nl lines per CTA, so one CTA shape serves
+// all sizes and passes.  (A loop over items inside long-lived CTAs was tried
+// first: with the pass bodies inside a loop the compiler no longer kept their
+// butterfly arrays in registers, 3 to 13 KB of stack per thread.)
 constexpr int kBatchMax = 48;
 constexpr int kBatchEmax = 16;
 constexpr int kBatchMaxM = 32 * kBatchEmax;
@@ -384,7 +388,7 @@ struct InstDesc {
 constexpr int kStateHeader = 4;
 constexpr int kStateWords = kStateHeader + kBatchMax * kBatchPasses;
 
-struct PersistArgs {
+struct QueueArgs {
     int count, d, nl, npass;
     int total;                                  // items in the queue
     int start[kBatchPasses + 1];                // first item of each pass
@@ -420,7 +424,7 @@ __device__ __forceinline__ unsigned ld_relaxed_gpu(const unsigned *p)
 // Thread 0 of the CTA: take the next item and wait for its dependency.
 // Returns false when the queue is empty, the batch was aborted or the wait ran
 // out; otherwise the item's pass, instance and tile.
-__device__ __forceinline__ bool take_item(const PersistArgs &a, int *pass, int *inst, int *tile)
+__device__ __forceinline__ bool take_item(const QueueArgs &a, int *pass, int *inst, int *tile)
 {
     unsigned *next = a.state, *status = a.state + 1, *abort_flag = a.state + 2;
     const unsigned *done = a.state + kStateHeader;
@@ -454,61 +458,85 @@ __device__ __forceinline__ bool take_item(const PersistArgs &a, int *pass, int *
     return true;
 }
 
+// One tile of pass PASS of one instance.
+template <class Pol, int D, int PASS>
+__device__ __forceinline__ void queue_tile(const InstDesc &d, int nl, int t, unsigned char *smem_raw)
+{
+    using io = typename Pol::io_t;
+    using tw = typename Pol::tw_t;
+    constexpr int last = D == 3 ? 4 : 2;
+    const int gx = d.gx[PASS];
+    const int bx = t % gx, by = t / gx;
+    const int nx = d.n[0], ny = d.n[1], nz = D == 3 ? d.n[2] : 1, hx = nx + 1;
+    S_t<Pol> *W1 = static_cast<S_t<Pol> *>(d.W1);
+    S_t<Pol> *W2 = static_cast<S_t<Pol> *>(d.W2);
+    const auto *mult = static_cast<const typename Pol::mult_t *>(d.mult);
+    const tw *tw0 = static_cast<const tw *>(d.tw[0]);
+    const tw *tw1 = static_cast<const tw *>(d.tw[1]);
+    if constexpr (PASS == 0) {
+        body_xf<Pol, kBatchEmax>(static_cast<const io *>(d.rho), W1, nx, ny, hx, d.sc[0], nl, 32, tw0, bx, by,
+                                 smem_raw);
+    } else if constexpr (PASS == last) {
+        body_xi<Pol, kBatchEmax, true>(W1, static_cast<io *>(d.u), nx, ny, hx, d.sc[0], nl, 32, tw0, bx, by,
+                                       smem_raw);
+    } else if constexpr (D == 2) {
+        body_conv<Pol, kBatchEmax, true>(W1, mult, hx, ny, 0, 1, ny + 1, d.sc[1], nl, 32, tw1, bx, smem_raw,
+                                         d.full != 0);
+    } else if constexpr (PASS == 1) {
+        body_yf<Pol, kBatchEmax, true>(W1, W2, ny, nz, hx, d.sc[1], nl, 32, tw1, bx, by, smem_raw);
+    } else if constexpr (PASS == 2) {
+        body_conv<Pol, kBatchEmax, true>(W2, mult, hx * d.M[1], nz, 1, d.M[1], ny + 1, d.sc[2], nl, 32,
+                                         static_cast<const tw *>(d.tw[2]), bx, smem_raw, d.full != 0);
+    } else {
+        body_yi<Pol, kBatchEmax, true>(W2, W1, ny, nz, hx, d.sc[1], nl, 32, tw1, bx, by, smem_raw);
+    }
+}
+
+// Item of a CTA (shared): valid if go != 0.
+struct QueueItem {
+    int go, pass, inst, tile;
+};
+
+// The tile of pass PASS if the CTA's item belongs to that pass, then one
+// release of the instance's count for the pass.
+template <class Pol, int D, int PASS>
+__device__ __forceinline__ void queue_pass(const QueueArgs &a, const QueueItem &it, unsigned char *smem_raw)
+{
+    if (it.go && it.pass == PASS) {
+        const int i = it.inst;
+        queue_tile<Pol, D, PASS>(a.inst[i], a.nl, it.tile, smem_raw);
+        // every thread's stores of the tile, then one release of the count
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            unsigned *cnt = a.state + kStateHeader + i * kBatchPasses + PASS;
+            asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(cnt) : "memory");
+        }
+    }
+}
+
 template <class Pol, int D>
 // Resident CTAs per SM asked of the compiler: FP64 and double-float 2 (a
 // 128-register cap), FP32 3 (85 registers)
 __global__ void __launch_bounds__(32 * kBatchMaxLines, std::is_same<Pol, F32>::value ? 3 : 2)
-    k_persist(const __grid_constant__ PersistArgs a)
+    k_batch_queue(const __grid_constant__ QueueArgs a)
 {
-    using io = typename Pol::io_t;
-    using tw = typename Pol::tw_t;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ int s_go, s_pass, s_inst, s_tile;
-    constexpr int last = D == 3 ? 4 : 2;
-    const int nl = a.nl;
-    for (;;) {
-        if (threadIdx.x == 0) {
-            int p = 0, i = 0, t = 0;
-            s_go = take_item(a, &p, &i, &t) ? 1 : 0;
-            s_pass = p;
-            s_inst = i;
-            s_tile = t;
-        }
-        __syncthreads();
-        if (!s_go) break;
-        const int pass = s_pass, i = s_inst, t = s_tile;
-        const InstDesc &d = a.inst[i];
-        const int gx = d.gx[pass];
-        const int bx = t % gx, by = t / gx;
-        const int nx = d.n[0], ny = d.n[1], nz = D == 3 ? d.n[2] : 1, hx = nx + 1;
-        S_t<Pol> *W1 = static_cast<S_t<Pol> *>(d.W1);
-        S_t<Pol> *W2 = static_cast<S_t<Pol> *>(d.W2);
-        const auto *mult = static_cast<const typename Pol::mult_t *>(d.mult);
-        const tw *tw0 = static_cast<const tw *>(d.tw[0]);
-        const tw *tw1 = static_cast<const tw *>(d.tw[1]);
-        if (pass == 0) {
-            body_xf<Pol, kBatchEmax>(static_cast<const io *>(d.rho), W1, nx, ny, hx, d.sc[0], nl, 32, tw0, bx, by,
-                                     smem_raw);
-        } else if (pass == last) {
-            body_xi<Pol, kBatchEmax, true>(W1, static_cast<io *>(d.u), nx, ny, hx, d.sc[0], nl, 32, tw0, bx, by,
-                                           smem_raw);
-        } else if constexpr (D == 2) {
-            body_conv<Pol, kBatchEmax, true>(W1, mult, hx, ny, 0, 1, ny + 1, d.sc[1], nl, 32, tw1, bx, smem_raw,
-                                             d.full != 0);
-        } else if (pass == 1) {
-            body_yf<Pol, kBatchEmax, true>(W1, W2, ny, nz, hx, d.sc[1], nl, 32, tw1, bx, by, smem_raw);
-        } else if (pass == 2) {
-            body_conv<Pol, kBatchEmax, true>(W2, mult, hx * d.M[1], nz, 1, d.M[1], ny + 1, d.sc[2], nl, 32,
-                                             static_cast<const tw *>(d.tw[2]), bx, smem_raw, d.full != 0);
-        } else {
-            body_yi<Pol, kBatchEmax, true>(W2, W1, ny, nz, hx, d.sc[1], nl, 32, tw1, bx, by, smem_raw);
-        }
-        // every thread's stores of the tile, then one release of the count
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            __threadfence();
-            atomicAdd(a.state + kStateHeader + i * kBatchPasses + pass, 1u);
-        }
+    __shared__ QueueItem it;
+    if (threadIdx.x == 0) {
+        int p = 0, i = 0, t = 0;
+        it.go = take_item(a, &p, &i, &t) ? 1 : 0;
+        it.pass = p;
+        it.inst = i;
+        it.tile = t;
+    }
+    __syncthreads();
+    if (!it.go) return;
+    queue_pass<Pol, D, 0>(a, it, smem_raw);
+    queue_pass<Pol, D, 1>(a, it, smem_raw);
+    queue_pass<Pol, D, 2>(a, it, smem_raw);
+    if constexpr (D == 3) {
+        queue_pass<Pol, D, 3>(a, it, smem_raw);
+        queue_pass<Pol, D, 4>(a, it, smem_raw);
     }
 }
 
@@ -1450,7 +1478,7 @@ std::atomic<unsigned long long> g_batch_wait_ns{kBatchWaitDefaultNs};
 std::atomic<int> g_batch_hold{-1};
 
 template <class Pol>
-gsm_status_t launch_persist_t(PersistArgs &a, const std::vector<const Plan *> &plans, const void *const *rho,
+gsm_status_t launch_queue_t(QueueArgs &a, const std::vector<const Plan *> &plans, const void *const *rho,
                               void *const *u, cudaStream_t st, bool dry)
 {
     const int np = a.d == 3 ? 5 : 3;
@@ -1492,19 +1520,12 @@ gsm_status_t launch_persist_t(PersistArgs &a, const std::vector<const Plan *> &p
     }
     for (int pass = np; pass <= kBatchPasses; ++pass) a.start[pass] = item;
     a.total = item;
-    auto kernel = a.d == 3 ? k_persist<Pol, 3> : k_persist<Pol, 2>;
+    auto kernel = a.d == 3 ? k_batch_queue<Pol, 3> : k_batch_queue<Pol, 2>;
     cudaError_t e = raise_smem(kernel, smem);
     if (e == cudaSuccess && !dry) {
-        int occ = 0, sms = 0, dev = 0;
-        e = cudaGetDevice(&dev);
-        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, a.nl * 32, smem);
-        if (e == cudaSuccess) {
-            // one CTA per resident slot: the CTAs loop over the queue
-            const int grid = std::max(1, std::min(a.total, std::max(1, occ) * sms));
-            kernel<<<grid, a.nl * 32, smem, st>>>(a);
-            e = cudaGetLastError();
-        }
+        // one CTA per item
+        kernel<<<std::max(1, a.total), a.nl * 32, smem, st>>>(a);
+        e = cudaGetLastError();
     }
     GSM_CUDA_TRY(e);
     return GSM_OK;
@@ -1521,8 +1542,8 @@ void set_batch_wait(unsigned long long wait_ns, int hold)
 }
 
 // u[i] = U_i * rho[i]: plans with all padded lengths <= 512 are grouped by
-// (precision, dimension) into persistent launches of up to kBatchMax
-// instances; the others are applied one by one.  Group g keeps its queue
+// (precision, dimension) into queue launches (k_batch_queue) of up to
+// kBatchMax instances; the others are applied one by one.  Group g keeps its queue
 // state at state + g * kStateWords (batch_state_bytes(count) bytes in all,
 // zeroed here first).  dry: only prepare the kernels (shared-memory limits),
 // launch nothing.
@@ -1551,7 +1572,7 @@ gsm_status_t launch_batched(int count, const Plan *const *plans, const void *con
             w.push_back(u[j]);
             done[j] = 1;
         }
-        PersistArgs *a = new (std::nothrow) PersistArgs();
+        QueueArgs *a = new (std::nothrow) QueueArgs();
         if (!a) {
             set_error("host allocation failed");
             return GSM_ERR_OOM;
@@ -1565,9 +1586,9 @@ gsm_status_t launch_batched(int count, const Plan *const *plans, const void *con
         ++group;
         gsm_status_t s;
         switch (plans[i]->opt.precision) {
-        case GSM_FP64: s = launch_persist_t<F64>(*a, grp, r.data(), w.data(), st, dry); break;
-        case GSM_FP32: s = launch_persist_t<F32>(*a, grp, r.data(), w.data(), st, dry); break;
-        default: s = launch_persist_t<DF64>(*a, grp, r.data(), w.data(), st, dry); break;
+        case GSM_FP64: s = launch_queue_t<F64>(*a, grp, r.data(), w.data(), st, dry); break;
+        case GSM_FP32: s = launch_queue_t<F32>(*a, grp, r.data(), w.data(), st, dry); break;
+        default: s = launch_queue_t<DF64>(*a, grp, r.data(), w.data(), st, dry); break;
         }
         delete a;
         if (s != GSM_OK) return s;
@@ -1575,7 +1596,7 @@ gsm_status_t launch_batched(int count, const Plan *const *plans, const void *con
     return GSM_OK;
 }
 
-// Status of the persistent launches whose queue state is at `state`, read
+// Status of the queue launches whose queue state is at `state`, read
 // after everything queued on `st`: GSM_ERR_TIMEOUT if a bounded wait ran out.
 gsm_status_t batch_status(const unsigned *state, int count, cudaStream_t st)
 {
@@ -1584,7 +1605,7 @@ gsm_status_t batch_status(const unsigned *state, int count, cudaStream_t st)
     GSM_CUDA_TRY(cudaStreamSynchronize(st));
     for (size_t g = 0; g * kStateWords < h.size(); ++g)
         if (h[g * kStateWords + 1] != 0) {
-            set_error("a bounded wait of the persistent batch kernel ran out; this batch's outputs are not valid");
+            set_error("a bounded wait of the batch kernel ran out; this batch's outputs are not valid");
             return GSM_ERR_TIMEOUT;
         }
     return GSM_OK;

@@ -5,7 +5,7 @@ library fail, for every k along a call, and gsm_debug_alloc_stats shows that
 each failing call returns GSM_ERR_OOM and leaves the library's live
 allocations as they were (nothing leaks), and that the call succeeds once k
 is past its last allocation.  Stale handles: a destroyed plan or batch handle
-is rejected with GSM_ERR_BAD_PLAN.  Bounded waits: the persistent batch
+is rejected with GSM_ERR_BAD_PLAN.  Bounded waits: the batch queue
 kernel, told by a test hook that one instance's first pass never completes,
 reports GSM_ERR_TIMEOUT after the bound with every CTA returned, and the next
 batch on the same context gives the right bits.  No test here makes a GPU

@@ -122,7 +122,8 @@ def test_plan_factors_and_tensor_match_oracle(gsm, kernel, beta):
     w_o, tau_o, S_o, _ = oracle.gs(kernel, beta=beta)
     if S_o != info["S"]:
         assert kernel == "poisson2d" and abs(S_o - info["S"]) <= 3, (kernel, S_o, info["S"])
-        w_o, tau_o, _, _ = oracle.gs(kernel, S=info["S"], beta=beta)
+        S_o = info["S"]
+        w_o, tau_o, _, _ = oracle.gs(kernel, S=S_o, beta=beta)
     w_g, tau_g = plan.gs_terms()
     assert len(w_g) == len(w_o)
     assert np.max(np.abs(w_g - w_o) / np.abs(w_o)) < 1e-13
@@ -133,7 +134,7 @@ def test_plan_factors_and_tensor_match_oracle(gsm, kernel, beta):
     # integrand; its rounding reaches ~1e-14 (factors are at most 4)
     assert np.max(np.abs(g - ref)) < 2e-14
     kh = plan.kernel_tensor()
-    kho, _ = oracle.kernel_hat(kernel, n, 5.0, beta=beta)
+    kho, _ = oracle.kernel_hat(kernel, n, 5.0, S=S_o, beta=beta)
     kho = kho.transpose(*range(d)[::-1])       # oracle is [kz][ky][kx]; plan is [kx][ky][kz]
     # rounding of sum_q w_q prod g_q is relative to sum_q |w_q| prod |g_q|, which
     # for ln r (terms of both signs, constant C0 ~ S/4) is ~100x the result
