@@ -130,10 +130,13 @@ static void free_plan(Plan *p)
         for (int b = 0; b < a; ++b) dup |= (p->d_g[b] == p->d_g[a]);
         if (!dup) dev_free(p->d_g[a]);
     }
-    for (int a = 0; a < 3; ++a) {
-        bool dup = false;
-        for (int b = 0; b < a; ++b) dup |= (p->d_tw[b] == p->d_tw[a]);
-        if (!dup) dev_free(p->d_tw[a]);
+    {
+        void *tabs[6] = {p->d_tw[0], p->d_tw[1], p->d_tw[2], p->d_twi[0], p->d_twi[1], p->d_twi[2]};
+        for (int a = 0; a < 6; ++a) {
+            bool dup = false;
+            for (int b = 0; b < a; ++b) dup |= (tabs[b] == tabs[a]);
+            if (!dup) dev_free(tabs[a]);
+        }
     }
     dev_free(p->d_khat);
     if (p->d_mult != p->d_mult64) dev_free(p->d_mult);

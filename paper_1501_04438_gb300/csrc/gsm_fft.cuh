@@ -23,11 +23,12 @@ namespace gsm {
 
 constexpr int kMaxStages = 12;
 
-// Radix schedule of one FFT length.
+// Radix schedule of one FFT length: stage st has radix r[st] (8, 4, 2, 5 or 3,
+// in any order whose product is M).
 struct Sched {
     int M;
     int nst;
-    int r[kMaxStages];
+    unsigned char r[kMaxStages];
 };
 
 template <class Pol>
@@ -348,11 +349,16 @@ __device__ __forceinline__ void fft_stage(typename Pol::scplx *s, int M, int Ns,
 }
 
 // ---------------------------------------------------------------- FMA-form stages (FP64)
-// FMA-form constants exist for the twiddled stages of radix 8, 4 and 2 (they
-// come first in every schedule, so their Ns are powers of two): gslots(R)
-// slots for each index j < Ns, rounded up to whole blocks of kGBlk indices,
-// stage after stage in schedule order.
+// FMA-form constants exist for the twiddled stages (Ns > 1) of radix 8 and 4,
+// and of radix 2 when Ns is even, that is whenever D = R Ns is a multiple of 4,
+// so that the nearest quarter turn of every twiddle is exact: gslots(R) slots
+// for each index j < Ns, rounded up to whole blocks of kGBlk indices, stage
+// after stage in schedule order.
 __host__ __device__ __forceinline__ bool gtabled(int R) { return R == 8 || R == 4 || R == 2; }
+__host__ __device__ __forceinline__ bool gtabled_at(int R, long Ns)
+{
+    return Ns > 1 && gtabled(R) && ((long)R * Ns) % 4 == 0;
+}
 __host__ __device__ __forceinline__ int gslots(int R) { return R == 8 ? 16 : (R == 4 ? 8 : 4); }
 constexpr int kGBlk = 32;
 
@@ -373,7 +379,7 @@ __host__ __device__ inline size_t gtable_offset(const Sched &sc, int st)
 {
     size_t off = 0, Ns = 1;
     for (int i = 0; i < st && i < sc.nst; ++i) {
-        if (Ns > 1 && gtabled(sc.r[i])) off += gblock(sc.r[i], Ns);
+        if (gtabled_at(sc.r[i], (long)Ns)) off += gblock(sc.r[i], Ns);
         Ns *= (size_t)sc.r[i];
     }
     return off;
@@ -524,7 +530,7 @@ __device__ __forceinline__ void bfly2_fma(cx<double> *v, const double *__restric
     if (!HALFOUT) v[1] = {fma(-f, X.re, x0.re), fma(-f, X.im, x0.im)};
 }
 
-// Twiddled Stockham stage of radix RAD (8, 4 or 2; Ns > 1, a power of two) in
+// Twiddled Stockham stage of radix RAD (8, 4 or 2; gtabled_at(RAD, Ns)) in
 // FMA form; HALF = 2: only the outputs t < RAD/2 (the crop).  Same data
 // movement as fft_stage; gt points at this stage's constants.
 template <int RAD, bool FWD, int NB, int HALF>
@@ -540,7 +546,7 @@ __device__ __forceinline__ void fft_stage_fma(double2 *s, int M, int Ns, const d
         if (b < nb) {
 #pragma unroll
             for (int t = 0; t < RAD; ++t) v[i][t] = F64::ld(s[pidx<F64>(b + t * nb)]);
-            const double *c = gt + gindex(RAD, b & (Ns - 1));
+            const double *c = gt + gindex(RAD, stage_mod(b, Ns));
             if constexpr (RAD == 8) bfly8_fma<FWD, NOUT>(v[i], c);
             else if constexpr (RAD == 4) bfly4_fma<FWD, HALF == 2>(v[i], c);
             else bfly2_fma<FWD, HALF == 2>(v[i], c);
@@ -551,7 +557,7 @@ __device__ __forceinline__ void fft_stage_fma(double2 *s, int M, int Ns, const d
     for (int i = 0; i < NB; ++i) {
         const int b = g.t + i * g.T;
         if (b < nb) {
-            const int j = b & (Ns - 1);
+            const int j = stage_mod(b, Ns);
             const int d0 = (b - j) * RAD + j;
 #pragma unroll
             for (int t = 0; t < NOUT; ++t) s[pidx<F64>(d0 + t * Ns)] = F64::st(v[i][t]);
@@ -563,14 +569,16 @@ __device__ __forceinline__ void fft_stage_fma(double2 *s, int M, int Ns, const d
 // All stages of the FFT of one line by one group.  EMAX bounds the elements
 // per thread (M <= EMAX * T).  The caller synchronises the group (or CTA)
 // after writing the line; the last stage ends with a group barrier, so the
-// group may read the result right away.  The schedule lists radices in the
-// order 8, 4, 2, 5, 3 (make_sched): each radix gets one loop of its own, so the
-// first stage has an even radix whenever M is even.
+// group may read the result right away.  The schedule may list its radices
+// in any order: the stages run in runs of equal radix, each radix with a loop
+// of its own (a loop mixing several large stage bodies costs the register
+// allocator dearly), the five loops repeated until every stage has run.
 // ZPAD: the second half of the input is zero and is not read (the first stage
-// is pruned); the caller need not write it.  CROP: only the first half of the
-// output is needed (the last stage is pruned when its radix is even; the
-// second half of the line is then left undefined).  Both apply to policies
-// with kPrune only; for the others the full stages run.
+// is pruned, so the first radix must be even); the caller need not write it.
+// CROP: only the first half of the output is needed (the last stage is pruned
+// when its radix is even; the second half of the line is then left
+// undefined).  Both apply to policies with kPrune only; for the others the
+// full stages run and the caller writes the zeros.
 // gt (FP64 only, may be NULL): the constants of the FMA-form stages
 // (fft_stage_fma), laid out as gtable_offset describes; with NULL every stage
 // takes the twiddle table tw.  Stages [st_begin, st_end) run (st_end < 0: to
@@ -598,96 +606,107 @@ __device__ __forceinline__ void fft_line(typename Pol::scplx *s, const Sched &sc
             fft_stage<Pol, RAD, FWD, NB, 0>(s, M, Ns, tw, g);                                  \
     } while (0)
     if constexpr (std::is_same<Pol, F64>::value) {
-        // stages of radix 8, 4, 2 come first in the schedule (Ns powers of two).
-        // The untwiddled first stage is peeled off so that each loop holds only
-        // one FMA-form stage body (a loop mixing several large stage bodies
-        // costs the register allocator dearly).
-        if (gt != nullptr && sc.nst > 0 && gtabled(sc.r[0])) {
+        if (gt != nullptr) {
+            // the untwiddled first stage is peeled off so that each loop below
+            // holds one FMA-form stage body
             if (st == 0 && st < nend) {
                 const int r0 = sc.r[0];
-                if (r0 == 8) {
-                    if (ZPAD) fft_stage<Pol, 8, FWD, (EMAX + 7) / 8, 1>(s, M, 1, tw, g);
-                    else fft_stage<Pol, 8, FWD, (EMAX + 7) / 8, 0>(s, M, 1, tw, g);
-                } else if (r0 == 4) {
-                    if (ZPAD) fft_stage<Pol, 4, FWD, (EMAX + 3) / 4, 1>(s, M, 1, tw, g);
-                    else fft_stage<Pol, 4, FWD, (EMAX + 3) / 4, 0>(s, M, 1, tw, g);
-                } else {
-                    if (ZPAD) fft_stage<Pol, 2, FWD, (EMAX + 1) / 2, 1>(s, M, 1, tw, g);
-                    else fft_stage<Pol, 2, FWD, (EMAX + 1) / 2, 0>(s, M, 1, tw, g);
-                }
+                if (r0 == 8) GSM_STAGE(8);
+                else if (r0 == 4) GSM_STAGE(4);
+                else if (r0 == 2) GSM_STAGE(2);
+                else if (r0 == 5) GSM_STAGE(5);
+                else GSM_STAGE(3);
                 st = 1;
                 Ns = r0;
             }
             size_t goff = gtable_offset(sc, st);
-            for (; st < nend && sc.r[st] == 8; ++st, Ns *= 8) {
-                if (CROP && st == last) fft_stage_fma<8, FWD, (EMAX + 7) / 8, 2>(s, M, Ns, gt + goff, g);
-                else fft_stage_fma<8, FWD, (EMAX + 7) / 8, 0>(s, M, Ns, gt + goff, g);
-                goff += gblock(8, Ns);
+            while (st < nend) {
+                for (; st < nend && sc.r[st] == 8; ++st, Ns *= 8) {
+                    if (CROP && st == last) fft_stage_fma<8, FWD, (EMAX + 7) / 8, 2>(s, M, Ns, gt + goff, g);
+                    else fft_stage_fma<8, FWD, (EMAX + 7) / 8, 0>(s, M, Ns, gt + goff, g);
+                    goff += gblock(8, Ns);
+                }
+                for (; st < nend && sc.r[st] == 4; ++st, Ns *= 4) {
+                    if (CROP && st == last) fft_stage_fma<4, FWD, (EMAX + 3) / 4, 2>(s, M, Ns, gt + goff, g);
+                    else fft_stage_fma<4, FWD, (EMAX + 3) / 4, 0>(s, M, Ns, gt + goff, g);
+                    goff += gblock(4, Ns);
+                }
+                for (; st < nend && sc.r[st] == 2; ++st, Ns *= 2) {
+                    if (gtabled_at(2, Ns)) {
+                        if (CROP && st == last) fft_stage_fma<2, FWD, (EMAX + 1) / 2, 2>(s, M, Ns, gt + goff, g);
+                        else fft_stage_fma<2, FWD, (EMAX + 1) / 2, 0>(s, M, Ns, gt + goff, g);
+                        goff += gblock(2, Ns);
+                    } else {
+                        GSM_STAGE(2);
+                    }
+                }
+                for (; st < nend && sc.r[st] == 5; ++st, Ns *= 5) GSM_STAGE(5);
+                for (; st < nend && sc.r[st] == 3; ++st, Ns *= 3) GSM_STAGE(3);
             }
-            for (; st < nend && sc.r[st] == 4; ++st, Ns *= 4) {
-                if (CROP && st == last) fft_stage_fma<4, FWD, (EMAX + 3) / 4, 2>(s, M, Ns, gt + goff, g);
-                else fft_stage_fma<4, FWD, (EMAX + 3) / 4, 0>(s, M, Ns, gt + goff, g);
-                goff += gblock(4, Ns);
-            }
-            for (; st < nend && sc.r[st] == 2; ++st, Ns *= 2) {
-                if (CROP && st == last) fft_stage_fma<2, FWD, (EMAX + 1) / 2, 2>(s, M, Ns, gt + goff, g);
-                else fft_stage_fma<2, FWD, (EMAX + 1) / 2, 0>(s, M, Ns, gt + goff, g);
-                goff += gblock(2, Ns);
-            }
+            return;
         }
     }
-    for (; st < nend && sc.r[st] == 8; ++st, Ns *= 8) GSM_STAGE(8);
-    for (; st < nend && sc.r[st] == 4; ++st, Ns *= 4) GSM_STAGE(4);
-    for (; st < nend && sc.r[st] == 2; ++st, Ns *= 2) GSM_STAGE(2);
-    for (; st < nend && sc.r[st] == 5; ++st, Ns *= 5) GSM_STAGE(5);
-    for (; st < nend && sc.r[st] == 3; ++st, Ns *= 3) GSM_STAGE(3);
+    while (st < nend) {
+        for (; st < nend && sc.r[st] == 8; ++st, Ns *= 8) GSM_STAGE(8);
+        for (; st < nend && sc.r[st] == 4; ++st, Ns *= 4) GSM_STAGE(4);
+        for (; st < nend && sc.r[st] == 2; ++st, Ns *= 2) GSM_STAGE(2);
+        for (; st < nend && sc.r[st] == 5; ++st, Ns *= 5) GSM_STAGE(5);
+        for (; st < nend && sc.r[st] == 3; ++st, Ns *= 3) GSM_STAGE(3);
+    }
 #undef GSM_STAGE
 }
 
-// Whether fft_fused_mid8 applies: the schedule starts and ends with radix 8
-// (M = 8^k, k >= 2).
-__host__ __device__ __forceinline__ bool fusable8(const Sched &sc)
+// The radix of the stage that fft_fused_mid can fuse for a transform whose
+// forward schedule is scf and inverse schedule sci: the forward's last radix
+// when the inverse starts with the same radix (8, 4 or 2) and both have at
+// least two stages; 0 when they cannot be fused.
+__host__ __device__ __forceinline__ int fused_radix(const Sched &scf, const Sched &sci)
 {
-    return sc.nst >= 2 && sc.r[0] == 8 && sc.r[sc.nst - 1] == 8;
+    if (scf.nst < 2 || sci.nst < 2) return 0;
+    const int R = scf.r[scf.nst - 1];
+    return (R == sci.r[0] && gtabled(R)) ? R : 0;
 }
 
-// The last forward stage, a pointwise multiplication by mult(k) and the first
-// inverse stage of a line whose schedule starts and ends with radix 8, in
-// registers.  The forward stage's butterfly b (Ns = M/8 = nb, so j = b)
-// leaves its outputs at the natural indices b + t M/8, which are exactly the
-// inputs of the inverse's (untwiddled) butterfly b; that one writes to 8b + t.
-// Saves two shared-memory round trips and a barrier over running the two
-// transforms and the multiplication apart.  Follow with
-// fft_line<Pol, false, ...>(..., st_begin = 1).
-template <class Pol, int NB, class MultF>
-__device__ __forceinline__ void fft_fused_mid8(typename Pol::scplx *s, const Sched &sc,
-                                               const typename Pol::tw_t *__restrict__ tw, const Group &g,
-                                               const double *__restrict__ gt, MultF mult)
+// The last forward stage (radix R, schedule scf), a pointwise multiplication
+// by mult(k) and the first inverse stage (radix R, schedule sci) of a line, in
+// registers.  The forward stage's butterfly b (Ns = M/R = nb, so j = b and the
+// twiddles are w_M^(b t)) leaves its outputs at the natural indices b + t M/R,
+// which are exactly the inputs of the inverse's untwiddled butterfly b; that
+// one writes to R b + t.  Saves two shared-memory round trips and a barrier
+// over running the two transforms and the multiplication apart.  Follow with
+// fft_line<Pol, false, ...>(..., sci, ..., st_begin = 1).
+template <class Pol, int R, int NB, class MultF>
+__device__ __forceinline__ void fft_fused_mid(typename Pol::scplx *s, const Sched &scf,
+                                              const typename Pol::tw_t *__restrict__ tw, const Group &g,
+                                              const double *__restrict__ gt, MultF mult)
 {
-    using R = typename Pol::real;
-    const int M = sc.M, nb = M / 8;
-    cx<R> v[NB][8];
+    using Rl = typename Pol::real;
+    const int M = scf.M, nb = M / R;
+    cx<Rl> v[NB][R];
 #pragma unroll
     for (int i = 0; i < NB; ++i) {
         const int b = g.t + i * g.T;
         if (b < nb) {
 #pragma unroll
-            for (int t = 0; t < 8; ++t) v[i][t] = Pol::ld(s[pidx<Pol>(b + t * nb)]);
+            for (int t = 0; t < R; ++t) v[i][t] = Pol::ld(s[pidx<Pol>(b + t * nb)]);
             bool done = false;
             if constexpr (std::is_same<Pol, F64>::value) {
-                if (gt != nullptr) {
-                    bfly8_fma<true, 8>(v[i], gt + gtable_offset(sc, sc.nst - 1) + gindex(8, b));
+                if (gt != nullptr && gtabled_at(R, nb)) {
+                    const double *c = gt + gtable_offset(scf, scf.nst - 1) + gindex(R, b);
+                    if constexpr (R == 8) bfly8_fma<true, 8>(v[i], c);
+                    else if constexpr (R == 4) bfly4_fma<true, false>(v[i], c);
+                    else bfly2_fma<true, false>(v[i], c);
                     done = true;
                 }
             }
             if (!done) {
 #pragma unroll
-                for (int t = 1; t < 8; ++t) v[i][t] = cmul(v[i][t], Pol::tw(tw[b * t]));   // twiddle step 1
-                bfly<R, 8, true, 0>(v[i]);
+                for (int t = 1; t < R; ++t) v[i][t] = cmul(v[i][t], Pol::tw(tw[b * t]));   // twiddle step 1
+                bfly<Rl, R, true, 0>(v[i]);
             }
 #pragma unroll
-            for (int t = 0; t < 8; ++t) v[i][t] = cscale(v[i][t], mult(b + t * nb));
-            bfly<R, 8, false, 0>(v[i]);
+            for (int t = 0; t < R; ++t) v[i][t] = cscale(v[i][t], mult(b + t * nb));
+            bfly<Rl, R, false, 0>(v[i]);
         }
     }
     group_sync(g);
@@ -696,7 +715,7 @@ __device__ __forceinline__ void fft_fused_mid8(typename Pol::scplx *s, const Sch
         const int b = g.t + i * g.T;
         if (b < nb) {
 #pragma unroll
-            for (int t = 0; t < 8; ++t) s[pidx<Pol>(8 * b + t)] = Pol::st(v[i][t]);
+            for (int t = 0; t < R; ++t) s[pidx<Pol>(R * b + t)] = Pol::st(v[i][t]);
         }
     }
     group_sync(g);

@@ -51,7 +51,9 @@ struct Plan {
     double *d_khat = nullptr;                     // sum_q w_q G_k^q, octant, FP64
     double *d_mult64 = nullptr;                   // full multiplier, FP64, octant
     void *d_mult = nullptr;                       // multiplier in the pass precision
-    void *d_tw[3] = {nullptr, nullptr, nullptr};  // twiddle tables per axis
+    void *d_tw[3] = {nullptr, nullptr, nullptr};  // per axis: twiddles, then (FP64) the FMA-form
+                                                  // constants of the forward schedule
+    void *d_twi[3] = {nullptr, nullptr, nullptr}; // the same for the inverse schedule (may alias d_tw)
     void *d_work1 = nullptr, *d_work2 = nullptr;  // FFT workspace
     size_t work1_bytes = 0, work2_bytes = 0;
     size_t mult_elems = 0;         // octant entries (FP64 tables)
@@ -64,7 +66,7 @@ struct Plan {
     double *d_scratch = nullptr;                           // energy partial sums
     size_t scratch_elems = 0;
 
-    Sched sched[3];
+    Sched sched_f[3], sched_i[3];   // radix schedules of the forward and inverse transforms per axis
     PassCfg cfg_xf, cfg_yf, cfg_conv, cfg_yi, cfg_xi;
 };
 
@@ -156,9 +158,18 @@ gsm_status_t launch_fft_lines(int M, int nlines, int sign, gsm_precision_t prec,
                               const double *in, double *out, cudaStream_t st);
 gsm_status_t launch_fft_lines_noalloc(int M, int nlines, int sign, gsm_precision_t prec,
                                       const double *in, double *out, cudaStream_t st);
+// the twiddle tables of one axis for its current forward and inverse schedules
+// (frees the axis's previous tables unless another axis shares them)
 gsm_status_t make_twiddles(Plan *p, int axis, cudaStream_t st);
 gsm_status_t make_pass_multiplier(Plan *p, cudaStream_t st);
+// default radix schedule of length M: radices 8, 4, 2, 5, 3 in that order
 bool make_sched(int M, Sched *s);
+// schedule with the given radices in the given order (each 8, 4, 2, 5 or 3,
+// product M); forward: the first radix must be even (the pruned first stage
+// of a zero-padded transform)
+bool make_sched_order(int M, const int *radices, int count, bool forward, Sched *s);
+// set the schedule of one axis and direction and rebuild that axis's tables
+gsm_status_t set_axis_schedule(Plan *p, int axis, bool inverse, const Sched &sc, cudaStream_t st);
 size_t cplx_bytes(gsm_precision_t prec);
 
 }  // namespace gsm

@@ -170,8 +170,10 @@ __global__ void __launch_bounds__(kMaxThreads) k_yf(const S_t<Pol> *__restrict__
 // full: the multiplier is stored for the whole half spectrum, row line * M.
 template <class Pol, int EMAX, bool CG = false>
 __device__ __forceinline__ void body_conv(S_t<Pol> *__restrict__ W, const typename Pol::mult_t *__restrict__ mult,
-                                          int nlines, int n, int is3d, int My, int ny1, const Sched &sc, int nl,
-                                          int gthr, const typename Pol::tw_t *__restrict__ tw, int bx,
+                                          int nlines, int n, int is3d, int My, int ny1, const Sched &sc,
+                                          const Sched &sci, int nl, int gthr,
+                                          const typename Pol::tw_t *__restrict__ tw,
+                                          const typename Pol::tw_t *__restrict__ twi, int bx,
                                           unsigned char *smem_raw, bool full = false)
 {
     using R = typename Pol::real;
@@ -200,13 +202,16 @@ __device__ __forceinline__ void body_conv(S_t<Pol> *__restrict__ W, const typena
         mrow = mult + (size_t)line * (n + 1);
     }
     auto mult_of = [&](int k) -> R { return Pol::mult(mrow[full ? k : min(k, M - k)]); };
-    const double *gt = g8_table<Pol>(tw, M);
-    if (fusable8(sc)) {
+    const double *gt = g8_table<Pol>(tw, M), *gti = g8_table<Pol>(twi, M);
+    const int fr = fused_radix(sc, sci);
+    if (fr != 0) {
         // forward up to its last stage; last forward stage, multiplication and
         // first inverse stage in registers; the rest of the inverse
         fft_line<Pol, true, EMAX, true, false>(s, sc, tw, g, gt, 0, sc.nst - 1);
-        fft_fused_mid8<Pol, (EMAX + 7) / 8>(s, sc, tw, g, gt, mult_of);
-        fft_line<Pol, false, EMAX, false, true>(s, sc, tw, g, gt, 1);
+        if (fr == 8) fft_fused_mid<Pol, 8, (EMAX + 7) / 8>(s, sc, tw, g, gt, mult_of);
+        else if (fr == 4) fft_fused_mid<Pol, 4, (EMAX + 3) / 4>(s, sc, tw, g, gt, mult_of);
+        else fft_fused_mid<Pol, 2, (EMAX + 1) / 2>(s, sc, tw, g, gt, mult_of);
+        fft_line<Pol, false, EMAX, false, true>(s, sci, twi, g, gti, 1);
     } else {
         fft_line<Pol, true, EMAX, true, false>(s, sc, tw, g, gt);
         for (int k = g.t; k < M; k += g.T) {
@@ -214,7 +219,7 @@ __device__ __forceinline__ void body_conv(S_t<Pol> *__restrict__ W, const typena
             s[p] = Pol::st(cscale(Pol::ld(s[p]), mult_of(k)));
         }
         group_sync(g);
-        fft_line<Pol, false, EMAX, false, true>(s, sc, tw, g, gt);
+        fft_line<Pol, false, EMAX, false, true>(s, sci, twi, g, gti);
     }
     for (int z = g.t; z < n; z += g.T) w[z] = s[pidx<Pol>(z)];
 }
@@ -222,11 +227,13 @@ __device__ __forceinline__ void body_conv(S_t<Pol> *__restrict__ W, const typena
 template <class Pol, int EMAX>
 __global__ void __launch_bounds__(kMaxThreads) k_conv(S_t<Pol> *__restrict__ W, const typename Pol::mult_t *__restrict__ mult,
                                                       int nlines, int n, int is3d, int My, int ny1, Sched sc,
-                                                      int nl, int gthr, const typename Pol::tw_t *__restrict__ tw,
-                                                      int full)
+                                                      Sched sci, int nl, int gthr,
+                                                      const typename Pol::tw_t *__restrict__ tw,
+                                                      const typename Pol::tw_t *__restrict__ twi, int full)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    body_conv<Pol, EMAX>(W, mult, nlines, n, is3d, My, ny1, sc, nl, gthr, tw, blockIdx.x, smem_raw, full != 0);
+    body_conv<Pol, EMAX>(W, mult, nlines, n, is3d, My, ny1, sc, sci, nl, gthr, tw, twi, blockIdx.x, smem_raw,
+                         full != 0);
 }
 
 // ------------------------------------------------------------------ pass yi
@@ -375,9 +382,9 @@ struct InstDesc {
     void *u;
     void *W1, *W2;
     const void *mult;
-    const void *tw[3];
+    const void *tw[3], *twi[3];   // forward and inverse tables per axis
     int n[3], M[3];
-    Sched sc[3];
+    Sched sc[3], sci[3];          // forward and inverse schedules per axis
     int gx[kBatchPasses];   // x extent of each pass's tile grid
     int full;               // multiplier over the whole half spectrum
 };
@@ -471,24 +478,23 @@ __device__ __forceinline__ void queue_tile(const InstDesc &d, int nl, int t, uns
     S_t<Pol> *W1 = static_cast<S_t<Pol> *>(d.W1);
     S_t<Pol> *W2 = static_cast<S_t<Pol> *>(d.W2);
     const auto *mult = static_cast<const typename Pol::mult_t *>(d.mult);
-    const tw *tw0 = static_cast<const tw *>(d.tw[0]);
-    const tw *tw1 = static_cast<const tw *>(d.tw[1]);
+    auto T = [&](const void *t) { return static_cast<const tw *>(t); };
     if constexpr (PASS == 0) {
-        body_xf<Pol, kBatchEmax>(static_cast<const io *>(d.rho), W1, nx, ny, hx, d.sc[0], nl, 32, tw0, bx, by,
-                                 smem_raw);
+        body_xf<Pol, kBatchEmax>(static_cast<const io *>(d.rho), W1, nx, ny, hx, d.sc[0], nl, 32, T(d.tw[0]), bx,
+                                 by, smem_raw);
     } else if constexpr (PASS == last) {
-        body_xi<Pol, kBatchEmax, true>(W1, static_cast<io *>(d.u), nx, ny, hx, d.sc[0], nl, 32, tw0, bx, by,
-                                       smem_raw);
+        body_xi<Pol, kBatchEmax, true>(W1, static_cast<io *>(d.u), nx, ny, hx, d.sci[0], nl, 32, T(d.twi[0]), bx,
+                                       by, smem_raw);
     } else if constexpr (D == 2) {
-        body_conv<Pol, kBatchEmax, true>(W1, mult, hx, ny, 0, 1, ny + 1, d.sc[1], nl, 32, tw1, bx, smem_raw,
-                                         d.full != 0);
+        body_conv<Pol, kBatchEmax, true>(W1, mult, hx, ny, 0, 1, ny + 1, d.sc[1], d.sci[1], nl, 32, T(d.tw[1]),
+                                         T(d.twi[1]), bx, smem_raw, d.full != 0);
     } else if constexpr (PASS == 1) {
-        body_yf<Pol, kBatchEmax, true>(W1, W2, ny, nz, hx, d.sc[1], nl, 32, tw1, bx, by, smem_raw);
+        body_yf<Pol, kBatchEmax, true>(W1, W2, ny, nz, hx, d.sc[1], nl, 32, T(d.tw[1]), bx, by, smem_raw);
     } else if constexpr (PASS == 2) {
-        body_conv<Pol, kBatchEmax, true>(W2, mult, hx * d.M[1], nz, 1, d.M[1], ny + 1, d.sc[2], nl, 32,
-                                         static_cast<const tw *>(d.tw[2]), bx, smem_raw, d.full != 0);
+        body_conv<Pol, kBatchEmax, true>(W2, mult, hx * d.M[1], nz, 1, d.M[1], ny + 1, d.sc[2], d.sci[2], nl, 32,
+                                         T(d.tw[2]), T(d.twi[2]), bx, smem_raw, d.full != 0);
     } else {
-        body_yi<Pol, kBatchEmax, true>(W2, W1, ny, nz, hx, d.sc[1], nl, 32, tw1, bx, by, smem_raw);
+        body_yi<Pol, kBatchEmax, true>(W2, W1, ny, nz, hx, d.sci[1], nl, 32, T(d.twi[1]), bx, by, smem_raw);
     }
 }
 
@@ -612,7 +618,7 @@ void launch_g8table(const Sched &sc, double2 *dst, cudaStream_t st)
     d.n = 0;
     long Ns = 1, entries = 0;
     for (int i = 0; i < sc.nst; ++i) {
-        if (Ns > 1 && gtabled(sc.r[i])) {
+        if (gtabled_at(sc.r[i], Ns)) {
             d.s[d.n].R = sc.r[i];
             d.s[d.n].Ns = Ns;
             d.s[d.n].off = (long)gtable_offset(sc, i);
@@ -820,6 +826,8 @@ void launch_pass_t(const Plan *p, int pass, const void *rho_v, void *u_v, cudaSt
     const auto *mult = static_cast<const typename Pol::mult_t *>(p->d_mult);
     const tw *twx = static_cast<const tw *>(p->d_tw[0]);
     const tw *twy = static_cast<const tw *>(p->d_tw[1]);
+    const tw *twxi = static_cast<const tw *>(p->d_twi[0]);
+    const tw *twyi = static_cast<const tw *>(p->d_twi[1]);
     const int last = p->d == 3 ? 4 : 2;
     if constexpr (std::is_same<Pol, F32>::value) {
         if ((pass == 0 || pass == last) && p->M[0] == 512 && p->rr_conv) {
@@ -832,13 +840,13 @@ void launch_pass_t(const Plan *p, int pass, const void *rho_v, void *u_v, cudaSt
         const PassCfg &c = p->cfg_xf;
         dim3 g((ny + 2 * c.nl - 1) / (2 * c.nl), nz);
         with_emax(c, [&](auto E) {
-            k_xf<Pol, E()><<<g, c.nthr, c.smem, st>>>(rho, W1, nx, ny, hx, p->sched[0], c.nl, c.gthr, twx);
+            k_xf<Pol, E()><<<g, c.nthr, c.smem, st>>>(rho, W1, nx, ny, hx, p->sched_f[0], c.nl, c.gthr, twx);
         });
     } else if (pass == last) {
         const PassCfg &c = p->cfg_xi;
         dim3 g((ny + 2 * c.nl - 1) / (2 * c.nl), nz);
         with_emax(c, [&](auto E) {
-            k_xi<Pol, E()><<<g, c.nthr, c.smem, st>>>(W1, u, nx, ny, hx, p->sched[0], c.nl, c.gthr, twx);
+            k_xi<Pol, E()><<<g, c.nthr, c.smem, st>>>(W1, u, nx, ny, hx, p->sched_i[0], c.nl, c.gthr, twxi);
         });
     } else if (p->d == 2) {
         const PassCfg &c = p->cfg_conv;
@@ -849,12 +857,13 @@ void launch_pass_t(const Plan *p, int pass, const void *rho_v, void *u_v, cudaSt
             }
         }
         with_emax(c, [&](auto E) {
-            k_conv<Pol, E()><<<(hx + c.nl - 1) / c.nl, c.nthr, c.smem, st>>>(W1, mult, hx, ny, 0, 1, ny + 1,
-                                                                          p->sched[1], c.nl, c.gthr, twy,
-                                                                          p->mult_full ? 1 : 0);
+            k_conv<Pol, E()><<<(hx + c.nl - 1) / c.nl, c.nthr, c.smem, st>>>(
+                W1, mult, hx, ny, 0, 1, ny + 1, p->sched_f[1], p->sched_i[1], c.nl, c.gthr, twy, twyi,
+                p->mult_full ? 1 : 0);
         });
     } else {
         const tw *twz = static_cast<const tw *>(p->d_tw[2]);
+        const tw *twzi = static_cast<const tw *>(p->d_twi[2]);
         const int My = p->M[1];
         if (pass == 1) {
             if constexpr (std::is_same<Pol, F32>::value) {
@@ -866,7 +875,7 @@ void launch_pass_t(const Plan *p, int pass, const void *rho_v, void *u_v, cudaSt
             const PassCfg &c = p->cfg_yf;
             dim3 g((nz + c.nl - 1) / c.nl, hx);
             with_emax(c, [&](auto E) {
-                k_yf<Pol, E()><<<g, c.nthr, c.smem, st>>>(W1, W2, ny, nz, hx, p->sched[1], c.nl, c.gthr, twy);
+                k_yf<Pol, E()><<<g, c.nthr, c.smem, st>>>(W1, W2, ny, nz, hx, p->sched_f[1], c.nl, c.gthr, twy);
             });
         } else if (pass == 2) {
             const PassCfg &c = p->cfg_conv;
@@ -879,7 +888,8 @@ void launch_pass_t(const Plan *p, int pass, const void *rho_v, void *u_v, cudaSt
             }
             with_emax(c, [&](auto E) {
                 k_conv<Pol, E()><<<(nlines + c.nl - 1) / c.nl, c.nthr, c.smem, st>>>(
-                    W2, mult, nlines, nz, 1, My, ny + 1, p->sched[2], c.nl, c.gthr, twz, p->mult_full ? 1 : 0);
+                    W2, mult, nlines, nz, 1, My, ny + 1, p->sched_f[2], p->sched_i[2], c.nl, c.gthr, twz, twzi,
+                    p->mult_full ? 1 : 0);
             });
         } else {
             if constexpr (std::is_same<Pol, F32>::value) {
@@ -891,7 +901,7 @@ void launch_pass_t(const Plan *p, int pass, const void *rho_v, void *u_v, cudaSt
             const PassCfg &c = p->cfg_yi;
             dim3 g((nz + c.nl - 1) / c.nl, hx);
             with_emax(c, [&](auto E) {
-                k_yi<Pol, E()><<<g, c.nthr, c.smem, st>>>(W2, W1, ny, nz, hx, p->sched[1], c.nl, c.gthr, twy);
+                k_yi<Pol, E()><<<g, c.nthr, c.smem, st>>>(W2, W1, ny, nz, hx, p->sched_i[1], c.nl, c.gthr, twyi);
             });
         }
     }
@@ -954,6 +964,14 @@ int pass_len(const Plan *p, int pass)
 
 std::mutex g_tune_mutex;
 
+bool same_sched(const Sched &a, const Sched &b)
+{
+    if (a.M != b.M || a.nst != b.nst) return false;
+    for (int i = 0; i < a.nst; ++i)
+        if (a.r[i] != b.r[i]) return false;
+    return true;
+}
+
 std::string tune_key(const Plan *p, int pass)
 {
     cudaDeviceProp prop;
@@ -964,12 +982,126 @@ std::string tune_key(const Plan *p, int pass)
     for (char &ch : name)
         if (ch == ' ') ch = '_';
     char buf[256];
-    snprintf(buf, sizeof(buf), "v3 %s p%d d%d n%d,%d,%d pass%d", name.c_str(), (int)p->opt.precision, p->d, p->n[0],
+    snprintf(buf, sizeof(buf), "v4 %s p%d d%d n%d,%d,%d pass%d", name.c_str(), (int)p->opt.precision, p->d, p->n[0],
              p->n[1], p->d == 3 ? p->n[2] : 1, pass);
     return buf;
 }
 
-bool cache_lookup(const char *path, const std::string &key, int *nl, int *emax)
+std::string sched_str(const Sched &sc)
+{
+    std::string out;
+    for (int i = 0; i < sc.nst; ++i) {
+        if (i) out += '.';
+        out += std::to_string((int)sc.r[i]);
+    }
+    return out;
+}
+
+bool sched_parse(const char *txt, int M, bool forward, Sched *sc)
+{
+    int r[kMaxStages], n = 0;
+    const char *c = txt;
+    while (*c && n < kMaxStages) {
+        char *end = nullptr;
+        const long v = strtol(c, &end, 10);
+        if (end == c) break;
+        r[n++] = (int)v;
+        c = end;
+        if (*c != '.') break;
+        ++c;
+    }
+    return make_sched_order(M, r, n, forward, sc);
+}
+
+// The axis whose schedules pass `pass` uses, and which of them: 3D xf, yf
+// the forward, xi, yi the inverse, conv both (axis z); 2D xf, xi and conv
+// (both, axis y).
+void pass_axis(const Plan *p, int pass, int *axis, bool *fwd, bool *inv)
+{
+    const int last = p->d == 3 ? 4 : 2;
+    const int conv = p->d == 3 ? 2 : 1;
+    *fwd = *inv = false;
+    if (pass == 0) { *axis = 0; *fwd = true; }
+    else if (pass == last) { *axis = 0; *inv = true; }
+    else if (pass == conv) { *axis = p->d - 1; *fwd = *inv = true; }
+    else if (pass == 1) { *axis = 1; *fwd = true; }
+    else { *axis = 1; *inv = true; }
+}
+
+// FP32 passes with padded length 512 run register-resident kernels with a
+// fixed decomposition: no schedule to choose.
+bool pass_uses_rr(const Plan *p, int pass)
+{
+    int axis;
+    bool f, i;
+    pass_axis(p, pass, &axis, &f, &i);
+    return p->opt.precision == GSM_FP32 && p->rr_conv && p->M[axis] == 512;
+}
+
+// Distinct orders of the default radices of M (forward: even first radix),
+// the default order first, at most `cap`.
+std::vector<Sched> sched_orders(int M, bool forward, size_t cap)
+{
+    Sched def;
+    std::vector<Sched> out;
+    if (!make_sched(M, &def)) return out;
+    out.push_back(def);
+    std::vector<int> r(def.r, def.r + def.nst);
+    std::sort(r.begin(), r.end());
+    do {
+        Sched sc;
+        if (out.size() >= cap) break;
+        if (!make_sched_order(M, r.data(), (int)r.size(), forward, &sc)) continue;
+        bool seen = false;
+        for (const Sched &o : out) seen |= same_sched(o, sc);
+        if (!seen) out.push_back(sc);
+    } while (std::next_permutation(r.begin(), r.end()));
+    return out;
+}
+
+// Candidate (forward, inverse) schedules of pass `pass`, the current pair
+// first: single-direction passes vary their own direction; the conv pass
+// tries the pairs whose forward last and inverse first stages can be fused,
+// then equal orders.
+std::vector<std::pair<Sched, Sched>> sched_candidates(const Plan *p, int pass)
+{
+    int axis;
+    bool f, i;
+    pass_axis(p, pass, &axis, &f, &i);
+    const int M = p->M[axis];
+    std::vector<std::pair<Sched, Sched>> out;
+    out.push_back({p->sched_f[axis], p->sched_i[axis]});
+    auto add = [&](const Sched &a, const Sched &b) {
+        for (const auto &o : out)
+            if (same_sched(o.first, a) && same_sched(o.second, b)) return;
+        out.push_back({a, b});
+    };
+    if (f && i) {
+        const std::vector<Sched> fw = sched_orders(M, true, 24), iv = sched_orders(M, false, 24);
+        for (const Sched &a : fw)
+            for (const Sched &b : iv)
+                if (out.size() < 10 && fused_radix(a, b) != 0) add(a, b);
+        for (const Sched &a : fw) {
+            Sched b = a;
+            if (out.size() < 12) add(a, b);
+        }
+    } else if (f) {
+        for (const Sched &a : sched_orders(M, true, 8)) add(a, p->sched_i[axis]);
+    } else {
+        for (const Sched &b : sched_orders(M, false, 8)) add(p->sched_f[axis], b);
+    }
+    return out;
+}
+
+gsm_status_t apply_axis_pair(Plan *p, int axis, const Sched &a, const Sched &b, cudaStream_t st)
+{
+    gsm_status_t s = GSM_OK;
+    if (!same_sched(p->sched_f[axis], a)) s = set_axis_schedule(p, axis, false, a, st);
+    if (s == GSM_OK && !same_sched(p->sched_i[axis], b)) s = set_axis_schedule(p, axis, true, b, st);
+    return s;
+}
+
+bool cache_lookup(const char *path, const std::string &key, int *nl, int *emax, std::string *fs, std::string *is)
 {
     FILE *f = fopen(path, "r");
     if (!f) return false;
@@ -979,15 +1111,33 @@ bool cache_lookup(const char *path, const std::string &key, int *nl, int *emax)
         const size_t kl = key.size();
         if (strncmp(line, key.c_str(), kl) == 0 && line[kl] == ' ') {
             int a = 0, b = 0;
-            if (sscanf(line + kl, " nl=%d emax=%d", &a, &b) == 2) {
+            char sf[64] = {0}, si[64] = {0};
+            if (sscanf(line + kl, " nl=%d emax=%d f=%63s i=%63s", &a, &b, sf, si) == 4) {
                 *nl = a;
                 *emax = b;
+                *fs = sf;
+                *is = si;
                 hit = true;
             }
         }
     }
     fclose(f);
     return hit;
+}
+
+template <class Pol>
+float time_pass(const Plan *p, int pass, const void *rho, void *u, cudaStream_t st, cudaEvent_t e0, cudaEvent_t e1,
+                cudaError_t *err)
+{
+    launch_pass_t<Pol>(p, pass, rho, u, st);
+    cudaEventRecord(e0, st);
+    for (int r = 0; r < 3; ++r) launch_pass_t<Pol>(p, pass, rho, u, st);
+    cudaEventRecord(e1, st);
+    *err = cudaEventSynchronize(e1);
+    if (*err == cudaSuccess) *err = cudaGetLastError();
+    float ms = 0.f;
+    if (*err == cudaSuccess) cudaEventElapsedTime(&ms, e0, e1);
+    return ms / 3.f;
 }
 
 template <class Pol>
@@ -1006,25 +1156,58 @@ gsm_status_t autotune_t(Plan *p, cudaStream_t st, std::string *report)
     if (e == cudaSuccess) e = cudaEventCreate(&e1);
     const char *cache = getenv("GSM_AUTOTUNE_CACHE");
     const int np = p->d == 3 ? 5 : 3;
-    char buf[256];
-    for (int pass = 0; pass < np; ++pass) launch_pass_t<Pol>(p, pass, rho, u, st);
-    for (int pass = 0; pass < np && e == cudaSuccess; ++pass) {
+    char buf[320];
+    gsm_status_t s = GSM_OK;
+    if (e == cudaSuccess)
+        for (int pass = 0; pass < np; ++pass) launch_pass_t<Pol>(p, pass, rho, u, st);
+    for (int pass = 0; pass < np && e == cudaSuccess && s == GSM_OK; ++pass) {
         PassCfg *cfg = pass_cfg(p, pass);
         const int M = pass_len(p, pass);
+        int axis;
+        bool df, di;
+        pass_axis(p, pass, &axis, &df, &di);
         const std::string key = tune_key(p, pass);
         int cnl = 0, cem = 0;
+        std::string cf, ci;
         if (cache) {
             std::lock_guard<std::mutex> lock(g_tune_mutex);
             PassCfg c;
-            if (cache_lookup(cache, key, &cnl, &cem) && make_cfg<Pol>(M, cnl, cem, &c) &&
+            Sched a, b;
+            if (cache_lookup(cache, key, &cnl, &cem, &cf, &ci) && make_cfg<Pol>(M, cnl, cem, &c) &&
+                sched_parse(cf.c_str(), p->M[axis], true, &a) && sched_parse(ci.c_str(), p->M[axis], false, &b) &&
                 raise_pass_smem<Pol>(p, pass, c) == cudaSuccess) {
+                s = apply_axis_pair(p, axis, df ? a : p->sched_f[axis], di ? b : p->sched_i[axis], st);
+                if (s != GSM_OK) break;
                 *cfg = c;
-                snprintf(buf, sizeof(buf), "pass %d M=%d cached nl=%d gthr=%d emax=%d\n", pass, M, c.nl, c.gthr,
-                         c.emax);
+                snprintf(buf, sizeof(buf), "pass %d M=%d cached nl=%d gthr=%d emax=%d fwd=%s inv=%s\n", pass, M, c.nl,
+                         c.gthr, c.emax, sched_str(p->sched_f[axis]).c_str(), sched_str(p->sched_i[axis]).c_str());
                 *report += buf;
                 continue;
             }
         }
+        // 1. the radix schedule, with the current launch shape
+        if (!pass_uses_rr(p, pass)) {
+            const auto cands = sched_candidates(p, pass);
+            size_t best_i = 0;
+            float best_ms = 1e30f;
+            for (size_t ci2 = 0; ci2 < cands.size() && e == cudaSuccess; ++ci2) {
+                s = apply_axis_pair(p, axis, cands[ci2].first, cands[ci2].second, st);
+                if (s != GSM_OK) break;
+                const float ms = time_pass<Pol>(p, pass, rho, u, st, e0, e1, &e);
+                if (e != cudaSuccess) break;
+                snprintf(buf, sizeof(buf), "pass %d M=%d schedule fwd=%s inv=%s: %.4f ms\n", pass, M,
+                         sched_str(cands[ci2].first).c_str(), sched_str(cands[ci2].second).c_str(), ms);
+                *report += buf;
+                if (ms < best_ms) {
+                    best_ms = ms;
+                    best_i = ci2;
+                }
+            }
+            if (s != GSM_OK || e != cudaSuccess) break;
+            s = apply_axis_pair(p, axis, cands[best_i].first, cands[best_i].second, st);
+            if (s != GSM_OK) break;
+        }
+        // 2. the launch shape (elements per thread, lines per CTA) with that schedule
         PassCfg best = *cfg;
         float best_ms = 1e30f;
         const int nls[] = {1, 2, 3, 4, 6, 8, 12, 16};
@@ -1034,15 +1217,8 @@ gsm_status_t autotune_t(Plan *p, cudaStream_t st, std::string *report)
                 if (!make_cfg<Pol>(M, nl, emax, &c)) continue;
                 if (raise_pass_smem<Pol>(p, pass, c) != cudaSuccess) continue;
                 *cfg = c;
-                launch_pass_t<Pol>(p, pass, rho, u, st);
-                cudaEventRecord(e0, st);
-                for (int r = 0; r < 3; ++r) launch_pass_t<Pol>(p, pass, rho, u, st);
-                cudaEventRecord(e1, st);
-                e = cudaEventSynchronize(e1);
+                const float ms = time_pass<Pol>(p, pass, rho, u, st, e0, e1, &e);
                 if (e != cudaSuccess) break;
-                float ms = 0.f;
-                cudaEventElapsedTime(&ms, e0, e1);
-                ms /= 3.f;
                 snprintf(buf, sizeof(buf), "pass %d M=%d nl=%d gthr=%d emax=%d smem=%zu: %.4f ms\n", pass, M, c.nl,
                          c.gthr, c.emax, c.smem, ms);
                 *report += buf;
@@ -1051,19 +1227,22 @@ gsm_status_t autotune_t(Plan *p, cudaStream_t st, std::string *report)
                     best = c;
                 }
             }
+            if (e != cudaSuccess) break;
         }
         *cfg = best;
         if (cache && e == cudaSuccess) {
             std::lock_guard<std::mutex> lock(g_tune_mutex);
             FILE *f = fopen(cache, "a");
             if (f) {
-                fprintf(f, "%s nl=%d emax=%d\n", key.c_str(), best.nl, best.emax);
+                fprintf(f, "%s nl=%d emax=%d f=%s i=%s\n", key.c_str(), best.nl, best.emax,
+                        sched_str(p->sched_f[axis]).c_str(), sched_str(p->sched_i[axis]).c_str());
                 fclose(f);
             }
         }
     }
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
+    if (s != GSM_OK) return s;
     GSM_CUDA_TRY(e);
     GSM_CUDA_TRY(cudaGetLastError());
     return GSM_OK;
@@ -1127,20 +1306,114 @@ bool make_sched(int M, Sched *s)
 
 size_t cplx_bytes(gsm_precision_t prec) { return prec == GSM_FP32 ? 8 : 16; }
 
-gsm_status_t make_twiddles(Plan *p, int axis, cudaStream_t st)
+namespace {
+
+// Whether the table made for (M, schedule a) serves (M, schedule b): equal M
+// and, in FP64 (whose tables end with the schedule's FMA-form constants),
+// equal schedules.
+bool table_serves(const Plan *p, const Sched &a, const Sched &b)
 {
-    for (int b = 0; b < axis; ++b)
-        if (p->M[b] == p->M[axis]) {
-            p->d_tw[axis] = p->d_tw[b];
+    return a.M == b.M && (p->opt.precision != GSM_FP64 || same_sched(a, b));
+}
+
+// The table of (axis, inverse?): an existing table that serves it, or a new one.
+gsm_status_t table_for(Plan *p, int axis, bool inverse, cudaStream_t st, void **out)
+{
+    const Sched &want = inverse ? p->sched_i[axis] : p->sched_f[axis];
+    for (int b = 0; b < p->d; ++b) {
+        if (p->d_tw[b] && table_serves(p, p->sched_f[b], want) && !(b == axis && inverse == false)) {
+            *out = p->d_tw[b];
             return GSM_OK;
         }
-    const int M = p->M[axis];
-    const size_t g8 = p->opt.precision == GSM_FP64 ? g8_table_doubles(p->sched[axis]) : 0;
-    GSM_CUDA_TRY(dev_alloc(&p->d_tw[axis], cplx_bytes(p->opt.precision) * M + sizeof(double) * g8));
-    k_twiddles<<<(M + 255) / 256, 256, 0, st>>>(M, p->opt.precision, p->d_tw[axis]);
-    if (g8 > 0) launch_g8table(p->sched[axis], static_cast<double2 *>(p->d_tw[axis]) + M, st);
-    GSM_CUDA_TRY(cudaGetLastError());
+        if (p->d_twi[b] && table_serves(p, p->sched_i[b], want) && !(b == axis && inverse == true)) {
+            *out = p->d_twi[b];
+            return GSM_OK;
+        }
+    }
+    const int M = want.M;
+    const size_t g8 = p->opt.precision == GSM_FP64 ? g8_table_doubles(want) : 0;
+    void *t = nullptr;
+    GSM_CUDA_TRY(dev_alloc(&t, cplx_bytes(p->opt.precision) * M + sizeof(double) * g8));
+    k_twiddles<<<(M + 255) / 256, 256, 0, st>>>(M, p->opt.precision, t);
+    if (g8 > 0) launch_g8table(want, static_cast<double2 *>(t) + M, st);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        dev_free(t);
+        GSM_CUDA_TRY(e);
+    }
+    *out = t;
     return GSM_OK;
+}
+
+// Frees the table t unless a table slot of the plan still holds it.
+void release_table(Plan *p, void *t)
+{
+    if (!t) return;
+    for (int b = 0; b < 3; ++b)
+        if (p->d_tw[b] == t || p->d_twi[b] == t) return;
+    dev_free(t);
+}
+
+}  // namespace
+
+gsm_status_t make_twiddles(Plan *p, int axis, cudaStream_t st)
+{
+    void *old_f = p->d_tw[axis], *old_i = p->d_twi[axis];
+    p->d_tw[axis] = p->d_twi[axis] = nullptr;
+    void *tf = nullptr, *ti = nullptr;
+    gsm_status_t s = table_for(p, axis, false, st, &tf);
+    if (s != GSM_OK) {
+        p->d_tw[axis] = old_f;
+        p->d_twi[axis] = old_i;
+        return s;
+    }
+    p->d_tw[axis] = tf;
+    s = table_for(p, axis, true, st, &ti);
+    if (s != GSM_OK) {
+        p->d_tw[axis] = old_f;
+        p->d_twi[axis] = old_i;
+        release_table(p, tf);
+        return s;
+    }
+    p->d_twi[axis] = ti;
+    // the device may still run work that reads the old tables: wait before freeing
+    if ((old_f && old_f != tf && old_f != ti) || (old_i && old_i != tf && old_i != ti)) {
+        GSM_CUDA_TRY(cudaStreamSynchronize(st));
+        release_table(p, old_f);
+        if (old_i != old_f) release_table(p, old_i);
+    }
+    return GSM_OK;
+}
+
+bool make_sched_order(int M, const int *radices, int count, bool forward, Sched *s)
+{
+    if (M < 2 || M > kMaxM || count < 1 || count > kMaxStages || !radices) return false;
+    long prod = 1;
+    for (int i = 0; i < count; ++i) {
+        const int r = radices[i];
+        if (r != 8 && r != 4 && r != 2 && r != 5 && r != 3) return false;
+        prod *= r;
+    }
+    if (prod != M) return false;
+    if (forward && (radices[0] % 2) != 0) return false;   // the pruned first stage of the zero-padded transform
+    s->M = M;
+    s->nst = count;
+    for (int i = 0; i < kMaxStages; ++i) s->r[i] = (unsigned char)(i < count ? radices[i] : 0);
+    return true;
+}
+
+gsm_status_t set_axis_schedule(Plan *p, int axis, bool inverse, const Sched &sc, cudaStream_t st)
+{
+    if (axis < 0 || axis >= p->d || sc.M != p->M[axis]) {
+        set_error("schedule does not fit the axis");
+        return GSM_ERR_INVALID_ARG;
+    }
+    Sched &slot = inverse ? p->sched_i[axis] : p->sched_f[axis];
+    const Sched old = slot;
+    slot = sc;
+    gsm_status_t s = make_twiddles(p, axis, st);
+    if (s != GSM_OK) slot = old;
+    return s;
 }
 
 gsm_status_t make_pass_multiplier(Plan *p, cudaStream_t st)
@@ -1159,11 +1432,13 @@ gsm_status_t make_pass_multiplier(Plan *p, cudaStream_t st)
 
 gsm_status_t configure_passes(Plan *p)
 {
-    for (int a = 0; a < p->d; ++a)
-        if (!make_sched(p->M[a], &p->sched[a])) {
+    for (int a = 0; a < p->d; ++a) {
+        if (!make_sched(p->M[a], &p->sched_f[a])) {
             set_error("padded length 2n must be a product of 2, 3 and 5");
             return GSM_ERR_UNSUPPORTED_SIZE;
         }
+        p->sched_i[a] = p->sched_f[a];
+    }
     switch (p->opt.precision) {
     case GSM_FP64: return configure_t<F64>(p);
     case GSM_FP32: return configure_t<F32>(p);
@@ -1190,6 +1465,7 @@ gsm_status_t x_slabs_t(const Plan *p, bool inverse, int z0, int z1, const void *
     const size_t in_off = (size_t)z0 * ny * nx, w_off = (size_t)z0 * hx * ny;
     S_t<Pol> *W1 = static_cast<S_t<Pol> *>(p->d_work1) + w_off;
     const tw *twx = static_cast<const tw *>(p->d_tw[0]);
+    const tw *twxi = static_cast<const tw *>(p->d_twi[0]);
     if (z1 <= z0) return GSM_OK;
     if constexpr (std::is_same<Pol, F32>::value) {
         if (p->M[0] == 512 && p->rr_conv) {
@@ -1204,14 +1480,14 @@ gsm_status_t x_slabs_t(const Plan *p, bool inverse, int z0, int z1, const void *
         dim3 g((ny + 2 * c.nl - 1) / (2 * c.nl), z1 - z0);
         const io *rho = static_cast<const io *>(rho_v) + in_off;
         with_emax(c, [&](auto E) {
-            k_xf<Pol, E()><<<g, c.nthr, c.smem, st>>>(rho, W1, nx, ny, hx, p->sched[0], c.nl, c.gthr, twx);
+            k_xf<Pol, E()><<<g, c.nthr, c.smem, st>>>(rho, W1, nx, ny, hx, p->sched_f[0], c.nl, c.gthr, twx);
         });
     } else {
         const PassCfg &c = p->cfg_xi;
         dim3 g((ny + 2 * c.nl - 1) / (2 * c.nl), z1 - z0);
         io *u = static_cast<io *>(u_v) + in_off;
         with_emax(c, [&](auto E) {
-            k_xi<Pol, E()><<<g, c.nthr, c.smem, st>>>(W1, u, nx, ny, hx, p->sched[0], c.nl, c.gthr, twx);
+            k_xi<Pol, E()><<<g, c.nthr, c.smem, st>>>(W1, u, nx, ny, hx, p->sched_i[0], c.nl, c.gthr, twxi);
         });
     }
     GSM_CUDA_TRY(cudaGetLastError());
@@ -1497,7 +1773,11 @@ gsm_status_t launch_queue_t(QueueArgs &a, const std::vector<const Plan *> &plans
             d.n[ax] = ax < p->d ? p->n[ax] : 1;
             d.M[ax] = ax < p->d ? p->M[ax] : 1;
             d.tw[ax] = ax < p->d ? p->d_tw[ax] : nullptr;
-            if (ax < p->d) d.sc[ax] = p->sched[ax];
+            d.twi[ax] = ax < p->d ? p->d_twi[ax] : nullptr;
+            if (ax < p->d) {
+                d.sc[ax] = p->sched_f[ax];
+                d.sci[ax] = p->sched_i[ax];
+            }
             if (ax < p->d) smem = std::max(smem, pass_smem<Pol>(p->M[ax], a.nl));
         }
         for (int pass = 0; pass < np; ++pass) {
