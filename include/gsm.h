@@ -127,6 +127,9 @@ typedef struct {
     int launch_emax[5];         /*   elements per thread (see gsm_plan_autotune) */
     double box[3];              /* half-width of each axis (L for a cube), x first */
     double beta;                /* exponent of the power kernels (1 otherwise) */
+    int radix_fwd[3][12];       /* per axis: radices of the forward FFT in stage order,
+                                   0 after the last (see gsm_plan_set_schedule) */
+    int radix_inv[3][12];       /* the same for the inverse FFT */
 } gsm_plan_info_t;
 
 void gsm_default_options(gsm_options_t *opt);
@@ -178,18 +181,39 @@ gsm_status_t gsm_apply(gsm_plan_t p, const void *rho, void *u, void *cuda_stream
 gsm_status_t gsm_apply_pass(gsm_plan_t p, int pass, const void *rho, void *u, void *cuda_stream);
 
 /*
- * Choose the launch shape of each pass by measurement (no counterpart in the
- * paper; it changes no result, only speed): for every pass, candidate shapes
- * (elements per thread, lines per CTA) are timed with CUDA events on the
- * plan's own workspace and the fastest is kept in the plan.  Temporary input
- * and output arrays are allocated for the run; the stream is synchronised.
- * If the environment variable GSM_AUTOTUNE_CACHE names a file, shapes found
- * there for this device, precision and grid are used without timing, and new
+ * Choose the radix schedule and the launch shape of each pass by measurement
+ * (no counterpart in the paper, whose FFTs come from a library).  For every
+ * pass: first its radix schedule (the order of the radix-8, 4, 2, 5, 3 stages
+ * of the pass's transform; for the conv pass the forward and the inverse
+ * schedule together, including the pairs whose forward last and inverse
+ * first stages share a radix and run fused with the multiplication), then its
+ * launch shape (elements per thread, lines per CTA), each timed with CUDA
+ * events on the plan's own workspace; the fastest is kept in the plan.  A
+ * different schedule rounds differently, so results may change in the last
+ * bits; the launch shape changes none.  Temporary input and output arrays are
+ * allocated for the run; the stream is synchronised.  If the environment
+ * variable GSM_AUTOTUNE_CACHE names a file, schedules and shapes found there
+ * for this device, precision and grid are used without timing, and new
  * results are appended.  `report` (may be NULL) receives a text table of the
  * timings, truncated to report_len bytes.  Same plan rules as gsm_apply: no
  * apply may be in flight on the plan.
  */
 gsm_status_t gsm_plan_autotune(gsm_plan_t p, void *cuda_stream, char *report, size_t report_len);
+
+/*
+ * Set the radix schedule of one transform of a plan (no counterpart in the
+ * paper): axis 0..d-1, inverse 0 for the forward FFT along that axis, 1 for
+ * the inverse; radices[0..count-1] in stage order, each 8, 4, 2, 5 or 3, their
+ * product the padded length M of the axis.  A forward schedule must start
+ * with an even radix (the first stage of the zero-padded transform is
+ * pruned).  The plan's twiddle tables for that transform are rebuilt on
+ * `cuda_stream` (synchronised when an old table is freed).  FP32 passes with
+ * a padded length of 512 use register-resident kernels of fixed shape and
+ * ignore the schedule.  Same plan rules as gsm_apply.  Errors:
+ * GSM_ERR_BAD_PLAN, GSM_ERR_INVALID_ARG (bad axis or schedule), GSM_ERR_OOM.
+ */
+gsm_status_t gsm_plan_set_schedule(gsm_plan_t p, int axis, int inverse, const int *radices, int count,
+                                   void *cuda_stream);
 
 /*
  * Same as gsm_apply with HOST arrays, synchronising the stream before it
@@ -275,8 +299,9 @@ gsm_status_t gsm_plan_info(gsm_plan_t p, gsm_plan_info_t *info);
  * gsm_plan_save writes into the HOST buffer `buf` (capacity bytes) the plan's
  * problem (kernel, d, n, box, delta, beta, dipolar n and m, requested accuracy), its
  * Gaussian sum (S, w_q, tau_q), Taylor coefficients c0, c2, the FP64 octant
- * kernel tensor ((n_x+1)(n_y+1)(n_z+1) doubles) and the launch shape of every
- * pass (as tuned by gsm_plan_autotune), followed by a 64-bit FNV-1a checksum.
+ * kernel tensor ((n_x+1)(n_y+1)(n_z+1) doubles), the launch shape of every
+ * pass and the radix schedules (as tuned by gsm_plan_autotune), followed by a
+ * 64-bit FNV-1a checksum.
  * *bytes always receives the size needed; with buf == NULL nothing else
  * happens (size query).  A buffer smaller than that size:
  * GSM_ERR_INVALID_ARG.  Synchronous (device-to-host copies).
@@ -284,9 +309,9 @@ gsm_status_t gsm_plan_info(gsm_plan_t p, gsm_plan_info_t *info);
  * gsm_plan_load creates a plan from such bytes without recomputing the
  * Gaussian sum, the Taylor coefficients or the tensor; the multiplier,
  * twiddles and workspace are rebuilt on `cuda_stream`.  precision < 0 keeps
- * the saved precision (and its launch shapes); GSM_FP64 / GSM_FP32 /
- * GSM_FP32X2 reuse the same FP64 tensor for another pass precision with
- * default launch shapes.  The result equals the saved plan bit for bit.  A
+ * the saved precision (and its launch shapes and schedules); GSM_FP64 /
+ * GSM_FP32 / GSM_FP32X2 reuse the same FP64 tensor for another pass precision
+ * with default launch shapes and schedules.  The result equals the saved plan bit for bit.  A
  * wrong magic, version, size or checksum: GSM_ERR_INVALID_ARG, *out = NULL.
  * The format is native little-endian; the caller owns buf.
  */

@@ -177,7 +177,16 @@ class Plan:
                 "launch_nl": list(inf.launch_nl[: inf.npasses]),
                 "launch_threads": list(inf.launch_threads[: inf.npasses]),
                 "launch_emax": list(inf.launch_emax[: inf.npasses]),
-                "box": tuple(inf.box[: self.d]), "beta": inf.beta}
+                "box": tuple(inf.box[: self.d]), "beta": inf.beta,
+                "radix_fwd": [[r for r in inf.radix_fwd[a] if r] for a in range(self.d)],
+                "radix_inv": [[r for r in inf.radix_inv[a] if r] for a in range(self.d)]}
+
+    def set_schedule(self, axis: int, radices, inverse: bool = False, stream=None):
+        """Radix order of the forward (or inverse) FFT along `axis`
+        (gsm_plan_set_schedule), e.g. (4, 8, 8) for a padded length of 256."""
+        r = (ctypes.c_int * len(radices))(*[int(v) for v in radices])
+        _abi.check(_abi.load().gsm_plan_set_schedule(self.handle, int(axis), 1 if inverse else 0, r, len(radices),
+                                                     _stream_ptr(stream)))
 
     def gs_terms(self):
         nt = self.info()["nterms"]
@@ -220,8 +229,8 @@ class Plan:
         return out
 
     def autotune(self, stream=None) -> str:
-        """Time candidate launch shapes of every pass and keep the fastest
-        (gsm_plan_autotune); returns the timing report."""
+        """Time candidate radix schedules and launch shapes of every pass and
+        keep the fastest (gsm_plan_autotune); returns the timing report."""
         buf = ctypes.create_string_buffer(1 << 16)
         _abi.check(_abi.load().gsm_plan_autotune(self.handle, _stream_ptr(stream), buf, len(buf)))
         return buf.value.decode()

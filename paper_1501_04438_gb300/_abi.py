@@ -21,7 +21,7 @@ EXPORTS = ["gsm_default_options", "gsm_plan", "gsm_apply", "gsm_apply_pass", "gs
            "gsm_plan_gs_terms", "gsm_plan_kernel_tensor", "gsm_plan_factors", "gsm_fft_lines",
            "gsm_fft_lines_noalloc", "gsm_batch_create", "gsm_batch_launch", "gsm_batch_destroy",
            "gsm_plan_save", "gsm_plan_load", "gsm_debug_fail_alloc", "gsm_debug_alloc_stats",
-           "gsm_batch_wait", "gsm_debug_batch_wait"]
+           "gsm_batch_wait", "gsm_debug_batch_wait", "gsm_plan_set_schedule"]
 
 
 class Options(ctypes.Structure):
@@ -37,7 +37,8 @@ class PlanInfo(ctypes.Structure):
                 ("precision", ctypes.c_int), ("bytes_multiplier", ctypes.c_size_t),
                 ("bytes_workspace", ctypes.c_size_t), ("npasses", ctypes.c_int),
                 ("launch_nl", ctypes.c_int * 5), ("launch_threads", ctypes.c_int * 5),
-                ("launch_emax", ctypes.c_int * 5), ("box", ctypes.c_double * 3), ("beta", ctypes.c_double)]
+                ("launch_emax", ctypes.c_int * 5), ("box", ctypes.c_double * 3), ("beta", ctypes.c_double),
+                ("radix_fwd", (ctypes.c_int * 12) * 3), ("radix_inv", (ctypes.c_int * 12) * 3)]
 
 
 class GSMError(RuntimeError):
@@ -72,6 +73,7 @@ def load(path: str = LIB_PATH):
         L.gsm_apply_host.argtypes = [_vp, _vp, _vp, _vp]
         L.gsm_apply_pass.argtypes = [_vp, ctypes.c_int, _vp, _vp, _vp]
         L.gsm_plan_autotune.argtypes = [_vp, _vp, ctypes.c_char_p, ctypes.c_size_t]
+        L.gsm_plan_set_schedule.argtypes = [_vp, ctypes.c_int, ctypes.c_int, _ip, ctypes.c_int, _vp]
         L.gsm_apply_batched.argtypes = [ctypes.c_int, ctypes.POINTER(_vp), ctypes.POINTER(_vp),
                                         ctypes.POINTER(_vp), _vp]
         L.gsm_batch_create.argtypes = [ctypes.POINTER(_vp), ctypes.c_int, ctypes.POINTER(_vp), ctypes.POINTER(_vp),

@@ -327,7 +327,7 @@ gsm_status_t gsm_plan(gsm_plan_t *out, gsm_kernel_t kind, int d, double L, const
 // Gaussian sum (w, tau), the FP64 octant kernel tensor, then a 64-bit FNV-1a
 // checksum of everything before it.
 static const uint64_t kSaveMagic = 0x47534d5341564531ull;   // "GSMSAVE1"
-static const uint32_t kSaveVersion = 2;
+static const uint32_t kSaveVersion = 3;
 
 struct SaveHeader {
     uint64_t magic;
@@ -335,7 +335,9 @@ struct SaveHeader {
     int32_t kind, d, n[3], precision, S, nterms, npasses, nl[5], emax[5], pad_;
     double L, eta[3], eps, delta, dip_n[3], dip_m[3], gs_err, c0, c2, beta;
     uint64_t mult_elems;
+    uint8_t radix[2][3][kMaxStages];   // forward, inverse radices per axis (0 after the last)
 };
+static_assert(sizeof(SaveHeader) % 8 == 0, "the arrays after the header stay 8-byte aligned");
 
 static uint64_t fnv1a(const unsigned char *b, size_t len)
 {
@@ -398,6 +400,11 @@ gsm_status_t gsm_plan_save(gsm_plan_t h, void *buf, size_t capacity, size_t *byt
     hd.c2 = p->c2;
     hd.beta = p->opt.beta;
     hd.mult_elems = p->mult_elems;
+    for (int a = 0; a < p->d; ++a)
+        for (int st = 0; st < kMaxStages; ++st) {
+            hd.radix[0][a][st] = st < p->sched_f[a].nst ? p->sched_f[a].r[st] : 0;
+            hd.radix[1][a][st] = st < p->sched_i[a].nst ? p->sched_i[a].r[st] : 0;
+        }
     unsigned char *b = static_cast<unsigned char *>(buf);
     memcpy(b, &hd, sizeof(hd));
     size_t off = sizeof(hd);
@@ -495,6 +502,24 @@ gsm_status_t gsm_plan_load(gsm_plan_t *out, const void *buf, size_t bytes, int p
         // cannot run keeps the default
         for (int i = 0; i < hd.npasses; ++i)
             if (set_pass_shape(p, i, hd.nl[i], hd.emax[i]) != GSM_OK) set_error("");
+        // and the saved schedules; one this plan cannot take keeps the default
+        for (int a = 0; a < hd.d; ++a)
+            for (int dir = 0; dir < 2; ++dir) {
+                int r[kMaxStages], cnt = 0;
+                while (cnt < kMaxStages && hd.radix[dir][a][cnt] != 0) {
+                    r[cnt] = hd.radix[dir][a][cnt];
+                    ++cnt;
+                }
+                Sched sc;
+                if (cnt > 0 && make_sched_order(p->M[a], r, cnt, dir == 0, &sc)) {
+                    gsm_status_t ss = set_axis_schedule(p, a, dir == 1, sc, static_cast<cudaStream_t>(cuda_stream));
+                    if (ss == GSM_ERR_OOM) {
+                        release_handle(g_live_plans, p);
+                        free_plan(p);
+                        return ss;
+                    }
+                }
+            }
     }
     *out = h;
     return GSM_OK;
@@ -926,7 +951,32 @@ gsm_status_t gsm_plan_info(gsm_plan_t h, gsm_plan_info_t *info)
         info->launch_threads[i] = c->gthr;
         info->launch_emax[i] = c->emax;
     }
+    for (int a = 0; a < p->d; ++a)
+        for (int st = 0; st < 12 && st < kMaxStages; ++st) {
+            info->radix_fwd[a][st] = st < p->sched_f[a].nst ? p->sched_f[a].r[st] : 0;
+            info->radix_inv[a][st] = st < p->sched_i[a].nst ? p->sched_i[a].r[st] : 0;
+        }
     return GSM_OK;
+}
+
+gsm_status_t gsm_plan_set_schedule(gsm_plan_t h, int axis, int inverse, const int *radices, int count,
+                                   void *cuda_stream)
+{
+    Plan *p = checked(h);
+    if (!p) {
+        set_error("bad plan handle");
+        return GSM_ERR_BAD_PLAN;
+    }
+    if (axis < 0 || axis >= p->d || !radices) {
+        set_error("axis out of range or radices NULL");
+        return GSM_ERR_INVALID_ARG;
+    }
+    Sched sc;
+    if (!make_sched_order(p->M[axis], radices, count, inverse == 0, &sc)) {
+        set_error("radices must be 8, 4, 2, 5 or 3 with product 2n of the axis (forward: even first radix)");
+        return GSM_ERR_INVALID_ARG;
+    }
+    return set_axis_schedule(p, axis, inverse != 0, sc, static_cast<cudaStream_t>(cuda_stream));
 }
 
 gsm_status_t gsm_plan_destroy(gsm_plan_t h)

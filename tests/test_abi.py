@@ -79,12 +79,14 @@ def test_box_and_saved_plan_errors_without_gpu(libpath):
     size = ctypes.c_size_t()
     assert lib.gsm_plan_save(None, None, 0, ctypes.byref(size)) == 7
     assert lib.gsm_plan_load(ctypes.byref(h), b"short", 5, -1, None) == 1
-    # a header of the saved layout: magic, version, header bytes, 20 int32, 16 doubles, u64
+    # a header of the saved layout: magic, version, header bytes, 20 int32, 16 doubles, u64,
+    # then the forward and inverse radices of three axes (12 bytes each)
     nterms = 4
     ints = [0, 3, 8, 8, 8, 0, 3, nterms, 5] + [1] * 5 + [8] * 5 + [0]
     dbl = [1.0, 1.0, 1.0, 1.0, 2e-15, 1e-3, 0, 0, 1, 0, 0, 1, 0.0, 0.0, 0.0, 1.0]
-    hdr = struct.pack("<QII20i16dQ", 0x47534D5341564531, 2, 232, *ints, *dbl, 9 ** 3)
-    assert len(hdr) == 232
+    radices = bytes([8, 2] + [0] * 10) * 6
+    hdr = struct.pack("<QII20i16dQ", 0x47534D5341564531, 3, 304, *ints, *dbl, 9 ** 3) + radices
+    assert len(hdr) == 304
     body = hdr + b"\0" * (8 * (2 * nterms + 9 ** 3))
     bad = body + struct.pack("<Q", 12345)
     assert lib.gsm_plan_load(ctypes.byref(h), bad, len(bad), -1, None) == 1

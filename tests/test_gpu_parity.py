@@ -340,21 +340,99 @@ def test_hartree_energy_and_gradient(gsm, kernel):
     assert np.max(np.abs(g - g_o)) < 1e-12 * np.max(np.abs(g_o))
 
 
+def _orders(radices, forward):
+    """Distinct orders of a multiset of radices; forward transforms start with
+    an even radix (their first stage is pruned)."""
+    import itertools
+    out = []
+    for perm in itertools.permutations(radices):
+        if perm not in out and (not forward or perm[0] % 2 == 0):
+            out.append(perm)
+    return out
+
+
+SCHED_CASES = [
+    ("coulomb3d", (24, 20, 16), 3.0),     # M = 48 (8 2 3), 40 (8 5), 32 (8 4)
+    ("coulomb3d", (12, 48, 40), 3.0),     # M = 24 (8 3), 96 (8 4 3), 80 (8 2 5)
+    ("poisson2d", (96, 120), 6.0),        # M = 192 (8 8 3), 240 (8 2 5 3)
+]
+
+
 @pytest.mark.parametrize("precision", ["fp64", "fp32x2", "fp32"])
-def test_autotune_changes_no_bits(gsm, precision):
+@pytest.mark.parametrize("kernel,n,L", SCHED_CASES, ids=[f"{c[0]}-{'x'.join(map(str, c[1]))}" for c in SCHED_CASES])
+def test_radix_schedules_against_oracle(gsm, kernel, n, L, precision):
+    """Every order of each axis's radices, forward and inverse (conv axis: the
+    pairs whose forward last and inverse first stages share a radix run fused
+    with the multiplication), against the oracle: stages with odd strides
+    (radix 8 or 4 after 5 or 3, in FMA form in FP64; radix 2 after an odd
+    radix, in plain form), pruned first stages of radix 2, 4 and 8."""
+    torch = _torch()
+    rho = np.random.default_rng(81).standard_normal(tuple(reversed(n)))
+    uo, _ = oracle.apply(kernel, rho, L, taylor_mode=1)
+    dt = torch.float32 if precision == "fp32" else torch.float64
+    r = torch.tensor(rho, dtype=dt, device="cuda")
+    plan = gsm.Plan(kernel, L, n, precision=precision)
+    info = plan.info()
+    d = len(n)
+    runs = 0
+    for axis in range(d):
+        base_f, base_i = info["radix_fwd"][axis], info["radix_inv"][axis]
+        fw = _orders(base_f, True)[:6]
+        iv = _orders(base_i, False)[:6]
+        for f in fw:
+            plan.set_schedule(axis, f)
+            for i in iv:
+                plan.set_schedule(axis, i, inverse=True)
+                u = plan.apply(r).double().cpu().numpy()
+                assert_rel(u, uo, tol(precision, plan), f"axis {axis} fwd {f} inv {i}")
+                runs += 1
+        plan.set_schedule(axis, base_f)
+        plan.set_schedule(axis, base_i, inverse=True)
+    assert runs >= 10
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32x2", "fp32"])
+def test_autotune_picks_valid_schedules(gsm, precision):
+    """The tuner's schedules and shapes: each schedule a valid order of the
+    axis's radices (forward: even first), the result against the oracle, and
+    a saved plan keeps them."""
     torch = _torch()
     dt = torch.float32 if precision == "fp32" else torch.float64
     for kernel, n in (("coulomb3d", (24, 20, 16)), ("poisson2d", (120, 96))):
-        d = len(n)
         rho = np.random.default_rng(14).standard_normal(tuple(reversed(n)))
         plan = gsm.Plan(kernel, 3.0, n, precision=precision)
-        r = torch.tensor(rho, dtype=dt, device="cuda")
-        u0 = plan.apply(r).clone()
         report = plan.autotune()
-        assert "pass" in report
-        u1 = plan.apply(r)
-        torch.cuda.synchronize()
-        assert torch.equal(u0, u1)
+        assert "schedule" in report and "nl=" in report
+        info = plan.info()
+        for axis in range(len(n)):
+            for rad, fwd in ((info["radix_fwd"][axis], True), (info["radix_inv"][axis], False)):
+                assert int(np.prod(rad)) == info["M"][axis] and set(rad) <= {8, 4, 2, 5, 3}
+                assert not fwd or rad[0] % 2 == 0
+        u = plan.apply(torch.tensor(rho, dtype=dt, device="cuda")).double().cpu().numpy()
+        uo, _ = oracle.apply(kernel, rho, 3.0, taylor_mode=1)
+        assert_rel(u, uo, tol(precision, plan), f"{kernel} tuned")
+        loaded = gsm.Plan.load(plan.save())
+        li = loaded.info()
+        assert li["radix_fwd"] == info["radix_fwd"] and li["radix_inv"] == info["radix_inv"]
+        u2 = loaded.apply(torch.tensor(rho, dtype=dt, device="cuda")).double().cpu().numpy()
+        assert np.array_equal(u, u2)
+
+
+def test_launch_shape_changes_no_bits(gsm):
+    """A launch shape (lines per CTA, elements per thread) changes only how the
+    same butterflies are spread over threads: the same bits."""
+    torch = _torch()
+    rho = torch.tensor(np.random.default_rng(15).standard_normal((16, 20, 24)), device="cuda")
+    plan = gsm.Plan("coulomb3d", 3.0, (24, 20, 16))
+    u0 = plan.apply(rho).clone()
+    plan.autotune()        # also picks schedules: set the defaults back
+    info0 = gsm.Plan("coulomb3d", 3.0, (24, 20, 16)).info()
+    for axis in range(3):
+        plan.set_schedule(axis, info0["radix_fwd"][axis])
+        plan.set_schedule(axis, info0["radix_inv"][axis], inverse=True)
+    u1 = plan.apply(rho)
+    torch.cuda.synchronize()
+    assert torch.equal(u0, u1)
 
 
 # ------------------------------------------------------------------ full sizes
