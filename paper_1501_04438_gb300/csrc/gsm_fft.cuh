@@ -621,6 +621,7 @@ __device__ __forceinline__ void fft_line(typename Pol::scplx *s, const Sched &sc
             }
             size_t goff = gtable_offset(sc, st);
             while (st < nend) {
+                const int st0 = st;
                 for (; st < nend && sc.r[st] == 8; ++st, Ns *= 8) {
                     if (CROP && st == last) fft_stage_fma<8, FWD, (EMAX + 7) / 8, 2>(s, M, Ns, gt + goff, g);
                     else fft_stage_fma<8, FWD, (EMAX + 7) / 8, 0>(s, M, Ns, gt + goff, g);
@@ -642,16 +643,19 @@ __device__ __forceinline__ void fft_line(typename Pol::scplx *s, const Sched &sc
                 }
                 for (; st < nend && sc.r[st] == 5; ++st, Ns *= 5) GSM_STAGE(5);
                 for (; st < nend && sc.r[st] == 3; ++st, Ns *= 3) GSM_STAGE(3);
+                if (st == st0) break;   // a radix outside 8, 4, 2, 5, 3 (schedules are checked on the host)
             }
             return;
         }
     }
     while (st < nend) {
+        const int st0 = st;
         for (; st < nend && sc.r[st] == 8; ++st, Ns *= 8) GSM_STAGE(8);
         for (; st < nend && sc.r[st] == 4; ++st, Ns *= 4) GSM_STAGE(4);
         for (; st < nend && sc.r[st] == 2; ++st, Ns *= 2) GSM_STAGE(2);
         for (; st < nend && sc.r[st] == 5; ++st, Ns *= 5) GSM_STAGE(5);
         for (; st < nend && sc.r[st] == 3; ++st, Ns *= 3) GSM_STAGE(3);
+        if (st == st0) break;
     }
 #undef GSM_STAGE
 }
