@@ -204,9 +204,16 @@ gsm_status_t gsm_plan_autotune(gsm_plan_t p, void *cuda_stream, char *report, si
  * Set the radix schedule of one transform of a plan (no counterpart in the
  * paper): axis 0..d-1, inverse 0 for the forward FFT along that axis, 1 for
  * the inverse; radices[0..count-1] in stage order, each 8, 4, 2, 5 or 3, their
- * product the padded length M of the axis.  A forward schedule must start
- * with an even radix (the first stage of the zero-padded transform is
- * pruned).  The plan's twiddle tables for that transform are rebuilt on
+ * product the padded length M of the axis, in the order the FFT engine runs
+ * stages: all 8s, then 4s, 2s, 5s, 3s (so a forward schedule starts with an
+ * even radix, as the pruned first stage of the zero-padded transform needs).
+ * One exception: the inverse along the last axis (the conv pass) may start
+ * with the last radix of that axis's forward schedule, followed by the rest in
+ * engine order; those two stages then run fused with the multiplication
+ * (e.g. forward 8 8 4, inverse 4 8 8).  A change that would leave the pair
+ * invalid is refused: to move from such a pair to another forward schedule,
+ * set the inverse to an engine-order schedule first.  The plan's twiddle
+ * tables for that axis are rebuilt on
  * `cuda_stream` (synchronised when an old table is freed).  FP32 passes with
  * a padded length of 512 use register-resident kernels of fixed shape and
  * ignore the schedule.  Same plan rules as gsm_apply.  Errors:

@@ -502,24 +502,26 @@ gsm_status_t gsm_plan_load(gsm_plan_t *out, const void *buf, size_t bytes, int p
         // cannot run keeps the default
         for (int i = 0; i < hd.npasses; ++i)
             if (set_pass_shape(p, i, hd.nl[i], hd.emax[i]) != GSM_OK) set_error("");
-        // and the saved schedules; one this plan cannot take keeps the default
-        for (int a = 0; a < hd.d; ++a)
-            for (int dir = 0; dir < 2; ++dir) {
+        // and the saved schedules; a pair this plan cannot take keeps the default
+        for (int a = 0; a < hd.d; ++a) {
+            Sched sc[2];
+            bool ok = true;
+            for (int dir = 0; dir < 2 && ok; ++dir) {
                 int r[kMaxStages], cnt = 0;
                 while (cnt < kMaxStages && hd.radix[dir][a][cnt] != 0) {
                     r[cnt] = hd.radix[dir][a][cnt];
                     ++cnt;
                 }
-                Sched sc;
-                if (cnt > 0 && make_sched_order(p->M[a], r, cnt, dir == 0, &sc)) {
-                    gsm_status_t ss = set_axis_schedule(p, a, dir == 1, sc, static_cast<cudaStream_t>(cuda_stream));
-                    if (ss == GSM_ERR_OOM) {
-                        release_handle(g_live_plans, p);
-                        free_plan(p);
-                        return ss;
-                    }
-                }
+                ok = cnt > 0 && make_sched_order(p->M[a], r, cnt, dir == 0, &sc[dir]);
             }
+            if (!ok || !axis_pair_ok(p, a, sc[0], sc[1])) continue;
+            gsm_status_t ss = set_axis_pair(p, a, sc[0], sc[1], static_cast<cudaStream_t>(cuda_stream));
+            if (ss == GSM_ERR_OOM) {
+                release_handle(g_live_plans, p);
+                free_plan(p);
+                return ss;
+            }
+        }
     }
     *out = h;
     return GSM_OK;

@@ -566,13 +566,33 @@ __device__ __forceinline__ void fft_stage_fma(double2 *s, int M, int Ns, const d
     group_sync(g);
 }
 
+// Rank of a radix in the order the stages of a schedule run in: 8, 4, 2, 5, 3.
+__host__ __device__ __forceinline__ int radix_rank(int R)
+{
+    return R == 8 ? 0 : R == 4 ? 1 : R == 2 ? 2 : R == 5 ? 3 : R == 3 ? 4 : 99;
+}
+
+// Whether stages [from, nst) of sc are in the order 8, 4, 2, 5, 3 (radices of
+// equal rank together), the only order fft_line runs.
+__host__ __device__ inline bool sched_sorted_from(const Sched &sc, int from)
+{
+    for (int i = from; i < sc.nst; ++i) {
+        if (radix_rank(sc.r[i]) > 4) return false;
+        if (i > from && radix_rank(sc.r[i]) < radix_rank(sc.r[i - 1])) return false;
+    }
+    return true;
+}
+
 // All stages of the FFT of one line by one group.  EMAX bounds the elements
 // per thread (M <= EMAX * T).  The caller synchronises the group (or CTA)
 // after writing the line; the last stage ends with a group barrier, so the
-// group may read the result right away.  The schedule may list its radices
-// in any order: the stages run in runs of equal radix, each radix with a loop
-// of its own (a loop mixing several large stage bodies costs the register
-// allocator dearly), the five loops repeated until every stage has run.
+// group may read the result right away.  The stages from st_begin on must be
+// in the order 8, 4, 2, 5, 3 (sched_sorted_from, checked on the host): each
+// radix gets one loop of its own, once (a loop mixing several large stage
+// bodies, or one loop around these loops, costs the register allocator
+// dearly: measured 11 % on the double-float passes).  Schedules that start
+// with another radix (the inverse of a conv pass whose first stage is fused,
+// fft_fused_mid) run from st_begin = 1.
 // ZPAD: the second half of the input is zero and is not read (the first stage
 // is pruned, so the first radix must be even); the caller need not write it.
 // CROP: only the first half of the output is needed (the last stage is pruned
@@ -620,55 +640,40 @@ __device__ __forceinline__ void fft_line(typename Pol::scplx *s, const Sched &sc
                 Ns = r0;
             }
             size_t goff = gtable_offset(sc, st);
-            while (st < nend) {
-                const int st0 = st;
-                for (; st < nend && sc.r[st] == 8; ++st, Ns *= 8) {
-                    if (CROP && st == last) fft_stage_fma<8, FWD, (EMAX + 7) / 8, 2>(s, M, Ns, gt + goff, g);
-                    else fft_stage_fma<8, FWD, (EMAX + 7) / 8, 0>(s, M, Ns, gt + goff, g);
-                    goff += gblock(8, Ns);
-                }
-                for (; st < nend && sc.r[st] == 4; ++st, Ns *= 4) {
-                    if (CROP && st == last) fft_stage_fma<4, FWD, (EMAX + 3) / 4, 2>(s, M, Ns, gt + goff, g);
-                    else fft_stage_fma<4, FWD, (EMAX + 3) / 4, 0>(s, M, Ns, gt + goff, g);
-                    goff += gblock(4, Ns);
-                }
-                for (; st < nend && sc.r[st] == 2; ++st, Ns *= 2) {
-                    if (gtabled_at(2, Ns)) {
-                        if (CROP && st == last) fft_stage_fma<2, FWD, (EMAX + 1) / 2, 2>(s, M, Ns, gt + goff, g);
-                        else fft_stage_fma<2, FWD, (EMAX + 1) / 2, 0>(s, M, Ns, gt + goff, g);
-                        goff += gblock(2, Ns);
-                    } else {
-                        GSM_STAGE(2);
-                    }
-                }
-                for (; st < nend && sc.r[st] == 5; ++st, Ns *= 5) GSM_STAGE(5);
-                for (; st < nend && sc.r[st] == 3; ++st, Ns *= 3) GSM_STAGE(3);
-                if (st == st0) break;   // a radix outside 8, 4, 2, 5, 3 (schedules are checked on the host)
+            for (; st < nend && sc.r[st] == 8; ++st, Ns *= 8) {
+                if (CROP && st == last) fft_stage_fma<8, FWD, (EMAX + 7) / 8, 2>(s, M, Ns, gt + goff, g);
+                else fft_stage_fma<8, FWD, (EMAX + 7) / 8, 0>(s, M, Ns, gt + goff, g);
+                goff += gblock(8, Ns);
             }
-            return;
+            for (; st < nend && sc.r[st] == 4; ++st, Ns *= 4) {
+                if (CROP && st == last) fft_stage_fma<4, FWD, (EMAX + 3) / 4, 2>(s, M, Ns, gt + goff, g);
+                else fft_stage_fma<4, FWD, (EMAX + 3) / 4, 0>(s, M, Ns, gt + goff, g);
+                goff += gblock(4, Ns);
+            }
+            for (; st < nend && sc.r[st] == 2 && gtabled_at(2, Ns); ++st, Ns *= 2) {
+                if (CROP && st == last) fft_stage_fma<2, FWD, (EMAX + 1) / 2, 2>(s, M, Ns, gt + goff, g);
+                else fft_stage_fma<2, FWD, (EMAX + 1) / 2, 0>(s, M, Ns, gt + goff, g);
+                goff += gblock(2, Ns);
+            }
         }
     }
-    while (st < nend) {
-        const int st0 = st;
-        for (; st < nend && sc.r[st] == 8; ++st, Ns *= 8) GSM_STAGE(8);
-        for (; st < nend && sc.r[st] == 4; ++st, Ns *= 4) GSM_STAGE(4);
-        for (; st < nend && sc.r[st] == 2; ++st, Ns *= 2) GSM_STAGE(2);
-        for (; st < nend && sc.r[st] == 5; ++st, Ns *= 5) GSM_STAGE(5);
-        for (; st < nend && sc.r[st] == 3; ++st, Ns *= 3) GSM_STAGE(3);
-        if (st == st0) break;
-    }
+    for (; st < nend && sc.r[st] == 8; ++st, Ns *= 8) GSM_STAGE(8);
+    for (; st < nend && sc.r[st] == 4; ++st, Ns *= 4) GSM_STAGE(4);
+    for (; st < nend && sc.r[st] == 2; ++st, Ns *= 2) GSM_STAGE(2);
+    for (; st < nend && sc.r[st] == 5; ++st, Ns *= 5) GSM_STAGE(5);
+    for (; st < nend && sc.r[st] == 3; ++st, Ns *= 3) GSM_STAGE(3);
 #undef GSM_STAGE
 }
 
 // The radix of the stage that fft_fused_mid can fuse for a transform whose
 // forward schedule is scf and inverse schedule sci: the forward's last radix
-// when the inverse starts with the same radix (8, 4 or 2) and both have at
-// least two stages; 0 when they cannot be fused.
+// when the inverse starts with the same radix and both have at least two
+// stages; 0 when they cannot be fused.
 __host__ __device__ __forceinline__ int fused_radix(const Sched &scf, const Sched &sci)
 {
     if (scf.nst < 2 || sci.nst < 2) return 0;
     const int R = scf.r[scf.nst - 1];
-    return (R == sci.r[0] && gtabled(R)) ? R : 0;
+    return R == sci.r[0] ? R : 0;
 }
 
 // The last forward stage (radix R, schedule scf), a pointwise multiplication
@@ -694,7 +699,7 @@ __device__ __forceinline__ void fft_fused_mid(typename Pol::scplx *s, const Sche
 #pragma unroll
             for (int t = 0; t < R; ++t) v[i][t] = Pol::ld(s[pidx<Pol>(b + t * nb)]);
             bool done = false;
-            if constexpr (std::is_same<Pol, F64>::value) {
+            if constexpr (std::is_same<Pol, F64>::value && (R == 8 || R == 4 || R == 2)) {
                 if (gt != nullptr && gtabled_at(R, nb)) {
                     const double *c = gt + gtable_offset(scf, scf.nst - 1) + gindex(R, b);
                     if constexpr (R == 8) bfly8_fma<true, 8>(v[i], c);

@@ -168,8 +168,11 @@ bool make_sched(int M, Sched *s);
 // product M); forward: the first radix must be even (the pruned first stage
 // of a zero-padded transform)
 bool make_sched_order(int M, const int *radices, int count, bool forward, Sched *s);
-// set the schedule of one axis and direction and rebuild that axis's tables
+// set the schedule of one axis and direction, or both, and rebuild that axis's tables
 gsm_status_t set_axis_schedule(Plan *p, int axis, bool inverse, const Sched &sc, cudaStream_t st);
+gsm_status_t set_axis_pair(Plan *p, int axis, const Sched &f, const Sched &i, cudaStream_t st);
+// whether a (forward, inverse) pair of schedules can run on the axis
+bool axis_pair_ok(const Plan *p, int axis, const Sched &f, const Sched &i);
 size_t cplx_bytes(gsm_precision_t prec);
 
 }  // namespace gsm

@@ -210,7 +210,9 @@ __device__ __forceinline__ void body_conv(S_t<Pol> *__restrict__ W, const typena
         fft_line<Pol, true, EMAX, true, false>(s, sc, tw, g, gt, 0, sc.nst - 1);
         if (fr == 8) fft_fused_mid<Pol, 8, (EMAX + 7) / 8>(s, sc, tw, g, gt, mult_of);
         else if (fr == 4) fft_fused_mid<Pol, 4, (EMAX + 3) / 4>(s, sc, tw, g, gt, mult_of);
-        else fft_fused_mid<Pol, 2, (EMAX + 1) / 2>(s, sc, tw, g, gt, mult_of);
+        else if (fr == 2) fft_fused_mid<Pol, 2, (EMAX + 1) / 2>(s, sc, tw, g, gt, mult_of);
+        else if (fr == 5) fft_fused_mid<Pol, 5, (EMAX + 4) / 5>(s, sc, tw, g, gt, mult_of);
+        else fft_fused_mid<Pol, 3, (EMAX + 2) / 3>(s, sc, tw, g, gt, mult_of);
         fft_line<Pol, false, EMAX, false, true>(s, sci, twi, g, gti, 1);
     } else {
         fft_line<Pol, true, EMAX, true, false>(s, sc, tw, g, gt);
@@ -1038,31 +1040,63 @@ bool pass_uses_rr(const Plan *p, int pass)
     return p->opt.precision == GSM_FP32 && p->rr_conv && p->M[axis] == 512;
 }
 
-// Distinct orders of the default radices of M (forward: even first radix),
-// the default order first, at most `cap`.
-std::vector<Sched> sched_orders(int M, bool forward, size_t cap)
+// Factorisations of M into radices 8, 4, 2, 5, 3 in the order fft_line runs
+// them, with at most one stage more than the default schedule; the default
+// first, at most `cap`.
+void factorise(int M, int from_rank, std::vector<int> &cur, int max_st, std::vector<std::vector<int>> &out)
+{
+    static const int radices[5] = {8, 4, 2, 5, 3};
+    if (M == 1) {
+        out.push_back(cur);
+        return;
+    }
+    if ((int)cur.size() >= max_st) return;
+    for (int k = from_rank; k < 5; ++k)
+        if (M % radices[k] == 0) {
+            cur.push_back(radices[k]);
+            factorise(M / radices[k], k, cur, max_st, out);
+            cur.pop_back();
+        }
+}
+
+std::vector<Sched> sched_factorisations(int M, size_t cap)
 {
     Sched def;
     std::vector<Sched> out;
     if (!make_sched(M, &def)) return out;
     out.push_back(def);
-    std::vector<int> r(def.r, def.r + def.nst);
-    std::sort(r.begin(), r.end());
-    do {
-        Sched sc;
+    std::vector<std::vector<int>> all;
+    std::vector<int> cur;
+    factorise(M, 0, cur, def.nst + 1, all);
+    std::sort(all.begin(), all.end(), [](const std::vector<int> &x, const std::vector<int> &y) {
+        return x.size() < y.size();
+    });
+    for (const auto &f : all) {
         if (out.size() >= cap) break;
-        if (!make_sched_order(M, r.data(), (int)r.size(), forward, &sc)) continue;
+        Sched sc;
+        if (!make_sched_order(M, f.data(), (int)f.size(), true, &sc)) continue;
         bool seen = false;
         for (const Sched &o : out) seen |= same_sched(o, sc);
         if (!seen) out.push_back(sc);
-    } while (std::next_permutation(r.begin(), r.end()));
+    }
     return out;
 }
 
+// The inverse schedule whose first stage fuses with the last stage of the
+// forward f: f's last radix, then f's other radices in run order.
+Sched fused_inverse(const Sched &f)
+{
+    Sched i = f;
+    i.r[0] = f.r[f.nst - 1];
+    for (int k = 0; k + 1 < f.nst; ++k) i.r[k + 1] = f.r[k];
+    return i;
+}
+
 // Candidate (forward, inverse) schedules of pass `pass`, the current pair
-// first: single-direction passes vary their own direction; the conv pass
-// tries the pairs whose forward last and inverse first stages can be fused,
-// then equal orders.
+// first: single-direction passes vary their own direction over the
+// factorisations of M; the conv pass tries, for each factorisation, the
+// inverse whose first stage fuses with the forward's last, and the same
+// order both ways.
 std::vector<std::pair<Sched, Sched>> sched_candidates(const Plan *p, int pass)
 {
     int axis;
@@ -1072,33 +1106,29 @@ std::vector<std::pair<Sched, Sched>> sched_candidates(const Plan *p, int pass)
     std::vector<std::pair<Sched, Sched>> out;
     out.push_back({p->sched_f[axis], p->sched_i[axis]});
     auto add = [&](const Sched &a, const Sched &b) {
+        if (!axis_pair_ok(p, axis, a, b)) return;
         for (const auto &o : out)
             if (same_sched(o.first, a) && same_sched(o.second, b)) return;
         out.push_back({a, b});
     };
+    const std::vector<Sched> fz = sched_factorisations(M, 6);
     if (f && i) {
-        const std::vector<Sched> fw = sched_orders(M, true, 24), iv = sched_orders(M, false, 24);
-        for (const Sched &a : fw)
-            for (const Sched &b : iv)
-                if (out.size() < 10 && fused_radix(a, b) != 0) add(a, b);
-        for (const Sched &a : fw) {
-            Sched b = a;
-            if (out.size() < 12) add(a, b);
+        for (const Sched &a : fz) {
+            if (a.nst >= 2) add(a, fused_inverse(a));
+            add(a, a);
         }
     } else if (f) {
-        for (const Sched &a : sched_orders(M, true, 8)) add(a, p->sched_i[axis]);
+        for (const Sched &a : fz) add(a, p->sched_i[axis]);
     } else {
-        for (const Sched &b : sched_orders(M, false, 8)) add(p->sched_f[axis], b);
+        for (const Sched &b : fz) add(p->sched_f[axis], b);
     }
     return out;
 }
 
 gsm_status_t apply_axis_pair(Plan *p, int axis, const Sched &a, const Sched &b, cudaStream_t st)
 {
-    gsm_status_t s = GSM_OK;
-    if (!same_sched(p->sched_f[axis], a)) s = set_axis_schedule(p, axis, false, a, st);
-    if (s == GSM_OK && !same_sched(p->sched_i[axis], b)) s = set_axis_schedule(p, axis, true, b, st);
-    return s;
+    if (same_sched(p->sched_f[axis], a) && same_sched(p->sched_i[axis], b)) return GSM_OK;
+    return set_axis_pair(p, axis, a, b, st);
 }
 
 bool cache_lookup(const char *path, const std::string &key, int *nl, int *emax, std::string *fs, std::string *is)
@@ -1158,6 +1188,11 @@ gsm_status_t autotune_t(Plan *p, cudaStream_t st, std::string *report)
     const int np = p->d == 3 ? 5 : 3;
     char buf[320];
     gsm_status_t s = GSM_OK;
+    Sched keep_f[3], keep_i[3];   // put back if the tuning fails part-way
+    for (int a = 0; a < p->d; ++a) {
+        keep_f[a] = p->sched_f[a];
+        keep_i[a] = p->sched_i[a];
+    }
     if (e == cudaSuccess)
         for (int pass = 0; pass < np; ++pass) launch_pass_t<Pol>(p, pass, rho, u, st);
     for (int pass = 0; pass < np && e == cudaSuccess && s == GSM_OK; ++pass) {
@@ -1242,6 +1277,11 @@ gsm_status_t autotune_t(Plan *p, cudaStream_t st, std::string *report)
     }
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
+    if (s != GSM_OK || e != cudaSuccess) {
+        const std::string msg = gsm_last_error();
+        for (int a = 0; a < p->d; ++a) apply_axis_pair(p, a, keep_f[a], keep_i[a], st);
+        set_error(msg);
+    }
     if (s != GSM_OK) return s;
     GSM_CUDA_TRY(e);
     GSM_CUDA_TRY(cudaGetLastError());
@@ -1402,18 +1442,46 @@ bool make_sched_order(int M, const int *radices, int count, bool forward, Sched 
     return true;
 }
 
-gsm_status_t set_axis_schedule(Plan *p, int axis, bool inverse, const Sched &sc, cudaStream_t st)
+// Whether (forward f, inverse i) can run on axis `axis`: the forward and,
+// except on the conv axis with a fused middle stage, the inverse in the order
+// fft_line runs (8, 4, 2, 5, 3); on the conv axis the inverse may instead
+// start with the forward's last radix, that stage being fused.
+bool axis_pair_ok(const Plan *p, int axis, const Sched &f, const Sched &i)
 {
-    if (axis < 0 || axis >= p->d || sc.M != p->M[axis]) {
+    if (!sched_sorted_from(f, 0)) return false;
+    if (sched_sorted_from(i, 0)) return true;
+    return axis == p->d - 1 && fused_radix(f, i) != 0 && sched_sorted_from(i, 1);
+}
+
+gsm_status_t set_axis_pair(Plan *p, int axis, const Sched &f, const Sched &i, cudaStream_t st)
+{
+    if (axis < 0 || axis >= p->d || f.M != p->M[axis] || i.M != p->M[axis]) {
         set_error("schedule does not fit the axis");
         return GSM_ERR_INVALID_ARG;
     }
-    Sched &slot = inverse ? p->sched_i[axis] : p->sched_f[axis];
-    const Sched old = slot;
-    slot = sc;
+    if (!axis_pair_ok(p, axis, f, i)) {
+        set_error("radices must run in the order 8, 4, 2, 5, 3; only the inverse of the conv axis may start "
+                  "with the forward's last radix (fused with the multiplication)");
+        return GSM_ERR_INVALID_ARG;
+    }
+    const Sched old_f = p->sched_f[axis], old_i = p->sched_i[axis];
+    p->sched_f[axis] = f;
+    p->sched_i[axis] = i;
     gsm_status_t s = make_twiddles(p, axis, st);
-    if (s != GSM_OK) slot = old;
+    if (s != GSM_OK) {
+        p->sched_f[axis] = old_f;
+        p->sched_i[axis] = old_i;
+    }
     return s;
+}
+
+gsm_status_t set_axis_schedule(Plan *p, int axis, bool inverse, const Sched &sc, cudaStream_t st)
+{
+    if (axis < 0 || axis >= p->d) {
+        set_error("axis out of range");
+        return GSM_ERR_INVALID_ARG;
+    }
+    return set_axis_pair(p, axis, inverse ? p->sched_f[axis] : sc, inverse ? sc : p->sched_i[axis], st);
 }
 
 gsm_status_t make_pass_multiplier(Plan *p, cudaStream_t st)

@@ -340,15 +340,31 @@ def test_hartree_energy_and_gradient(gsm, kernel):
     assert np.max(np.abs(g - g_o)) < 1e-12 * np.max(np.abs(g_o))
 
 
-def _orders(radices, forward):
-    """Distinct orders of a multiset of radices; forward transforms start with
-    an even radix (their first stage is pruned)."""
-    import itertools
+RADIX_ORDER = (8, 4, 2, 5, 3)     # the order the FFT engine runs stages in
+
+
+def _factorisations(M, max_stages):
+    """Factorisations of M into the radices 8, 4, 2, 5, 3, each in engine order."""
     out = []
-    for perm in itertools.permutations(radices):
-        if perm not in out and (not forward or perm[0] % 2 == 0):
-            out.append(perm)
+
+    def rec(m, k0, cur):
+        if m == 1:
+            out.append(tuple(cur))
+            return
+        if len(cur) >= max_stages:
+            return
+        for k in range(k0, 5):
+            r = RADIX_ORDER[k]
+            if m % r == 0:
+                rec(m // r, k, cur + [r])
+
+    rec(M, 0, [])
     return out
+
+
+def _fused_inverse(f):
+    """The inverse schedule whose first stage fuses with the forward's last."""
+    return (f[-1],) + tuple(f[:-1])
 
 
 SCHED_CASES = [
@@ -361,11 +377,13 @@ SCHED_CASES = [
 @pytest.mark.parametrize("precision", ["fp64", "fp32x2", "fp32"])
 @pytest.mark.parametrize("kernel,n,L", SCHED_CASES, ids=[f"{c[0]}-{'x'.join(map(str, c[1]))}" for c in SCHED_CASES])
 def test_radix_schedules_against_oracle(gsm, kernel, n, L, precision):
-    """Every order of each axis's radices, forward and inverse (conv axis: the
-    pairs whose forward last and inverse first stages share a radix run fused
-    with the multiplication), against the oracle: stages with odd strides
-    (radix 8 or 4 after 5 or 3, in FMA form in FP64; radix 2 after an odd
-    radix, in plain form), pruned first stages of radix 2, 4 and 8."""
+    """Radix schedules against the oracle: on each axis every factorisation of
+    M into radices 8, 4, 2, 5, 3 with at most one stage more than the default,
+    forward and inverse; on the conv axis (the last) each factorisation with
+    the inverse whose first stage fuses with the forward's last (radix 8, 4, 2
+    in FMA form in FP64, 5 and 3 in plain form) and with itself.  This covers
+    stages at odd strides (FMA-form radix 8 and 4 after a fused 5 or 3), pruned
+    first stages of radix 2, 4 and 8 and cropped last stages of every radix."""
     torch = _torch()
     rho = np.random.default_rng(81).standard_normal(tuple(reversed(n)))
     uo, _ = oracle.apply(kernel, rho, L, taylor_mode=1)
@@ -376,19 +394,40 @@ def test_radix_schedules_against_oracle(gsm, kernel, n, L, precision):
     d = len(n)
     runs = 0
     for axis in range(d):
-        base_f, base_i = info["radix_fwd"][axis], info["radix_inv"][axis]
-        fw = _orders(base_f, True)[:6]
-        iv = _orders(base_i, False)[:6]
-        for f in fw:
+        M = info["M"][axis]
+        base = tuple(info["radix_fwd"][axis])
+        facts = _factorisations(M, len(base) + 1)
+        assert base in facts
+        if axis == d - 1:
+            pairs = [(f, g) for f in facts for g in ((_fused_inverse(f), f) if len(f) > 1 else (f,))]
+        else:
+            pairs = [(f, g) for f in facts[:4] for g in facts[:4]]
+        for f, g in pairs:
+            plan.set_schedule(axis, base, inverse=True)      # an engine-order inverse first
             plan.set_schedule(axis, f)
-            for i in iv:
-                plan.set_schedule(axis, i, inverse=True)
-                u = plan.apply(r).double().cpu().numpy()
-                assert_rel(u, uo, tol(precision, plan), f"axis {axis} fwd {f} inv {i}")
-                runs += 1
-        plan.set_schedule(axis, base_f)
-        plan.set_schedule(axis, base_i, inverse=True)
-    assert runs >= 10
+            plan.set_schedule(axis, g, inverse=True)
+            got = plan.info()
+            assert tuple(got["radix_fwd"][axis]) == f and tuple(got["radix_inv"][axis]) == g
+            u = plan.apply(r).double().cpu().numpy()
+            assert_rel(u, uo, tol(precision, plan), f"axis {axis} fwd {f} inv {g}")
+            runs += 1
+        plan.set_schedule(axis, base, inverse=True)
+        plan.set_schedule(axis, base)
+    assert runs >= 8
+
+
+def test_schedule_rules_are_enforced(gsm):
+    """Schedules the engine cannot run are refused: a forward not in engine
+    order, an odd first radix, a wrong product, an inverse that starts out of
+    order on an axis other than the conv axis."""
+    plan = gsm.Plan("coulomb3d", 3.0, (24, 20, 16))        # M = 48, 40, 32
+    for axis, rad, inv in ((2, (4, 8), False), (1, (5, 8), False), (0, (8, 3, 2), False), (2, (8, 8), False),
+                           (0, (3, 8, 2), True), (1, (7, 6), True)):
+        with pytest.raises(gsm.GSMError):
+            plan.set_schedule(axis, rad, inverse=inv)
+    plan.set_schedule(2, (4, 8), inverse=True)             # conv axis: fuses with forward 8 4
+    with pytest.raises(gsm.GSMError):
+        plan.set_schedule(2, (8, 2, 2))                    # would leave the inverse unfused and out of order
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32x2", "fp32"])
