@@ -114,14 +114,30 @@ def test_apply_host_hartree_autotune_out_of_memory_leaks_nothing():
     lib.gsm_debug_fail_alloc(-1)
     e1, _, _ = plan.hartree(psi)
 
-    def tune():
-        st = lib.gsm_plan_autotune(plan.handle, None, None, 0)
-        return st, (lambda: None)
-
-    _sweep(tune)
-    u = plan.apply(torch.tensor(rho, device="cuda")).cpu().numpy()
-    assert np.array_equal(u, ref)
     plan.destroy()
+
+    # the tuner: a failure part-way puts the plan's schedules back (same bits
+    # as before); a success may change the plan's tables, so leaks are checked
+    # against the state before the plan was made
+    base = _stats()
+    for k in range(64):
+        p2 = gsm.Plan("coulomb3d", 3.0, (16, 12, 20))
+        info0 = p2.info()
+        lib.gsm_debug_fail_alloc(k)
+        st = lib.gsm_plan_autotune(p2.handle, None, None, 0)
+        lib.gsm_debug_fail_alloc(-1)
+        if st == 0:
+            p2.destroy()
+            assert _stats() == base
+            break
+        assert st == 3, (k, st)
+        info1 = p2.info()
+        assert info1["radix_fwd"] == info0["radix_fwd"] and info1["radix_inv"] == info0["radix_inv"]
+        assert np.array_equal(p2.apply(torch.tensor(rho, device="cuda")).cpu().numpy(), ref)
+        p2.destroy()
+        assert _stats() == base, (k, base, _stats())
+    else:
+        raise AssertionError("the tuner still failed after 64 allocations")
 
 
 def test_destroyed_handles_are_rejected():
