@@ -18,6 +18,8 @@
 //     DFT32 over k1, only the outputs b < 16 are formed: the crop).
 // The 32- and 16-point DFTs are two-level (4 x 8 and 4 x 4) on the butterflies
 // of gsm_fft.cuh with compile-time twiddles.
+#include <algorithm>
+
 #include "gsm_internal.h"
 
 namespace gsm {
@@ -159,6 +161,7 @@ constexpr int kRrLinesPerCta = 16;           // 16 lines x 16 threads = 256 thre
 constexpr int kRrRow = 17;                   // row pitch of the transpose buffer (bank spread)
 constexpr int kRrLineElems = 32 * kRrRow;    // one line's transpose buffer
 constexpr size_t kRrSmem = sizeof(float2) * kRrLinesPerCta * kRrLineElems;
+constexpr size_t kRrConvSmem = kRrSmem + sizeof(float2) * kRrLinesPerCta * 256;   // + staging buffer
 
 // The 512-point transforms of one line by its 16 threads, in pieces (S is the
 // line's transpose buffer; each thread reads and writes only its own rows
@@ -215,54 +218,91 @@ __device__ __forceinline__ void inv512_cols(cx<float> *v, const float2 *S, int t
     dft32<false, false, true>(v);
 }
 
-// Conv pass: one line of padded length 512 (n = 256 stored values) per 16 threads.
+// 16-byte asynchronous copy global -> shared (cp.async, completion by wait_group).
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
+{
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+// The stored lines of tile `tile` (kRrLinesPerCta lines of 256 values, one
+// contiguous block of W) into the staging buffer, 16 bytes per copy.
+__device__ __forceinline__ void conv_stage_tile(float2 *stage, const float2 *W, int tile, int nlines)
+{
+    const int line0 = tile * kRrLinesPerCta;
+    const int lines = min(kRrLinesPerCta, nlines - line0);
+    const float4 *src = reinterpret_cast<const float4 *>(W + (size_t)line0 * 256);
+    float4 *dst = reinterpret_cast<float4 *>(stage);
+    for (int i = threadIdx.x; i < lines * 128; i += blockDim.x) cp_async16(dst + i, src + i);
+    cp_async_commit();
+}
+
+// Conv pass: one line of padded length 512 (n = 256 stored values) per 16
+// threads, kRrLinesPerCta lines per tile.  Each CTA takes tiles blockIdx.x,
+// blockIdx.x + gridDim.x, ...; while it transforms one tile, the next tile's
+// lines (32 KB, contiguous) are copied into a staging buffer with cp.async, so
+// the loads of HBM overlap the arithmetic.
 // Multiplier of frequency k: mrow[k] (full) or mrow[min(k, 512 - k)].
 __global__ void __launch_bounds__(16 * kRrLinesPerCta, 2)
     k_conv_rr512(float2 *__restrict__ W, const float *__restrict__ mult, int nlines, int is3d, int My, int ny1,
                  int full, const float2 *__restrict__ tw)
 {
-    extern __shared__ float2 sbuf[];   // kRrLinesPerCta * kRrLineElems (dynamic: above 48 KB)
+    extern __shared__ float2 sbuf[];   // transpose buffers, then the staging buffer
     const int t = threadIdx.x & 15;
     const int l = threadIdx.x >> 4;
-    const int line = blockIdx.x * kRrLinesPerCta + l;
-    const bool active = line < nlines;      // a whole half-warp, both take part in the syncs
     float2 *S = sbuf + l * kRrLineElems;
-    float2 *w = W + (size_t)(active ? line : 0) * 256;
-    const int ln = active ? line : 0;       // inactive lines read nothing past the tables
-    const float *mrow;
-    if (full) {
-        mrow = mult + (size_t)ln * 512;
-    } else if (is3d) {
-        const int kx = ln / My, ky = ln - kx * My;
-        mrow = mult + ((size_t)kx * ny1 + min(ky, My - ky)) * 257;
-    } else {
-        mrow = mult + (size_t)ln * 257;
-    }
-    cx<float> v[32];
-#pragma unroll
-    for (int m = 0; m < 16; ++m) {
-        const float2 x = active ? w[t + 16 * m] : make_float2(0.f, 0.f);
-        v[m] = {x.x, x.y};
-    }
-    fwd512_cols(v, S, t, tw);
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-        const int k1 = t + 16 * h;
-        cx<float> *r = v + 16 * h;
-        fwd512_row(r, S, k1);
-#pragma unroll
-        for (int k2 = 0; k2 < 16; ++k2) {
-            const int k = k1 + 32 * k2;
-            const float m = active ? mrow[full ? k : min(k, 512 - k)] : 0.f;
-            r[k2] = {r[k2].re * m, r[k2].im * m};
+    float2 *stage = sbuf + kRrLinesPerCta * kRrLineElems;
+    const int ntiles = (nlines + kRrLinesPerCta - 1) / kRrLinesPerCta;
+    int tile = blockIdx.x;
+    if (tile < ntiles) conv_stage_tile(stage, W, tile, nlines);
+    for (; tile < ntiles; tile += gridDim.x) {
+        const int line = tile * kRrLinesPerCta + l;
+        const bool active = line < nlines;      // a whole half-warp, both take part in the syncs
+        const int ln = active ? line : 0;       // inactive lines read nothing past the tables
+        const float *mrow;
+        if (full) {
+            mrow = mult + (size_t)ln * 512;
+        } else if (is3d) {
+            const int kx = ln / My, ky = ln - kx * My;
+            mrow = mult + ((size_t)kx * ny1 + min(ky, My - ky)) * 257;
+        } else {
+            mrow = mult + (size_t)ln * 257;
         }
-        inv512_row(r, S, k1, tw);
-    }
-    inv512_cols(v, S, t);
-    if (active) {
+        cp_async_wait_all();
+        __syncthreads();                        // the tile's lines are in the staging buffer
+        cx<float> v[32];
 #pragma unroll
-        for (int b = 0; b < 16; ++b) w[t + 16 * b] = make_float2(v[b].re, v[b].im);
+        for (int m = 0; m < 16; ++m) {
+            const float2 x = active ? stage[l * 256 + t + 16 * m] : make_float2(0.f, 0.f);
+            v[m] = {x.x, x.y};
+        }
+        __syncthreads();                        // staging buffer read: the next tile may land
+        if (tile + (int)gridDim.x < ntiles) conv_stage_tile(stage, W, tile + gridDim.x, nlines);
+        fwd512_cols(v, S, t, tw);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int k1 = t + 16 * h;
+            cx<float> *r = v + 16 * h;
+            fwd512_row(r, S, k1);
+#pragma unroll
+            for (int k2 = 0; k2 < 16; ++k2) {
+                const int k = k1 + 32 * k2;
+                const float m = active ? mrow[full ? k : min(k, 512 - k)] : 0.f;
+                r[k2] = {r[k2].re * m, r[k2].im * m};
+            }
+            inv512_row(r, S, k1, tw);
+        }
+        inv512_cols(v, S, t);
+        if (active) {
+            float2 *w = W + (size_t)line * 256;
+#pragma unroll
+            for (int b = 0; b < 16; ++b) w[t + 16 * b] = make_float2(v[b].re, v[b].im);
+        }
+        __syncwarp();                           // the line's transpose buffer is free for the next tile
     }
+    cp_async_wait_all();
 }
 
 // 3D y-forward pass, ny = 256 (My = 512): W1[z][kx][y] -> W2[kx][ky][z].  CTA
@@ -307,40 +347,75 @@ __global__ void __launch_bounds__(16 * kRrLinesPerCta, 2)
 }
 
 // 3D y-inverse pass, ny = 256: W2[kx][ky][z] -> W1[z][kx][y] (crop to y < 256).
-__global__ void __launch_bounds__(16 * kRrLinesPerCta, 2)
+// Tile (z-block zb, kx): the kRrYiLines z-lines z = kRrYiLines zb + 0.. at kx,
+// whose input is 512 rows ky of kRrYiLines consecutive z (64 bytes each) in
+// W2[kx].  Each CTA takes tiles blockIdx.x, blockIdx.x + gridDim.x, ...; the
+// next tile's rows are copied with cp.async into a staging buffer (pitch 10
+// elements: 16-byte aligned rows, two-way bank conflicts on the transposed
+// read) while the current tile is transformed.  Three CTAs of 4 warps fit an SM.
+constexpr int kRrYiLines = 8;
+constexpr int kRrStagePitch = 10;
+constexpr size_t kRrYiSmem = sizeof(float2) * (kRrYiLines * kRrLineElems + 512 * kRrStagePitch);
+
+__device__ __forceinline__ void yi_stage_tile(float2 *stage, const float2 *W2, int tile, int nzb, int nz)
+{
+    const int kx = tile / nzb, z0 = (tile - kx * nzb) * kRrYiLines;
+    const float2 *in = W2 + (size_t)kx * 512 * nz;
+    const int zv = min(kRrYiLines, nz - z0);
+    if (zv == kRrYiLines && (nz % 2) == 0) {
+        // whole 64-byte rows, 16 bytes (2 values) per copy
+        for (int i = threadIdx.x; i < 512 * (kRrYiLines / 2); i += blockDim.x) {
+            const int ky = i / (kRrYiLines / 2), c = i % (kRrYiLines / 2);
+            cp_async16(stage + ky * kRrStagePitch + 2 * c, in + (size_t)ky * nz + z0 + 2 * c);
+        }
+    } else {
+        // ragged z-block or odd row pitch: plain loads (zeros past nz)
+        for (int i = threadIdx.x; i < 512 * kRrYiLines; i += blockDim.x) {
+            const int ky = i / kRrYiLines, r = i % kRrYiLines, zz = z0 + r;
+            stage[ky * kRrStagePitch + r] = zz < nz ? in[(size_t)ky * nz + zz] : make_float2(0.f, 0.f);
+        }
+    }
+    cp_async_commit();
+}
+
+__global__ void __launch_bounds__(16 * kRrYiLines, 3)
     k_yi_rr512(const float2 *__restrict__ W2, float2 *__restrict__ W1, int nz, int hx, const float2 *__restrict__ tw)
 {
-    extern __shared__ float2 sbuf[];
+    extern __shared__ float2 sbuf[];   // transpose buffers, then the staging buffer
     const int t = threadIdx.x & 15;
     const int l = threadIdx.x >> 4;
-    const int kx = blockIdx.y;
-    const int z0 = blockIdx.x * kRrLinesPerCta;
-    const int z = z0 + l;
-    const float2 *in = W2 + (size_t)kx * 512 * nz;
-#pragma unroll 8
-    for (int i = threadIdx.x; i < 512 * 16; i += blockDim.x) {   // unrolled: loads in flight
-        const int ky = i >> 4, zz = z0 + (i & 15);
-        sbuf[ky * kRrRow + (i & 15)] = zz < nz ? in[(size_t)ky * nz + zz] : make_float2(0.f, 0.f);
-    }
-    __syncthreads();
-    cx<float> v[32];
-#pragma unroll
-    for (int h = 0; h < 2; ++h)
-#pragma unroll
-        for (int k2 = 0; k2 < 16; ++k2) {
-            const float2 x = sbuf[(t + 16 * h + 32 * k2) * kRrRow + l];
-            v[16 * h + k2] = {x.x, x.y};
-        }
-    __syncthreads();                      // the buffer becomes the lines' transpose buffers
     float2 *S = sbuf + l * kRrLineElems;
-    inv512_row(v, S, t, tw);
-    inv512_row(v + 16, S, t + 16, tw);
-    inv512_cols(v, S, t);
-    if (z < nz) {
-        float2 *out = W1 + ((size_t)z * hx + kx) * 256;
+    float2 *stage = sbuf + kRrYiLines * kRrLineElems;
+    const int nzb = (nz + kRrYiLines - 1) / kRrYiLines;
+    const int ntiles = nzb * hx;
+    int tile = blockIdx.x;
+    if (tile < ntiles) yi_stage_tile(stage, W2, tile, nzb, nz);
+    for (; tile < ntiles; tile += gridDim.x) {
+        const int kx = tile / nzb, z0 = (tile - kx * nzb) * kRrYiLines;
+        const int z = z0 + l;
+        cp_async_wait_all();
+        __syncthreads();                  // the tile's rows are in the staging buffer
+        cx<float> v[32];
 #pragma unroll
-        for (int b = 0; b < 16; ++b) out[t + 16 * b] = make_float2(v[b].re, v[b].im);
+        for (int h = 0; h < 2; ++h)
+#pragma unroll
+            for (int k2 = 0; k2 < 16; ++k2) {
+                const float2 x = stage[(t + 16 * h + 32 * k2) * kRrStagePitch + l];
+                v[16 * h + k2] = {x.x, x.y};
+            }
+        __syncthreads();                  // staging buffer read: the next tile may land
+        if (tile + (int)gridDim.x < ntiles) yi_stage_tile(stage, W2, tile + gridDim.x, nzb, nz);
+        inv512_row(v, S, t, tw);
+        inv512_row(v + 16, S, t + 16, tw);
+        inv512_cols(v, S, t);
+        if (z < nz) {
+            float2 *out = W1 + ((size_t)z * hx + kx) * 256;
+#pragma unroll
+            for (int b = 0; b < 16; ++b) out[t + 16 * b] = make_float2(v[b].re, v[b].im);
+        }
+        __syncwarp();                     // the line's transpose buffer is free for the next tile
     }
+    cp_async_wait_all();
 }
 
 // x passes, nx = 256 (Mx = 512): 8 complex lines (16 real rows) per CTA of 128
@@ -475,11 +550,23 @@ gsm_status_t launch_conv_rr512_f32(void *W, const void *mult, int nlines, int is
                                    const void *tw, cudaStream_t st)
 {
     static bool raised[64] = {};
-    GSM_CUDA_TRY(raise_rr(k_conv_rr512, raised));
-    const int blocks = (nlines + kRrLinesPerCta - 1) / kRrLinesPerCta;
-    k_conv_rr512<<<blocks, 16 * kRrLinesPerCta, kRrSmem, st>>>(static_cast<float2 *>(W),
-                                                               static_cast<const float *>(mult), nlines, is3d, My,
-                                                               ny1, full ? 1 : 0, static_cast<const float2 *>(tw));
+    static int resident[64] = {};
+    GSM_CUDA_TRY(raise_rr(k_conv_rr512, raised, kRrConvSmem));
+    int dev = 0;
+    GSM_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return GSM_ERR_INVALID_ARG;
+    if (resident[dev] == 0) {
+        int occ = 0, sms = 0;
+        GSM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_conv_rr512, 16 * kRrLinesPerCta,
+                                                                   kRrConvSmem));
+        GSM_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        resident[dev] = std::max(1, occ) * sms;
+    }
+    const int tiles = (nlines + kRrLinesPerCta - 1) / kRrLinesPerCta;
+    const int blocks = std::max(1, std::min(tiles, resident[dev]));
+    k_conv_rr512<<<blocks, 16 * kRrLinesPerCta, kRrConvSmem, st>>>(static_cast<float2 *>(W),
+                                                                   static_cast<const float *>(mult), nlines, is3d, My,
+                                                                   ny1, full ? 1 : 0, static_cast<const float2 *>(tw));
     return GSM_OK;   // a launch error stays pending for the caller's check
 }
 
@@ -496,10 +583,23 @@ gsm_status_t launch_y_rr512_f32(bool inverse, const void *in, void *out, int nz,
                                                             static_cast<const float2 *>(tw));
     } else {
         static bool raised_i[64] = {};
-        GSM_CUDA_TRY(raise_rr(k_yi_rr512, raised_i));
-        k_yi_rr512<<<g, 16 * kRrLinesPerCta, kRrSmem, st>>>(static_cast<const float2 *>(in),
-                                                            static_cast<float2 *>(out), nz, hx,
-                                                            static_cast<const float2 *>(tw));
+        static int resident[64] = {};
+        GSM_CUDA_TRY(raise_rr(k_yi_rr512, raised_i, kRrYiSmem));
+        int dev = 0;
+        GSM_CUDA_TRY(cudaGetDevice(&dev));
+        if (dev < 0 || dev >= 64) return GSM_ERR_INVALID_ARG;
+        if (resident[dev] == 0) {
+            int occ = 0, sms = 0;
+            GSM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_yi_rr512, 16 * kRrYiLines,
+                                                                       kRrYiSmem));
+            GSM_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+            resident[dev] = std::max(1, occ) * sms;
+        }
+        const int tiles = ((nz + kRrYiLines - 1) / kRrYiLines) * hx;
+        const int blocks = std::max(1, std::min(tiles, resident[dev]));
+        k_yi_rr512<<<blocks, 16 * kRrYiLines, kRrYiSmem, st>>>(static_cast<const float2 *>(in),
+                                                                   static_cast<float2 *>(out), nz, hx,
+                                                                   static_cast<const float2 *>(tw));
     }
     return GSM_OK;   // a launch error stays pending for the caller's check
 }
