@@ -161,7 +161,6 @@ constexpr int kRrLinesPerCta = 16;           // 16 lines x 16 threads = 256 thre
 constexpr int kRrRow = 17;                   // row pitch of the transpose buffer (bank spread)
 constexpr int kRrLineElems = 32 * kRrRow;    // one line's transpose buffer
 constexpr size_t kRrSmem = sizeof(float2) * kRrLinesPerCta * kRrLineElems;
-constexpr size_t kRrConvSmem = kRrSmem + sizeof(float2) * kRrLinesPerCta * 256;   // + staging buffer
 
 // The 512-point transforms of one line by its 16 threads, in pieces (S is the
 // line's transpose buffer; each thread reads and writes only its own rows
@@ -227,82 +226,54 @@ __device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
-// The stored lines of tile `tile` (kRrLinesPerCta lines of 256 values, one
-// contiguous block of W) into the staging buffer, 16 bytes per copy.
-__device__ __forceinline__ void conv_stage_tile(float2 *stage, const float2 *W, int tile, int nlines)
-{
-    const int line0 = tile * kRrLinesPerCta;
-    const int lines = min(kRrLinesPerCta, nlines - line0);
-    const float4 *src = reinterpret_cast<const float4 *>(W + (size_t)line0 * 256);
-    float4 *dst = reinterpret_cast<float4 *>(stage);
-    for (int i = threadIdx.x; i < lines * 128; i += blockDim.x) cp_async16(dst + i, src + i);
-    cp_async_commit();
-}
-
-// Conv pass: one line of padded length 512 (n = 256 stored values) per 16
-// threads, kRrLinesPerCta lines per tile.  Each CTA takes tiles blockIdx.x,
-// blockIdx.x + gridDim.x, ...; while it transforms one tile, the next tile's
-// lines (32 KB, contiguous) are copied into a staging buffer with cp.async, so
-// the loads of HBM overlap the arithmetic.
+// Conv pass: one line of padded length 512 (n = 256 stored values) per 16 threads.
 // Multiplier of frequency k: mrow[k] (full) or mrow[min(k, 512 - k)].
 __global__ void __launch_bounds__(16 * kRrLinesPerCta, 2)
     k_conv_rr512(float2 *__restrict__ W, const float *__restrict__ mult, int nlines, int is3d, int My, int ny1,
                  int full, const float2 *__restrict__ tw)
 {
-    extern __shared__ float2 sbuf[];   // transpose buffers, then the staging buffer
+    extern __shared__ float2 sbuf[];   // kRrLinesPerCta * kRrLineElems (dynamic: above 48 KB)
     const int t = threadIdx.x & 15;
     const int l = threadIdx.x >> 4;
+    const int line = blockIdx.x * kRrLinesPerCta + l;
+    const bool active = line < nlines;      // a whole half-warp, both take part in the syncs
     float2 *S = sbuf + l * kRrLineElems;
-    float2 *stage = sbuf + kRrLinesPerCta * kRrLineElems;
-    const int ntiles = (nlines + kRrLinesPerCta - 1) / kRrLinesPerCta;
-    int tile = blockIdx.x;
-    if (tile < ntiles) conv_stage_tile(stage, W, tile, nlines);
-    for (; tile < ntiles; tile += gridDim.x) {
-        const int line = tile * kRrLinesPerCta + l;
-        const bool active = line < nlines;      // a whole half-warp, both take part in the syncs
-        const int ln = active ? line : 0;       // inactive lines read nothing past the tables
-        const float *mrow;
-        if (full) {
-            mrow = mult + (size_t)ln * 512;
-        } else if (is3d) {
-            const int kx = ln / My, ky = ln - kx * My;
-            mrow = mult + ((size_t)kx * ny1 + min(ky, My - ky)) * 257;
-        } else {
-            mrow = mult + (size_t)ln * 257;
-        }
-        cp_async_wait_all();
-        __syncthreads();                        // the tile's lines are in the staging buffer
-        cx<float> v[32];
-#pragma unroll
-        for (int m = 0; m < 16; ++m) {
-            const float2 x = active ? stage[l * 256 + t + 16 * m] : make_float2(0.f, 0.f);
-            v[m] = {x.x, x.y};
-        }
-        __syncthreads();                        // staging buffer read: the next tile may land
-        if (tile + (int)gridDim.x < ntiles) conv_stage_tile(stage, W, tile + gridDim.x, nlines);
-        fwd512_cols(v, S, t, tw);
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const int k1 = t + 16 * h;
-            cx<float> *r = v + 16 * h;
-            fwd512_row(r, S, k1);
-#pragma unroll
-            for (int k2 = 0; k2 < 16; ++k2) {
-                const int k = k1 + 32 * k2;
-                const float m = active ? mrow[full ? k : min(k, 512 - k)] : 0.f;
-                r[k2] = {r[k2].re * m, r[k2].im * m};
-            }
-            inv512_row(r, S, k1, tw);
-        }
-        inv512_cols(v, S, t);
-        if (active) {
-            float2 *w = W + (size_t)line * 256;
-#pragma unroll
-            for (int b = 0; b < 16; ++b) w[t + 16 * b] = make_float2(v[b].re, v[b].im);
-        }
-        __syncwarp();                           // the line's transpose buffer is free for the next tile
+    float2 *w = W + (size_t)(active ? line : 0) * 256;
+    const int ln = active ? line : 0;       // inactive lines read nothing past the tables
+    const float *mrow;
+    if (full) {
+        mrow = mult + (size_t)ln * 512;
+    } else if (is3d) {
+        const int kx = ln / My, ky = ln - kx * My;
+        mrow = mult + ((size_t)kx * ny1 + min(ky, My - ky)) * 257;
+    } else {
+        mrow = mult + (size_t)ln * 257;
     }
-    cp_async_wait_all();
+    cx<float> v[32];
+#pragma unroll
+    for (int m = 0; m < 16; ++m) {
+        const float2 x = active ? w[t + 16 * m] : make_float2(0.f, 0.f);
+        v[m] = {x.x, x.y};
+    }
+    fwd512_cols(v, S, t, tw);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int k1 = t + 16 * h;
+        cx<float> *r = v + 16 * h;
+        fwd512_row(r, S, k1);
+#pragma unroll
+        for (int k2 = 0; k2 < 16; ++k2) {
+            const int k = k1 + 32 * k2;
+            const float m = active ? mrow[full ? k : min(k, 512 - k)] : 0.f;
+            r[k2] = {r[k2].re * m, r[k2].im * m};
+        }
+        inv512_row(r, S, k1, tw);
+    }
+    inv512_cols(v, S, t);
+    if (active) {
+#pragma unroll
+        for (int b = 0; b < 16; ++b) w[t + 16 * b] = make_float2(v[b].re, v[b].im);
+    }
 }
 
 // 3D y-forward pass, ny = 256 (My = 512): W1[z][kx][y] -> W2[kx][ky][z].  CTA
@@ -473,60 +444,91 @@ __global__ void __launch_bounds__(16 * kRrXLines, 3)
 
 // x inverse: Z[k] = A + i B, Z[512 - k] = conj A + i conj B (A, B real at k = 0
 // and 256), inverse transform, real part to row y and imaginary part to row y + 1.
+// Tile (y-block yb, z): rows y = 16 yb .. 16 yb + 15 of slab z, whose input is
+// 257 rows k of 16 consecutive y (128 bytes each) in W1[z].  Each CTA takes
+// tiles blockIdx.x, blockIdx.x + gridDim.x, ...; the next tile's rows are
+// copied with cp.async into the staging buffer T (pitch 18 elements: 16-byte
+// aligned rows) while the current tile is transformed.
+constexpr int kRrXiPitch = 18;
+constexpr size_t kRrXiSmem = sizeof(float2) * (kRrXLines * kRrLineElems + 257 * kRrXiPitch);
+
+__device__ __forceinline__ void xi_stage_tile(float2 *T, const float2 *W1, int tile, int nyb, int ny)
+{
+    const int z = tile / nyb, y0 = (tile - z * nyb) * 2 * kRrXLines;
+    const float2 *in = W1 + (size_t)z * 257 * ny;
+    if (y0 + 2 * kRrXLines <= ny && (ny % 2) == 0) {
+        // whole 128-byte rows, 16 bytes (2 values) per copy
+        for (int i = threadIdx.x; i < 257 * kRrXLines; i += blockDim.x) {
+            const int k = i / kRrXLines, c = i % kRrXLines;
+            cp_async16(T + k * kRrXiPitch + 2 * c, in + (size_t)k * ny + y0 + 2 * c);
+        }
+    } else {
+        // ragged y-block or odd row pitch: plain loads (zeros past ny)
+        for (int i = threadIdx.x; i < 257 * 16; i += blockDim.x) {
+            const int k = i >> 4, r = i & 15;
+            T[k * kRrXiPitch + r] = y0 + r < ny ? in[(size_t)k * ny + y0 + r] : make_float2(0.f, 0.f);
+        }
+    }
+    cp_async_commit();
+}
+
 __global__ void __launch_bounds__(16 * kRrXLines, 3)
-    k_xi_rr512(const float2 *__restrict__ W1, float *__restrict__ u, int ny, const float2 *__restrict__ tw)
+    k_xi_rr512(const float2 *__restrict__ W1, float *__restrict__ u, int ny, int nz, const float2 *__restrict__ tw)
 {
     extern __shared__ float2 sbuf[];
     const int t = threadIdx.x & 15;
     const int l = threadIdx.x >> 4;
-    const int z = blockIdx.y;
-    const int y0 = blockIdx.x * 2 * kRrXLines;
-    const int ya = y0 + 2 * l;
     float2 *S = sbuf + l * kRrLineElems;
     float2 *T = sbuf + kRrXLines * kRrLineElems;
-    const float2 *in = W1 + (size_t)z * 257 * ny;
-#pragma unroll 8
-    for (int i = threadIdx.x; i < 257 * 16; i += blockDim.x) {   // unrolled: loads in flight
-        const int k = i >> 4, r = i & 15;
-        T[k * kRrXPitch + r] = y0 + r < ny ? in[(size_t)k * ny + y0 + r] : make_float2(0.f, 0.f);
-    }
-    __syncthreads();
-    for (int k = t; k <= 256; k += 16) {
-        const float2 a = T[k * kRrXPitch + 2 * l], b = T[k * kRrXPitch + 2 * l + 1];
-        cx<float> A = {a.x, a.y}, B = {b.x, b.y};
-        if (k == 0 || k == 256) {
-            A.im = 0.f;
-            B.im = 0.f;
+    const int nyb = (ny + 2 * kRrXLines - 1) / (2 * kRrXLines);
+    const int ntiles = nyb * nz;
+    int tile = blockIdx.x;
+    if (tile < ntiles) xi_stage_tile(T, W1, tile, nyb, ny);
+    for (; tile < ntiles; tile += gridDim.x) {
+        const int z = tile / nyb, y0 = (tile - z * nyb) * 2 * kRrXLines;
+        const int ya = y0 + 2 * l;
+        cp_async_wait_all();
+        __syncthreads();                       // the tile's rows are in T
+        for (int k = t; k <= 256; k += 16) {
+            const float2 a = T[k * kRrXiPitch + 2 * l], b = T[k * kRrXiPitch + 2 * l + 1];
+            cx<float> A = {a.x, a.y}, B = {b.x, b.y};
+            if (k == 0 || k == 256) {
+                A.im = 0.f;
+                B.im = 0.f;
+            }
+            const cx<float> zk = cadd(A, cmul_posi(B));
+            S[k] = make_float2(zk.re, zk.im);
+            if (k > 0 && k < 256) {
+                const cx<float> zm = cadd(cconj(A), cmul_posi(cconj(B)));
+                S[512 - k] = make_float2(zm.re, zm.im);
+            }
         }
-        const cx<float> zk = cadd(A, cmul_posi(B));
-        S[k] = make_float2(zk.re, zk.im);
-        if (k > 0 && k < 256) {
-            const cx<float> zm = cadd(cconj(A), cmul_posi(cconj(B)));
-            S[512 - k] = make_float2(zm.re, zm.im);
+        __syncthreads();                       // T read: the next tile may land
+        if (tile + (int)gridDim.x < ntiles) xi_stage_tile(T, W1, tile + gridDim.x, nyb, ny);
+        cx<float> v[32];
+#pragma unroll
+        for (int h = 0; h < 2; ++h)
+#pragma unroll
+            for (int k2 = 0; k2 < 16; ++k2) {
+                const float2 x = S[t + 16 * h + 32 * k2];
+                v[16 * h + k2] = {x.x, x.y};
+            }
+        __syncwarp();                          // natural order read: the buffer takes the rows
+        inv512_row(v, S, t, tw);
+        inv512_row(v + 16, S, t + 16, tw);
+        inv512_cols(v, S, t);
+        float *slab = u + (size_t)z * ny * 256;
+        if (ya < ny) {
+#pragma unroll
+            for (int b = 0; b < 16; ++b) slab[(size_t)ya * 256 + t + 16 * b] = v[b].re;
         }
-    }
-    __syncwarp();
-    cx<float> v[32];
+        if (ya + 1 < ny) {
 #pragma unroll
-    for (int h = 0; h < 2; ++h)
-#pragma unroll
-        for (int k2 = 0; k2 < 16; ++k2) {
-            const float2 x = S[t + 16 * h + 32 * k2];
-            v[16 * h + k2] = {x.x, x.y};
+            for (int b = 0; b < 16; ++b) slab[(size_t)(ya + 1) * 256 + t + 16 * b] = v[b].im;
         }
-    __syncwarp();                          // natural order read: the buffer takes the rows
-    inv512_row(v, S, t, tw);
-    inv512_row(v + 16, S, t + 16, tw);
-    inv512_cols(v, S, t);
-    float *slab = u + (size_t)z * ny * 256;
-    if (ya < ny) {
-#pragma unroll
-        for (int b = 0; b < 16; ++b) slab[(size_t)ya * 256 + t + 16 * b] = v[b].re;
+        __syncwarp();                          // the line's buffer is free for the next tile
     }
-    if (ya + 1 < ny) {
-#pragma unroll
-        for (int b = 0; b < 16; ++b) slab[(size_t)(ya + 1) * 256 + t + 16 * b] = v[b].im;
-    }
+    cp_async_wait_all();
 }
 
 // Raise the kernel's dynamic shared-memory limit to kRrSmem once per device;
@@ -550,23 +552,11 @@ gsm_status_t launch_conv_rr512_f32(void *W, const void *mult, int nlines, int is
                                    const void *tw, cudaStream_t st)
 {
     static bool raised[64] = {};
-    static int resident[64] = {};
-    GSM_CUDA_TRY(raise_rr(k_conv_rr512, raised, kRrConvSmem));
-    int dev = 0;
-    GSM_CUDA_TRY(cudaGetDevice(&dev));
-    if (dev < 0 || dev >= 64) return GSM_ERR_INVALID_ARG;
-    if (resident[dev] == 0) {
-        int occ = 0, sms = 0;
-        GSM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_conv_rr512, 16 * kRrLinesPerCta,
-                                                                   kRrConvSmem));
-        GSM_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-        resident[dev] = std::max(1, occ) * sms;
-    }
-    const int tiles = (nlines + kRrLinesPerCta - 1) / kRrLinesPerCta;
-    const int blocks = std::max(1, std::min(tiles, resident[dev]));
-    k_conv_rr512<<<blocks, 16 * kRrLinesPerCta, kRrConvSmem, st>>>(static_cast<float2 *>(W),
-                                                                   static_cast<const float *>(mult), nlines, is3d, My,
-                                                                   ny1, full ? 1 : 0, static_cast<const float2 *>(tw));
+    GSM_CUDA_TRY(raise_rr(k_conv_rr512, raised));
+    const int blocks = (nlines + kRrLinesPerCta - 1) / kRrLinesPerCta;
+    k_conv_rr512<<<blocks, 16 * kRrLinesPerCta, kRrSmem, st>>>(static_cast<float2 *>(W),
+                                                               static_cast<const float *>(mult), nlines, is3d, My,
+                                                               ny1, full ? 1 : 0, static_cast<const float2 *>(tw));
     return GSM_OK;   // a launch error stays pending for the caller's check
 }
 
@@ -617,9 +607,22 @@ gsm_status_t launch_x_rr512_f32(bool inverse, const void *in, void *out, int ny,
                                                         ny, static_cast<const float2 *>(tw));
     } else {
         static bool raised_i[64] = {};
-        GSM_CUDA_TRY(raise_rr(k_xi_rr512, raised_i, kRrXSmem));
-        k_xi_rr512<<<g, 16 * kRrXLines, kRrXSmem, st>>>(static_cast<const float2 *>(in), static_cast<float *>(out),
-                                                        ny, static_cast<const float2 *>(tw));
+        static int resident[64] = {};
+        GSM_CUDA_TRY(raise_rr(k_xi_rr512, raised_i, kRrXiSmem));
+        int dev = 0;
+        GSM_CUDA_TRY(cudaGetDevice(&dev));
+        if (dev < 0 || dev >= 64) return GSM_ERR_INVALID_ARG;
+        if (resident[dev] == 0) {
+            int occ = 0, sms = 0;
+            GSM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_xi_rr512, 16 * kRrXLines, kRrXiSmem));
+            GSM_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+            resident[dev] = std::max(1, occ) * sms;
+        }
+        const int tiles = g.x * g.y;
+        const int blocks = std::max(1, std::min(tiles, resident[dev]));
+        k_xi_rr512<<<blocks, 16 * kRrXLines, kRrXiSmem, st>>>(static_cast<const float2 *>(in),
+                                                              static_cast<float *>(out), ny, nz,
+                                                              static_cast<const float2 *>(tw));
     }
     return GSM_OK;   // a launch error stays pending for the caller's check
 }
