@@ -68,6 +68,12 @@ struct Plan {
 
     Sched sched_f[3], sched_i[3];   // radix schedules of the forward and inverse transforms per axis
     PassCfg cfg_xf, cfg_yf, cfg_conv, cfg_yi, cfg_xi;
+    // 2D conv of padded length >= kSplitMinM: each line as two transforms of
+    // half the length on a cluster of two CTAs (k_conv_split)
+    bool split_conv = false;
+    Sched sched_hf, sched_hi;
+    void *d_twh = nullptr, *d_twhi = nullptr;   // tables of the half length
+    PassCfg cfg_split;
 };
 
 // thread-local last error
@@ -164,6 +170,9 @@ gsm_status_t make_twiddles(Plan *p, int axis, cudaStream_t st);
 gsm_status_t make_pass_multiplier(Plan *p, cudaStream_t st);
 // default radix schedule of length M: radices 8, 4, 2, 5, 3 in that order
 bool make_sched(int M, Sched *s);
+constexpr int kSplitMinM = 4096;
+// the half-length schedules and tables of a split 2D conv (gsm_passes.cu)
+gsm_status_t make_split_tables(Plan *p, cudaStream_t st);
 // schedule with the given radices in the given order (each 8, 4, 2, 5 or 3,
 // product M); forward: the first radix must be even (the pruned first stage
 // of a zero-padded transform)

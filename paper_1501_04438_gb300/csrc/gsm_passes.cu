@@ -27,6 +27,7 @@
 #include <vector>
 #include <type_traits>
 
+#include <cooperative_groups.h>
 #include <cuda.h>
 
 #include "gsm_internal.h"
@@ -325,6 +326,88 @@ __global__ void __launch_bounds__(kMaxThreads) k_xi(const S_t<Pol> *__restrict__
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     body_xi<Pol, EMAX>(W1, u, nx, ny, hx, sc, nl, gthr, tw, blockIdx.x, blockIdx.y, smem_raw);
+}
+
+// ------------------------------------------------------------------ pass conv, long 2D lines
+// A conv line of padded length M = 2 Mh holds Mh values x[0..Mh) and zeros.
+// Its even and odd frequencies are then two transforms of length Mh:
+//   X[2k] = FFT_Mh(x)[k],   X[2k + 1] = FFT_Mh(x w_M^n)[k],
+// and the cropped inverse (outputs n < Mh) is
+//   u[n] = IFFT_Mh(E)[n] + w_M^(-n) IFFT_Mh(O)[n],
+// E, O the multiplied even and odd frequencies.  A cluster of two CTAs takes
+// one line: rank 0 the even half, rank 1 the odd half (a line of Mh values
+// each, half the shared memory of the whole line), then each adds its half of
+// the outputs to the other CTA's through distributed shared memory.  Two CTAs
+// per SM work on different lines, so one line's barrier-separated phases
+// overlap another's (one CTA per SM held a whole line of 8192 and left the
+// FP64 pipe idle during its shared-memory phases).  Schedules, tables:
+// length Mh (sched_hf, sched_hi, twh, twhi); twM: the M twiddles w_M^m.
+template <class Pol, int EMAX>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kMaxThreads)
+    k_conv_split(S_t<Pol> *__restrict__ W, const typename Pol::mult_t *__restrict__ mult, int nlines, int ny1,
+                 Sched sc, Sched sci, const typename Pol::tw_t *__restrict__ tw,
+                 const typename Pol::tw_t *__restrict__ twi, const typename Pol::tw_t *__restrict__ twM, int full)
+{
+    using R = typename Pol::real;
+    namespace cg = cooperative_groups;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    cg::cluster_group cl = cg::this_cluster();
+    const int rank = (int)cl.block_rank();
+    const int line = blockIdx.x >> 1;
+    const int Mh = sc.M, M = 2 * Mh;
+    const Group g = make_group(blockDim.x, 1);
+    S_t<Pol> *s = reinterpret_cast<S_t<Pol> *>(smem_raw);
+    S_t<Pol> *w = W + (size_t)line * Mh;
+    const bool active = line < nlines;   // every CTA of a cluster reaches both cluster barriers
+    if (active) {
+        for (int i = g.t; i < Mh; i += g.T) {
+            cx<R> v = Pol::ld(w[i]);
+            if (rank) v = cmul(v, Pol::tw(twM[i]));   // x w_M^n
+            s[pidx<Pol>(i)] = Pol::st(v);
+        }
+        group_sync(g);
+        const typename Pol::mult_t *mrow = mult + (size_t)line * (full ? M : ny1);
+        // output k' of this half is frequency k = 2 k' + rank
+        auto mult_of = [&](int kk) -> R {
+            const int k = 2 * kk + rank;
+            return Pol::mult(mrow[full ? k : min(k, M - k)]);
+        };
+        const double *gt = g8_table<Pol>(tw, Mh), *gti = g8_table<Pol>(twi, Mh);
+        const int fr = fused_radix(sc, sci);
+        if (fr != 0) {
+            fft_line<Pol, true, EMAX>(s, sc, tw, g, gt, 0, sc.nst - 1);
+            if (fr == 8) fft_fused_mid<Pol, 8, (EMAX + 7) / 8>(s, sc, tw, g, gt, mult_of);
+            else if (fr == 4) fft_fused_mid<Pol, 4, (EMAX + 3) / 4>(s, sc, tw, g, gt, mult_of);
+            else if (fr == 2) fft_fused_mid<Pol, 2, (EMAX + 1) / 2>(s, sc, tw, g, gt, mult_of);
+            else if (fr == 5) fft_fused_mid<Pol, 5, (EMAX + 4) / 5>(s, sc, tw, g, gt, mult_of);
+            else fft_fused_mid<Pol, 3, (EMAX + 2) / 3>(s, sc, tw, g, gt, mult_of);
+            fft_line<Pol, false, EMAX>(s, sci, twi, g, gti, 1);
+        } else {
+            fft_line<Pol, true, EMAX>(s, sc, tw, g, gt);
+            for (int k = g.t; k < Mh; k += g.T) {
+                const int p = pidx<Pol>(k);
+                s[p] = Pol::st(cscale(Pol::ld(s[p]), mult_of(k)));
+            }
+            group_sync(g);
+            fft_line<Pol, false, EMAX>(s, sci, twi, g, gti);
+        }
+        if (rank) {
+            for (int i = g.t; i < Mh; i += g.T) {
+                const int p = pidx<Pol>(i);
+                s[p] = Pol::st(cmulc(Pol::ld(s[p]), Pol::tw(twM[i])));   // w_M^(-n)
+            }
+        }
+    }
+    cl.sync();   // both halves transformed
+    if (active) {
+        const S_t<Pol> *peer = cl.map_shared_rank(s, rank ^ 1);
+        const int h = Mh / 2, n0 = rank * h;
+        for (int i = g.t; i < h; i += g.T) {
+            const int n = n0 + i, p = pidx<Pol>(n);
+            w[n] = Pol::st(cadd(Pol::ld(s[p]), Pol::ld(peer[p])));
+        }
+    }
+    cl.sync();   // the peer has read this CTA's half: its shared memory may go
 }
 
 // ------------------------------------------------------------------ FFT test hook
@@ -787,6 +870,16 @@ gsm_status_t configure_t(Plan *p)
         p->cfg_conv = choose_cfg<Pol>(p->M[2], std::max(1, 4096 / p->M[2]));
     } else {
         p->cfg_conv = choose_cfg<Pol>(p->M[1], std::max(1, 4096 / p->M[1]));
+        // long lines: two half-length transforms per line on a cluster of two CTAs
+        // (options.debug bit 1 keeps one CTA per line, for comparisons)
+        p->split_conv = p->M[1] >= kSplitMinM && (p->opt.debug & 2) == 0;
+        if (p->split_conv) {
+            if (!make_cfg<Pol>(p->M[1] / 2, 1, 16, &p->cfg_split)) {
+                set_error("no launch shape for the split conv pass");
+                return GSM_ERR_UNSUPPORTED_SIZE;
+            }
+            GSM_CUDA_TRY(raise_smem(k_conv_split<Pol, 16>, p->cfg_split.smem));
+        }
     }
     cudaError_t e = cudaSuccess;
     auto chk = [&](cudaError_t x) { if (e == cudaSuccess) e = x; };
@@ -857,6 +950,13 @@ void launch_pass_t(const Plan *p, int pass, const void *rho_v, void *u_v, cudaSt
                 launch_conv_rr512_f32(W1, mult, hx, 0, 1, ny + 1, p->mult_full, twy, st);
                 return;
             }
+        }
+        if (p->split_conv) {
+            const PassCfg &cs = p->cfg_split;
+            k_conv_split<Pol, 16><<<2 * hx, cs.nthr, cs.smem, st>>>(
+                W1, mult, hx, ny + 1, p->sched_hf, p->sched_hi, static_cast<const tw *>(p->d_twh),
+                static_cast<const tw *>(p->d_twhi), twy, p->mult_full ? 1 : 0);
+            return;
         }
         with_emax(c, [&](auto E) {
             k_conv<Pol, E()><<<(hx + c.nl - 1) / c.nl, c.nthr, c.smem, st>>>(
@@ -1040,6 +1140,9 @@ bool pass_uses_rr(const Plan *p, int pass)
     return p->opt.precision == GSM_FP32 && p->rr_conv && p->M[axis] == 512;
 }
 
+// The split 2D conv has a fixed launch shape and half-length schedules of its own.
+bool pass_is_split(const Plan *p, int pass) { return p->d == 2 && pass == 1 && p->split_conv; }
+
 // Factorisations of M into radices 8, 4, 2, 5, 3 in the order fft_line runs
 // them, with at most one stage more than the default schedule; the default
 // first, at most `cap`.
@@ -1219,6 +1322,11 @@ gsm_status_t autotune_t(Plan *p, cudaStream_t st, std::string *report)
                 *report += buf;
                 continue;
             }
+        }
+        if (pass_is_split(p, pass)) {
+            snprintf(buf, sizeof(buf), "pass %d M=%d split into two halves on a CTA pair (fixed shape)\n", pass, M);
+            *report += buf;
+            continue;
         }
         // 1. the radix schedule, with the current launch shape
         if (!pass_uses_rr(p, pass)) {
@@ -1421,6 +1529,33 @@ gsm_status_t make_twiddles(Plan *p, int axis, cudaStream_t st)
         GSM_CUDA_TRY(cudaStreamSynchronize(st));
         release_table(p, old_f);
         if (old_i != old_f) release_table(p, old_i);
+    }
+    return GSM_OK;
+}
+
+gsm_status_t make_split_tables(Plan *p, cudaStream_t st)
+{
+    const int Mh = p->M[1] / 2;
+    if (!make_sched(Mh, &p->sched_hf)) {
+        set_error("half length of the split conv is not a product of 2, 3 and 5");
+        return GSM_ERR_UNSUPPORTED_SIZE;
+    }
+    // the inverse starts with the forward's last radix: fused with the multiplication
+    p->sched_hi = p->sched_hf;
+    p->sched_hi.r[0] = p->sched_hf.r[p->sched_hf.nst - 1];
+    for (int k = 0; k + 1 < p->sched_hf.nst; ++k) p->sched_hi.r[k + 1] = p->sched_hf.r[k];
+    const Sched *sc[2] = {&p->sched_hf, &p->sched_hi};
+    void **dst[2] = {&p->d_twh, &p->d_twhi};
+    for (int k = 0; k < 2; ++k) {
+        const size_t g8 = p->opt.precision == GSM_FP64 ? g8_table_doubles(*sc[k]) : 0;
+        if (k == 1 && g8 == 0) {   // without FMA-form constants one table serves both
+            p->d_twhi = p->d_twh;
+            break;
+        }
+        GSM_CUDA_TRY(dev_alloc(dst[k], cplx_bytes(p->opt.precision) * Mh + sizeof(double) * g8));
+        k_twiddles<<<(Mh + 255) / 256, 256, 0, st>>>(Mh, p->opt.precision, *dst[k]);
+        if (g8 > 0) launch_g8table(*sc[k], static_cast<double2 *>(*dst[k]) + Mh, st);
+        GSM_CUDA_TRY(cudaGetLastError());
     }
     return GSM_OK;
 }

@@ -578,6 +578,23 @@ def test_fp32x2_error_class(gsm):
     assert relmax(u2, oracle.Prepared("poisson2d", 1024, 16.0).run(rho2)) < 1e-13
 
 
+@pytest.mark.parametrize("precision", ["fp64", "fp32x2", "fp32"])
+@pytest.mark.parametrize("kernel,n,L", [("poisson2d", (40, 2048), 8.0), ("coulomb2d", (24, 4096), 6.0),
+                                        ("ds2d", (18, 2048), 4.0)])
+def test_split_conv_long_lines(gsm, kernel, n, L, precision):
+    """2D conv lines of padded length >= 4096 run as two half-length transforms
+    on a CTA pair (even and odd frequencies, summed through distributed shared
+    memory): against the oracle, and against the one-CTA-per-line kernel
+    (options.debug bit 1)."""
+    rho = np.random.default_rng(91).standard_normal(tuple(reversed(n)))
+    u, plan = run(gsm, kernel, rho, L, precision)
+    u1, _ = run(gsm, kernel, rho, L, precision, debug=2)
+    uo, _ = oracle.apply(kernel, rho, L, taylor_mode=1)
+    assert_rel(u, uo, tol(precision, plan), f"{kernel} split")
+    assert_rel(u1, uo, tol(precision, plan), f"{kernel} one CTA per line")
+    assert_rel(u, u1, tol(precision, plan), f"{kernel} split vs one CTA per line")
+
+
 @pytest.mark.parametrize("kernel", ["poisson2d", "coulomb2d"])
 def test_full_size_4096_square_parity(gsm, kernel):
     """2D at 4096^2 (M = 8192 lines, one per CTA) against the oracle and the
