@@ -584,15 +584,25 @@ def test_fp32x2_error_class(gsm):
 def test_split_conv_long_lines(gsm, kernel, n, L, precision):
     """2D conv lines of padded length >= 4096 run as two half-length transforms
     on a CTA pair (even and odd frequencies, summed through distributed shared
-    memory): against the oracle, and against the one-CTA-per-line kernel
-    (options.debug bit 1)."""
-    rho = np.random.default_rng(91).standard_normal(tuple(reversed(n)))
-    u, plan = run(gsm, kernel, rho, L, precision)
-    u1, _ = run(gsm, kernel, rho, L, precision, debug=2)
-    uo, _ = oracle.apply(kernel, rho, L, taylor_mode=1)
-    assert_rel(u, uo, tol(precision, plan), f"{kernel} split")
-    assert_rel(u1, uo, tol(precision, plan), f"{kernel} one CTA per line")
-    assert_rel(u, u1, tol(precision, plan), f"{kernel} split vs one CTA per line")
+    memory): against the oracle on the seeded mixture, and against the
+    one-CTA-per-line kernel (options.debug bit 1) on white noise too.
+
+    The ln r kernels compare with the oracle on a smooth density only: the
+    oracle's Gaussian sum and the plan's each meet the 1e-13 target on their
+    own samples but differ in S (209 and 207), so their potentials differ by
+    up to 2e-13/(2 pi) int |source| -- above 1e-12 of max|u| for white noise
+    (measured 2.1e-12, and 2.1e-11 for the d_xx source), far below it for
+    resolved densities.  Split and unsplit use the same sum."""
+    rho_mix = wl.mixture(n, L, wl.mixture2d_params())
+    rho_rnd = np.random.default_rng(91).standard_normal(tuple(reversed(n)))
+    for name, rho in (("mixture", rho_mix), ("white noise", rho_rnd)):
+        u, plan = run(gsm, kernel, rho, L, precision)
+        u1, _ = run(gsm, kernel, rho, L, precision, debug=2)
+        assert_rel(u, u1, tol(precision, plan), f"{kernel} {name} split vs one CTA per line")
+        if name == "mixture" or kernel == "coulomb2d":
+            uo, _ = oracle.apply(kernel, rho, L, taylor_mode=1)
+            assert_rel(u, uo, tol(precision, plan), f"{kernel} {name} split")
+            assert_rel(u1, uo, tol(precision, plan), f"{kernel} {name} one CTA per line")
 
 
 @pytest.mark.parametrize("kernel", ["poisson2d", "coulomb2d"])
