@@ -417,10 +417,53 @@ def main():
                                 "passes_ms": {PASS_NAMES_3D[p]: float(np.mean(pm_[p])) for p in range(npass)}}
                 vp_plan.destroy()
             result["variants"] = variants
+            result["tc_dft32_stage"] = tc_stage_measure(torch, gsm, n, stream, flush)
         print(json.dumps(result), flush=True)
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
+
+
+# ------------------------------------------------------------------ tensor-core DFT stage
+def tc_stage_measure(torch, gsm, n, stream, flush):
+    """The length-32 DFT stage of the conv pass's forward transforms (a
+    padded line of 2n = 512 as 16 x 32: (n + 1) 2n lines, 16 vectors of 32
+    each) three ways: on the tensor cores with FP64-class digit planes
+    (gsm_dft32_tc), and through the FFT engine in FP64 and in FP32x2
+    (gsm_fft_lines).  Errors against the FP64 engine's result."""
+    nvec = (n + 1) * 2 * n * (2 * n // 32)
+    torch.manual_seed(7)
+    x = torch.complex(torch.randn(nvec, 32, dtype=torch.float64, device=stream.device),
+                      torch.randn(nvec, 32, dtype=torch.float64, device=stream.device))
+    out = {"vectors": nvec, "bytes_in_out": 2 * x.numel() * 16}
+
+    def timed(fn, reps=5):
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+        with torch.cuda.stream(stream):
+            y = fn()
+            for e0, e1 in evs:
+                flush.zero_()
+                e0.record(stream)
+                y = fn()
+                e1.record(stream)
+        torch.cuda.synchronize()
+        return y, float(np.median([a.elapsed_time(b) for a, b in evs]))
+
+    ref, ms64 = timed(lambda: gsm.fft_lines(x, -1, "fp64", stream=stream))
+    res = {"fft_engine_fp64": {"ms": ms64}}
+    y2, ms2 = timed(lambda: gsm.fft_lines(x, -1, "fp32x2", stream=stream))
+    scale = float(ref.abs().max())
+    res["fft_engine_fp32x2"] = {"ms": ms2, "rel_err_vs_fp64": float((y2 - ref).abs().max()) / scale}
+    try:
+        yt, mst = timed(lambda: gsm.dft32_tc(x, -1, stream=stream))
+        res["tensor_core_digit_planes"] = {"ms": mst, "rel_err_vs_fp64": float((yt - ref).abs().max()) / scale,
+                                           "mma_tflops": nvec / 128 * 84 * 2 * 128 * 64 * 16 / (mst / 1e3) / 1e12}
+    except Exception as exc:                 # reported, not hidden
+        res["tensor_core_digit_planes"] = {"error": str(exc)}
+    out.update(res)
+    del x, ref, y2
+    torch.cuda.empty_cache()
+    return out
 
 
 # ------------------------------------------------------------------ config suite

@@ -390,6 +390,21 @@ gsm_status_t gsm_fft_lines(int M, int nlines, int sign, gsm_precision_t precisio
 gsm_status_t gsm_fft_lines_noalloc(int M, int nlines, int sign, gsm_precision_t precision,
                                    const double *in_dev, double *out_dev, void *cuda_stream);
 
+/* --- tensor-core DFT stage (measurement hook) ----------------------------------
+ * No counterpart in the paper.  Unnormalised DFT of length 32 of `nvec`
+ * contiguous vectors (device, interleaved complex double),
+ * exp(sign 2 pi i jk/32), sign = -1 or +1, computed on the tensor cores
+ * (tcgen05, bf16 operands, FP32 accumulation in tensor memory) with FP64-class
+ * accuracy: each vector is scaled by a power of two and split into six 8-bit
+ * digit planes, the DFT matrix likewise, and the 21 plane products that carry
+ * 48 bits are accumulated exactly and recombined in 64-bit integer arithmetic
+ * (the error-free splitting of Ozaki, Ogita, Oishi and Rump).  It exists to
+ * measure whether tensor-core DFT stages pay for the FP64-class passes (they
+ * do not replace any pass).  Allocates its 48 KB table and a status word from
+ * the stream-ordered pool and synchronises `cuda_stream` before it returns;
+ * GSM_ERR_TIMEOUT if the bounded wait for the tensor-core products ran out. */
+gsm_status_t gsm_dft32_tc(int nvec, int sign, const double *in_dev, double *out_dev, void *cuda_stream);
+
 /* --- failure-handling test hooks ----------------------------------------------
  * No counterpart in the paper.  Every device allocation the library makes goes
  * through one internal function that counts what is live.  These two calls let

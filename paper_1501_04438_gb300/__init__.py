@@ -389,6 +389,20 @@ def fft_lines(x, sign: int = -1, precision: str = "fp64", stream=None):
     return out
 
 
+def dft32_tc(x, sign: int = -1, stream=None):
+    """Unnormalised length-32 DFT of each row of a complex128 CUDA tensor of
+    shape (nvec, 32) on the tensor cores with FP64-class accuracy
+    (gsm_dft32_tc, a measurement hook)."""
+    torch = _torch()
+    if x.dtype != torch.complex128 or x.dim() != 2 or x.shape[1] != 32 or not x.is_cuda:
+        raise ValueError("x must be a (nvec, 32) complex128 CUDA tensor")
+    x = x.contiguous()
+    out = torch.empty_like(x)
+    _abi.check(_abi.load().gsm_dft32_tc(x.shape[0], sign, ctypes.c_void_p(x.data_ptr()),
+                                        ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream)))
+    return out
+
+
 def _autograd():
     from . import autograd as ag
     return ag

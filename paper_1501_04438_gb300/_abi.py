@@ -21,7 +21,7 @@ EXPORTS = ["gsm_default_options", "gsm_plan", "gsm_apply", "gsm_apply_pass", "gs
            "gsm_plan_gs_terms", "gsm_plan_kernel_tensor", "gsm_plan_factors", "gsm_fft_lines",
            "gsm_fft_lines_noalloc", "gsm_batch_create", "gsm_batch_launch", "gsm_batch_destroy",
            "gsm_plan_save", "gsm_plan_load", "gsm_debug_fail_alloc", "gsm_debug_alloc_stats",
-           "gsm_batch_wait", "gsm_debug_batch_wait", "gsm_plan_set_schedule"]
+           "gsm_batch_wait", "gsm_debug_batch_wait", "gsm_plan_set_schedule", "gsm_dft32_tc"]
 
 
 class Options(ctypes.Structure):
@@ -96,6 +96,7 @@ def load(path: str = LIB_PATH):
         L.gsm_plan_factors.argtypes = [_vp, ctypes.c_int, _dp, ctypes.c_size_t]
         L.gsm_fft_lines.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp, _vp, _vp]
         L.gsm_fft_lines_noalloc.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp, _vp, _vp]
+        L.gsm_dft32_tc.argtypes = [ctypes.c_int, ctypes.c_int, _vp, _vp, _vp]
         L.gsm_debug_fail_alloc.argtypes = [ctypes.c_int]
         L.gsm_debug_alloc_stats.argtypes = [ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ctypes.c_size_t)]
         for name in EXPORTS:

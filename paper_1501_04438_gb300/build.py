@@ -17,7 +17,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libgsm.so")
-SOURCES = ["gsm_api.cu", "gsm_plan.cu", "gsm_passes.cu", "gsm_conv_rr.cu"]
+SOURCES = ["gsm_api.cu", "gsm_plan.cu", "gsm_passes.cu", "gsm_conv_rr.cu", "gsm_tc.cu"]
 HEADERS = ["gsm_arith.cuh", "gsm_fft.cuh", "gsm_internal.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]

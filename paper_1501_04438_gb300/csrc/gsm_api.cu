@@ -1069,6 +1069,16 @@ gsm_status_t gsm_fft_lines_noalloc(int M, int nlines, int sign, gsm_precision_t 
                                     static_cast<cudaStream_t>(cuda_stream));
 }
 
+gsm_status_t gsm_dft32_tc(int nvec, int sign, const double *in_dev, double *out_dev, void *cuda_stream)
+{
+    if (!in_dev || !out_dev || nvec < 0 || (sign != 1 && sign != -1)) {
+        set_error("bad DFT arguments");
+        return GSM_ERR_INVALID_ARG;
+    }
+    if (nvec == 0) return GSM_OK;
+    return launch_dft32_tc(nvec, sign, in_dev, out_dev, static_cast<cudaStream_t>(cuda_stream));
+}
+
 gsm_status_t gsm_debug_fail_alloc(int k)
 {
     g_fail_in.store(k < 0 ? -1 : (long)k);

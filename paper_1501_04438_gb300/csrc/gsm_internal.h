@@ -164,6 +164,8 @@ gsm_status_t launch_fft_lines(int M, int nlines, int sign, gsm_precision_t prec,
                               const double *in, double *out, cudaStream_t st);
 gsm_status_t launch_fft_lines_noalloc(int M, int nlines, int sign, gsm_precision_t prec,
                                       const double *in, double *out, cudaStream_t st);
+// length-32 DFTs on the tensor cores (gsm_tc.cu); synchronises the stream
+gsm_status_t launch_dft32_tc(int nvec, int sign, const double *in, double *out, cudaStream_t st);
 // the twiddle tables of one axis for its current forward and inverse schedules
 // (frees the axis's previous tables unless another axis shares them)
 gsm_status_t make_twiddles(Plan *p, int axis, cudaStream_t st);
