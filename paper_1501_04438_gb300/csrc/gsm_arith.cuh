@@ -63,6 +63,17 @@ __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
     float bb = __fsub_rn(s, a);
     e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
 }
+// s + e == a + b exactly when the exponent of a is at least that of b
+// (Dekker's fast two-sum, three additions).  Renormalising a pair (hi, lo)
+// of the pair arithmetic: |lo| < |hi| except after a cancellation, and then
+// s is still a + b rounded and the error of s + e is below u |lo|, well under
+// the pair's own error bound, which is relative to the operands before the
+// cancellation.
+__device__ __forceinline__ void fast_two_sum(float a, float b, float &s, float &e)
+{
+    s = __fadd_rn(a, b);
+    e = __fsub_rn(b, __fsub_rn(s, a));
+}
 __device__ __forceinline__ df radd(df a, df b)
 {
     float s, e;
@@ -143,7 +154,10 @@ struct F64 {
     using io_t = double;
     static constexpr int kId = 0;
     static constexpr int kPadShift = 3;   // one pad element per 8 (128 bytes)
-    static constexpr bool kPrune = true;  // FP64-pipe bound: prune padded/cropped stages
+    // pruned first (zero-padded) and last (cropped) stages: they pay where the
+    // arithmetic pipe is the limit, FP64 here
+    static constexpr bool kPrune = true;       // x and y passes
+    static constexpr bool kPruneConv = true;   // conv pass
     __device__ static __forceinline__ cx<real> ld(const scplx &v) { return {v.x, v.y}; }
     __device__ static __forceinline__ scplx st(cx<real> a) { return make_double2(a.re, a.im); }
     __device__ static __forceinline__ cx<real> tw(const tw_t &v) { return {v.x, v.y}; }
@@ -162,6 +176,7 @@ struct F32 {
     static constexpr int kId = 1;
     static constexpr int kPadShift = 4;   // one pad element per 16 (128 bytes)
     static constexpr bool kPrune = false;
+    static constexpr bool kPruneConv = false;
     __device__ static __forceinline__ cx<real> ld(const scplx &v) { return {v.x, v.y}; }
     __device__ static __forceinline__ scplx st(cx<real> a) { return make_float2(a.re, a.im); }
     __device__ static __forceinline__ cx<real> tw(const tw_t &v) { return {v.x, v.y}; }
@@ -179,16 +194,18 @@ struct DF64 {
     using io_t = double;
     static constexpr int kId = 2;
     static constexpr int kPadShift = 3;
+    // pruning pays in the conv pass (measured 9 %); in the x and y passes,
+    // which wait on memory more than on arithmetic, it made them slower
     static constexpr bool kPrune = false;
+    static constexpr bool kPruneConv = true;
     __device__ static __forceinline__ cx<real> ld(const scplx &v) { return {df{v.x, v.y}, df{v.z, v.w}}; }
-    // stored values are renormalised (two-sum: exact whatever the order of
-    // |hi| and |lo|), so the unnormalised parts of the pair arithmetic only
-    // live within one stage
+    // stored values are renormalised, so the unnormalised parts of the pair
+    // arithmetic only live within one stage (fast_two_sum: see there)
     __device__ static __forceinline__ scplx st(cx<real> a)
     {
         float4 r;
-        two_sum(a.re.hi, a.re.lo, r.x, r.y);
-        two_sum(a.im.hi, a.im.lo, r.z, r.w);
+        fast_two_sum(a.re.hi, a.re.lo, r.x, r.y);
+        fast_two_sum(a.im.hi, a.im.lo, r.z, r.w);
         return r;
     }
     __device__ static __forceinline__ cx<real> tw(const tw_t &v) { return {df{v.x, v.y}, df{v.z, v.w}}; }

@@ -597,8 +597,9 @@ __host__ __device__ inline bool sched_sorted_from(const Sched &sc, int from)
 // is pruned, so the first radix must be even); the caller need not write it.
 // CROP: only the first half of the output is needed (the last stage is pruned
 // when its radix is even; the second half of the line is then left
-// undefined).  Both apply to policies with kPrune only; for the others the
-// full stages run and the caller writes the zeros.
+// undefined).  The caller chooses them per pass from the policy's kPrune
+// (x and y passes) and kPruneConv (conv pass); without them the full stages
+// run and the caller writes the zeros.
 // gt (FP64 only, may be NULL): the constants of the FMA-form stages
 // (fft_stage_fma), laid out as gtable_offset describes; with NULL every stage
 // takes the twiddle table tw.  Stages [st_begin, st_end) run (st_end < 0: to
@@ -609,8 +610,7 @@ __device__ __forceinline__ void fft_line(typename Pol::scplx *s, const Sched &sc
                                          const double *__restrict__ gt = nullptr, int st_begin = 0,
                                          int st_end = -1)
 {
-    // pruning pays where the arithmetic pipe is the limit: FP64 only
-    constexpr bool ZPAD = ZPAD_ && Pol::kPrune, CROP = CROP_ && Pol::kPrune;
+    constexpr bool ZPAD = ZPAD_, CROP = CROP_;
     const int M = sc.M, last = sc.nst - 1;
     const int nend = st_end < 0 ? sc.nst : st_end;   // stages [st_begin, nend) run
     int Ns = 1, st = st_begin;

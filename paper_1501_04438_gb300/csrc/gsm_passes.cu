@@ -94,7 +94,7 @@ __device__ __forceinline__ void body_xf(const typename Pol::io_t *__restrict__ r
         s[pidx<Pol>(x)] = Pol::st(cx<R>{a, b});
     }
     group_sync(g);
-    fft_line<Pol, true, EMAX, true, false>(s, sc, tw, g, g8_table<Pol>(tw, M));
+    fft_line<Pol, true, EMAX, Pol::kPrune, false>(s, sc, tw, g, g8_table<Pol>(tw, M));
     __syncthreads();
     // Z = A + iB with A, B the transforms of the two real rows:
     // 2A[k] = Z[k] + conj Z[-k], 2B[k] = -i (Z[k] - conj Z[-k]); the factor 2
@@ -143,7 +143,7 @@ __device__ __forceinline__ void body_yf(const S_t<Pol> *__restrict__ W1, S_t<Pol
         s[pidx<Pol>(y)] = v;
     }
     group_sync(g);
-    fft_line<Pol, true, EMAX, true, false>(s, sc, tw, g, g8_table<Pol>(tw, M));
+    fft_line<Pol, true, EMAX, Pol::kPrune, false>(s, sc, tw, g, g8_table<Pol>(tw, M));
     __syncthreads();
     const S_t<Pol> *s0 = reinterpret_cast<const S_t<Pol> *>(smem_raw);
     S_t<Pol> *out = W2 + (size_t)kx * M * nz;
@@ -185,7 +185,7 @@ __device__ __forceinline__ void body_conv(S_t<Pol> *__restrict__ W, const typena
     const int line = bx * nl + l;
     if (line >= nlines) return;   // the whole group leaves; no CTA barrier follows
     S_t<Pol> *w = W + (size_t)line * n;
-    for (int z = g.t; z < (Pol::kPrune ? n : M); z += g.T) {   // z >= n: zero padding
+    for (int z = g.t; z < (Pol::kPruneConv ? n : M); z += g.T) {   // z >= n: zero padding
         S_t<Pol> v = Pol::st(cx<R>{Pol::zero(), Pol::zero()});
         if (z < n) v = ldw<CG>(w + z);
         s[pidx<Pol>(z)] = v;
@@ -208,21 +208,21 @@ __device__ __forceinline__ void body_conv(S_t<Pol> *__restrict__ W, const typena
     if (fr != 0) {
         // forward up to its last stage; last forward stage, multiplication and
         // first inverse stage in registers; the rest of the inverse
-        fft_line<Pol, true, EMAX, true, false>(s, sc, tw, g, gt, 0, sc.nst - 1);
+        fft_line<Pol, true, EMAX, Pol::kPruneConv, false>(s, sc, tw, g, gt, 0, sc.nst - 1);
         if (fr == 8) fft_fused_mid<Pol, 8, (EMAX + 7) / 8>(s, sc, tw, g, gt, mult_of);
         else if (fr == 4) fft_fused_mid<Pol, 4, (EMAX + 3) / 4>(s, sc, tw, g, gt, mult_of);
         else if (fr == 2) fft_fused_mid<Pol, 2, (EMAX + 1) / 2>(s, sc, tw, g, gt, mult_of);
         else if (fr == 5) fft_fused_mid<Pol, 5, (EMAX + 4) / 5>(s, sc, tw, g, gt, mult_of);
         else fft_fused_mid<Pol, 3, (EMAX + 2) / 3>(s, sc, tw, g, gt, mult_of);
-        fft_line<Pol, false, EMAX, false, true>(s, sci, twi, g, gti, 1);
+        fft_line<Pol, false, EMAX, false, Pol::kPruneConv>(s, sci, twi, g, gti, 1);
     } else {
-        fft_line<Pol, true, EMAX, true, false>(s, sc, tw, g, gt);
+        fft_line<Pol, true, EMAX, Pol::kPruneConv, false>(s, sc, tw, g, gt);
         for (int k = g.t; k < M; k += g.T) {
             const int p = pidx<Pol>(k);
             s[p] = Pol::st(cscale(Pol::ld(s[p]), mult_of(k)));
         }
         group_sync(g);
-        fft_line<Pol, false, EMAX, false, true>(s, sci, twi, g, gti);
+        fft_line<Pol, false, EMAX, false, Pol::kPruneConv>(s, sci, twi, g, gti);
     }
     for (int z = g.t; z < n; z += g.T) w[z] = s[pidx<Pol>(z)];
 }
@@ -261,7 +261,7 @@ __device__ __forceinline__ void body_yi(const S_t<Pol> *__restrict__ W2, S_t<Pol
     }
     __syncthreads();
     const int z = z0 + l;
-    fft_line<Pol, false, EMAX, false, true>(s, sc, tw, g, g8_table<Pol>(tw, M));
+    fft_line<Pol, false, EMAX, false, Pol::kPrune>(s, sc, tw, g, g8_table<Pol>(tw, M));
     if (z < nz) {
         S_t<Pol> *out = W1 + ((size_t)z * hx + kx) * ny;
         for (int y = g.t; y < ny; y += g.T) out[y] = s[pidx<Pol>(y)];
@@ -309,7 +309,7 @@ __device__ __forceinline__ void body_xi(const S_t<Pol> *__restrict__ W1, typenam
         if (k > 0 && k < nx) s0[ll * LS + pidx<Pol>(M - k)] = Pol::st(cadd(cconj(A), cmul_posi(cconj(B))));
     }
     __syncthreads();
-    fft_line<Pol, false, EMAX, false, true>(s, sc, tw, g, g8_table<Pol>(tw, M));
+    fft_line<Pol, false, EMAX, false, Pol::kPrune>(s, sc, tw, g, g8_table<Pol>(tw, M));
     const int ya = y0 + 2 * l;
     typename Pol::io_t *slab = u + (size_t)z * ny * nx;
     for (int x = g.t; x < nx; x += g.T) {
