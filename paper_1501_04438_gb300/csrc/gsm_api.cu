@@ -140,6 +140,7 @@ static void free_plan(Plan *p)
     }
     if (p->d_twhi != p->d_twh) dev_free(p->d_twhi);
     dev_free(p->d_twh);
+    dev_free(p->d_twxh);
     dev_free(p->d_khat);
     if (p->d_mult != p->d_mult64) dev_free(p->d_mult);
     dev_free(p->d_mult64);

@@ -74,6 +74,12 @@ struct Plan {
     Sched sched_hf, sched_hi;
     void *d_twh = nullptr, *d_twhi = nullptr;   // tables of the half length
     PassCfg cfg_split;
+    // 2D x forward pass of padded length >= kSplitMinM: each line as two
+    // half-length transforms on two CTAs (k_xf_split)
+    bool split_x = false;
+    Sched sched_xh;                 // length M[0] / 2
+    void *d_twxh = nullptr;         // its tables
+    PassCfg cfg_xsplit;
 };
 
 // thread-local last error
@@ -175,6 +181,7 @@ bool make_sched(int M, Sched *s);
 constexpr int kSplitMinM = 4096;
 // the half-length schedules and tables of a split 2D conv (gsm_passes.cu)
 gsm_status_t make_split_tables(Plan *p, cudaStream_t st);
+gsm_status_t make_xsplit_tables(Plan *p, cudaStream_t st);
 // schedule with the given radices in the given order (each 8, 4, 2, 5 or 3,
 // product M); forward: the first radix must be even (the pruned first stage
 // of a zero-padded transform)

@@ -410,6 +410,52 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kMaxThreads)
     cl.sync();   // the peer has read this CTA's half: its shared memory may go
 }
 
+// ------------------------------------------------------------------ x forward, long 2D lines
+// An x line of padded length M = 2 Mh (two real rows as one complex line)
+// holds Mh = nx values and zeros, so, as for the split conv, its even and odd
+// frequencies are two transforms of length Mh, of x and of x w_M^n.  The
+// forward needs no exchange: the Hermitian split pairs Z[k] with Z[M - k],
+// which has the parity of k, so each CTA of a pair (rank = blockIdx.x & 1)
+// transforms its half and writes the frequencies k = 2 k' + rank itself.
+// Two lines of Mh per SM overlap each other's barrier-separated phases, where
+// one line of 2 Mh per CTA filled an SM alone.  (The x inverse stays one line
+// per CTA: split the same way, with the halves summed through distributed
+// shared memory as in the conv, it was no faster: 1.19 -> 1.21 ms in FP64 at
+// 4096^2.)  sc: length Mh; tw: its tables; twM: the M twiddles w_M^m.
+template <class Pol, int EMAX>
+__global__ void __launch_bounds__(kMaxThreads)
+    k_xf_split(const typename Pol::io_t *__restrict__ rho, S_t<Pol> *__restrict__ W1, int nx, int ny, int hx,
+               Sched sc, const typename Pol::tw_t *__restrict__ tw, const typename Pol::tw_t *__restrict__ twM)
+{
+    using R = typename Pol::real;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int rank = blockIdx.x & 1, ya = 2 * (blockIdx.x >> 1);
+    const int Mh = sc.M;   // == nx
+    const Group g = make_group(blockDim.x, 1);
+    S_t<Pol> *s = reinterpret_cast<S_t<Pol> *>(smem_raw);
+    for (int x = g.t; x < nx; x += g.T) {
+        R a = Pol::zero(), b = Pol::zero();
+        if (ya < ny) a = Pol::from_io(rho[(size_t)ya * nx + x]);
+        if (ya + 1 < ny) b = Pol::from_io(rho[(size_t)(ya + 1) * nx + x]);
+        cx<R> v{a, b};
+        if (rank) v = cmul(v, Pol::tw(twM[x]));   // x w_M^x: the odd frequencies
+        s[pidx<Pol>(x)] = Pol::st(v);
+    }
+    group_sync(g);
+    fft_line<Pol, true, EMAX>(s, sc, tw, g, g8_table<Pol>(tw, Mh));
+    // frequency k = 2 k' + rank sits at k' of this half; M - k at (Mh - k' - rank) mod Mh
+    const int nk = rank ? nx / 2 : nx / 2 + 1;   // k = 0 .. nx of this parity (nx is even)
+    for (int kp = threadIdx.x; kp < nk; kp += blockDim.x) {
+        const int k = 2 * kp + rank;
+        int km = Mh - kp - rank;
+        if (km == Mh) km = 0;
+        const cx<R> zk = Pol::ld(s[pidx<Pol>(kp)]);
+        const cx<R> zm = cconj(Pol::ld(s[pidx<Pol>(km)]));
+        if (ya < ny) W1[(size_t)k * ny + ya] = Pol::st(cadd(zk, zm));
+        if (ya + 1 < ny) W1[(size_t)k * ny + ya + 1] = Pol::st(cmul_negi(csub(zk, zm)));
+    }
+}
+
 // ------------------------------------------------------------------ FFT test hook
 template <class Pol, bool FWD, int EMAX>
 __global__ void __launch_bounds__(kMaxThreads) k_fft_hook(const double2 *__restrict__ in, double2 *__restrict__ out,
@@ -880,6 +926,15 @@ gsm_status_t configure_t(Plan *p)
             }
             GSM_CUDA_TRY(raise_smem(k_conv_split<Pol, 16>, p->cfg_split.smem));
         }
+        // the same for the x forward pass
+        p->split_x = p->M[0] >= kSplitMinM && p->M[0] == 2 * p->n[0] && (p->opt.debug & 2) == 0;
+        if (p->split_x) {
+            if (!make_cfg<Pol>(p->M[0] / 2, 1, 16, &p->cfg_xsplit)) {
+                set_error("no launch shape for the split x pass");
+                return GSM_ERR_UNSUPPORTED_SIZE;
+            }
+            GSM_CUDA_TRY(raise_smem(k_xf_split<Pol, 16>, p->cfg_xsplit.smem));
+        }
     }
     cudaError_t e = cudaSuccess;
     auto chk = [&](cudaError_t x) { if (e == cudaSuccess) e = x; };
@@ -930,6 +985,12 @@ void launch_pass_t(const Plan *p, int pass, const void *rho_v, void *u_v, cudaSt
             else launch_x_rr512_f32(true, W1, u, ny, nz, twx, st);
             return;
         }
+    }
+    if (pass == 0 && p->split_x) {
+        const PassCfg &c = p->cfg_xsplit;
+        const tw *twh = static_cast<const tw *>(p->d_twxh);
+        k_xf_split<Pol, 16><<<2 * ((ny + 1) / 2), c.nthr, c.smem, st>>>(rho, W1, nx, ny, hx, p->sched_xh, twh, twx);
+        return;
     }
     if (pass == 0) {
         const PassCfg &c = p->cfg_xf;
@@ -1141,7 +1202,10 @@ bool pass_uses_rr(const Plan *p, int pass)
 }
 
 // The split 2D conv has a fixed launch shape and half-length schedules of its own.
-bool pass_is_split(const Plan *p, int pass) { return p->d == 2 && pass == 1 && p->split_conv; }
+bool pass_is_split(const Plan *p, int pass)
+{
+    return p->d == 2 && ((pass == 1 && p->split_conv) || (pass == 0 && p->split_x));
+}
 
 // Factorisations of M into radices 8, 4, 2, 5, 3 in the order fft_line runs
 // them, with at most one stage more than the default schedule; the default
@@ -1530,6 +1594,21 @@ gsm_status_t make_twiddles(Plan *p, int axis, cudaStream_t st)
         release_table(p, old_f);
         if (old_i != old_f) release_table(p, old_i);
     }
+    return GSM_OK;
+}
+
+gsm_status_t make_xsplit_tables(Plan *p, cudaStream_t st)
+{
+    const int Mh = p->M[0] / 2;
+    if (!make_sched(Mh, &p->sched_xh)) {
+        set_error("half length of the split x pass is not a product of 2, 3 and 5");
+        return GSM_ERR_UNSUPPORTED_SIZE;
+    }
+    const size_t g8 = p->opt.precision == GSM_FP64 ? g8_table_doubles(p->sched_xh) : 0;
+    GSM_CUDA_TRY(dev_alloc(&p->d_twxh, cplx_bytes(p->opt.precision) * Mh + sizeof(double) * g8));
+    k_twiddles<<<(Mh + 255) / 256, 256, 0, st>>>(Mh, p->opt.precision, p->d_twxh);
+    if (g8 > 0) launch_g8table(p->sched_xh, static_cast<double2 *>(p->d_twxh) + Mh, st);
+    GSM_CUDA_TRY(cudaGetLastError());
     return GSM_OK;
 }
 

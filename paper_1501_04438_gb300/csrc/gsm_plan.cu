@@ -736,6 +736,10 @@ gsm_status_t build_plan_data(Plan *p, cudaStream_t st, const StoredPlanData *sto
         gsm_status_t s = make_split_tables(p, st);
         if (s != GSM_OK) return s;
     }
+    if (p->split_x) {
+        gsm_status_t s = make_xsplit_tables(p, st);
+        if (s != GSM_OK) return s;
+    }
     if (p->kind == GSM_DIPOLAR_3D && p->dip_axis < 0) {
         DipFull dp;
         for (int a = 0; a < 3; ++a) {

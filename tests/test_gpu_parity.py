@@ -580,12 +580,16 @@ def test_fp32x2_error_class(gsm):
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32x2", "fp32"])
 @pytest.mark.parametrize("kernel,n,L", [("poisson2d", (40, 2048), 8.0), ("coulomb2d", (24, 4096), 6.0),
-                                        ("ds2d", (18, 2048), 4.0)])
+                                        ("ds2d", (18, 2048), 4.0), ("coulomb2d", (10, 2160), 6.0),
+                                        ("poisson2d", (2048, 20), 8.0), ("coulomb2d", (2160, 12), 6.0),
+                                        ("coulomb2d", (2048, 2048), 6.0)])
 def test_split_conv_long_lines(gsm, kernel, n, L, precision):
-    """2D conv lines of padded length >= 4096 run as two half-length transforms
-    on a CTA pair (even and odd frequencies, summed through distributed shared
-    memory): against the oracle on the seeded mixture, and against the
-    one-CTA-per-line kernel (options.debug bit 1) on white noise too.
+    """2D lines of padded length >= 4096 run as two half-length transforms on
+    a CTA pair (even and odd frequencies; the conv sums the halves of its
+    inverse through distributed shared memory), in the conv (y) and in the x
+    forward pass: against the oracle on the seeded mixture, and against the
+    one-CTA-per-line kernels (options.debug bit 1) on white noise too.  The
+    cases include half lengths with radix-3 and radix-5 stages (2160).
 
     The ln r kernels compare with the oracle on a smooth density only: the
     oracle's Gaussian sum and the plan's each meet the 1e-13 target on their
