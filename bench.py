@@ -308,7 +308,9 @@ def main():
     dom = int(np.argmax(avg_pass))
     dom_name = PASS_NAMES_3D[dom]
     peaks = load_peaks()
+    # the driver's measured copy bandwidth; without that file the recipe's fallback figure
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    hbm_src = "of measured" if "hbm_gbs" in peaks else "of fallback"
     f_conv, b_conv = conv_pass_model(n, cbytes)
     f_app, b_app = apply_model(n, cbytes)
     if dom_name == "conv":
@@ -329,11 +331,12 @@ def main():
     roof["peak_source"] = ("FP64 pipe: 152 SMs x 2 FMA/clk x 2 flop x 2.07 GHz (recipe nominal 1.25 TFLOP/s); "
                            "measured DFMA probe 1.20 TFLOP/s at 2.0 GHz" if prec == "fp64" else
                            ("FP32 pipe nominal (double-float arithmetic)" if prec == "fp32x2" else
-                            "measured HBM copy, MEASURED_PEAKS.json"))
+                            ("measured HBM copy, MEASURED_PEAKS.json" if "hbm_gbs" in peaks else
+                             "fallback HBM figure 6.8 TB/s (no MEASURED_PEAKS.json)")))
     # the five passes as built move 12 (instead of 8) half-spectrum slabs
     b_5 = b_app + 4 * cbytes * (n + 1) * n * n
     hbm_whole = {"bytes_model": b_app, "achieved_gbs": b_app / (ms_per_step / 1e3) / 1e9, "peak_gbs": hbm_peak,
-                 "frac": b_app / (ms_per_step / 1e3) / 1e9 / hbm_peak, "peak_source": "of measured",
+                 "frac": b_app / (ms_per_step / 1e3) / 1e9 / hbm_peak, "peak_source": hbm_src,
                  "bytes_model_5pass": float(b_5), "frac_5pass": b_5 / (ms_per_step / 1e3) / 1e9 / hbm_peak}
 
     result = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
