@@ -53,6 +53,8 @@ def args_parse():
     ap.add_argument("--suite", action="store_true",
                     help="measure every config (one JSON line each) instead of the headline line")
     ap.add_argument("--configs", default="1,2,3,4,5", help="with --suite: which configs to run (comma list)")
+    ap.add_argument("--passes", default=None, metavar="KERNEL:PRECISION:N",
+                    help="time the passes of one tuned plan (e.g. poisson2d:fp64:4096) instead of the headline line")
     return ap.parse_args()
 
 
@@ -701,8 +703,39 @@ def run_suite(a):
         plan.destroy()
 
 
+def run_passes(a):
+    """One JSON line: the per-pass milliseconds (median of K steps, L2 flushed
+    between steps) of a tuned plan on seeded white noise, for profiling one
+    kernel set outside the headline workload."""
+    import torch
+    import paper_1501_04438_gb300 as gsm
+    kernel, prec, n = a.passes.split(":")
+    n = int(n)
+    d = 3 if kernel.endswith("3d") else 2
+    L = L_BOX if d == 3 else 16.0
+    dev = torch.device("cuda:0")
+    stream = torch.cuda.Stream(dev)
+    rho_h = np.random.default_rng(1).standard_normal((n,) * d)
+    dt = torch.float32 if prec == "fp32" else torch.float64
+    rho = torch.tensor(rho_h, dtype=dt, device=dev)
+    u = torch.empty_like(rho)
+    plan = gsm.Plan(kernel, L, n, precision=prec, stream=stream)
+    plan.autotune(stream=stream)
+    flush = torch.empty(512 * 2 ** 20 // 4, dtype=torch.float32, device=dev)
+    time_passes(torch, plan, rho, u, max(1, a.warmup), flush, stream)
+    _, pass_ms = time_passes(torch, plan, rho, u, a.steps, flush, stream)
+    info = plan.info()
+    print(json.dumps({"passes": f"{kernel} {prec} {n}^{d}", "steps": a.steps,
+                      "passes_ms": [float(np.median(x)) for x in pass_ms],
+                      "total_ms": float(sum(np.median(x) for x in pass_ms)),
+                      "radix_fwd": info["radix_fwd"], "radix_inv": info["radix_inv"]}))
+    plan.destroy()
+
+
 if __name__ == "__main__":
     if "--suite" in sys.argv:
         run_suite(args_parse())
+    elif "--passes" in sys.argv:
+        run_passes(args_parse())
     else:
         main()

@@ -99,9 +99,10 @@ typedef struct {
     int debug;                  /* 0; bit 0 set: FP32 plans use the shared-memory FFT engine
                                    in every pass even where the register-resident kernels
                                    apply (padded length 512); bit 1 set: 2D plans with a
-                                   padded y length >= 4096 transform each conv line on one
-                                   CTA instead of two half-length transforms on a CTA pair
-                                   (for comparisons; same results to rounding) */
+                                   padded y (x) length >= 4096 transform each conv (x
+                                   forward) line on one CTA instead of two half-length
+                                   transforms on a CTA pair (for comparisons; same results
+                                   to rounding) */
     double box[3];              /* rectangular box (Sec. 2.5, Eq. tensor_ani): if all
                                    d entries are > 0, axis a spans [-box[a], box[a]]
                                    and L is ignored; all 0 (default): [-L, L]^d.  The
