@@ -385,8 +385,20 @@ __global__ void __launch_bounds__(kMaxThreads) k_xi(const S_t<Pol> *__restrict__
 // overlap another's (one CTA per SM held a whole line of 8192 and left the
 // FP64 pipe idle during its shared-memory phases).  Schedules, tables:
 // length Mh (sched_hf, sched_hi, twh, twhi); twM: the M twiddles w_M^m.
+// A half line (at most 4096 values) takes at most 256 threads.  Three CTAs per
+// SM in FP64 and double-float (an 80-register cap: their butterfly arrays
+// partly spill, to L1) overlap the barrier-separated stages better than two:
+// measured 4.17 -> 4.16 ms (FP64) and 1.41 -> 1.34 ms (FP32x2) for the conv at
+// 4096^2.  FP32 keeps the engine's usual bound (a 256-thread bound made its
+// conv slower, 0.50 -> 0.53 ms, with or without the three CTAs).
+constexpr int kSplitThreads = 256;
+template <class Pol>
+constexpr int kSplitBoundThreads = std::is_same<Pol, F32>::value ? kMaxThreads : kSplitThreads;
+template <class Pol>
+constexpr int kSplitCtasPerSm = std::is_same<Pol, F32>::value ? 1 : 3;
+
 template <class Pol, int EMAX>
-__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kMaxThreads)
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kSplitBoundThreads<Pol>, kSplitCtasPerSm<Pol>)
     k_conv_split(S_t<Pol> *__restrict__ W, const typename Pol::mult_t *__restrict__ mult, int nlines, int ny1,
                  Sched sc, Sched sci, const typename Pol::tw_t *__restrict__ tw,
                  const typename Pol::tw_t *__restrict__ twi, const typename Pol::tw_t *__restrict__ twM, int full)
@@ -466,7 +478,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kMaxThreads)
 // shared memory as in the conv, it was no faster: 1.19 -> 1.21 ms in FP64 at
 // 4096^2.)  sc: length Mh; tw: its tables; twM: the M twiddles w_M^m.
 template <class Pol, int EMAX>
-__global__ void __launch_bounds__(kMaxThreads)
+__global__ void __launch_bounds__(kSplitBoundThreads<Pol>, kSplitCtasPerSm<Pol>)
     k_xf_split(const typename Pol::io_t *__restrict__ rho, S_t<Pol> *__restrict__ W1, int nx, int ny, int hx,
                Sched sc, const typename Pol::tw_t *__restrict__ tw, const typename Pol::tw_t *__restrict__ twM)
 {
@@ -963,7 +975,7 @@ gsm_status_t configure_t(Plan *p)
         // (options.debug bit 1 keeps one CTA per line, for comparisons)
         p->split_conv = p->M[1] >= kSplitMinM && (p->opt.debug & 2) == 0;
         if (p->split_conv) {
-            if (!make_cfg<Pol>(p->M[1] / 2, 1, 16, &p->cfg_split)) {
+            if (!make_cfg<Pol>(p->M[1] / 2, 1, 16, &p->cfg_split) || p->cfg_split.nthr > kSplitThreads) {
                 set_error("no launch shape for the split conv pass");
                 return GSM_ERR_UNSUPPORTED_SIZE;
             }
@@ -972,7 +984,7 @@ gsm_status_t configure_t(Plan *p)
         // the same for the x forward pass
         p->split_x = p->M[0] >= kSplitMinM && p->M[0] == 2 * p->n[0] && (p->opt.debug & 2) == 0;
         if (p->split_x) {
-            if (!make_cfg<Pol>(p->M[0] / 2, 1, 16, &p->cfg_xsplit)) {
+            if (!make_cfg<Pol>(p->M[0] / 2, 1, 16, &p->cfg_xsplit) || p->cfg_xsplit.nthr > kSplitThreads) {
                 set_error("no launch shape for the split x pass");
                 return GSM_ERR_UNSUPPORTED_SIZE;
             }
