@@ -253,8 +253,18 @@ __device__ __forceinline__ void body_conv(S_t<Pol> *__restrict__ W, const typena
     for (int z = g.t; z < n; z += g.T) w[z] = s[pidx<Pol>(z)];
 }
 
+// The double-float conv kernel with 8 elements per thread is compiled for
+// three resident CTAs of up to 256 threads per SM (an 85-register bound):
+// more warps to hide its stalls than at its natural 108 registers (measured
+// 1.54 -> 1.50 ms at 256^3).  Its launch shapes keep to 256 threads.
+template <class Pol>
+constexpr int conv_max_threads(int emax) { return (std::is_same<Pol, DF64>::value && emax == 8) ? 256 : kMaxThreads; }
+template <class Pol>
+constexpr int conv_min_ctas(int emax) { return (std::is_same<Pol, DF64>::value && emax == 8) ? 3 : 1; }
+
 template <class Pol, int EMAX>
-__global__ void __launch_bounds__(kMaxThreads) k_conv(S_t<Pol> *__restrict__ W, const typename Pol::mult_t *__restrict__ mult,
+__global__ void __launch_bounds__(conv_max_threads<Pol>(EMAX), conv_min_ctas<Pol>(EMAX))
+    k_conv(S_t<Pol> *__restrict__ W, const typename Pol::mult_t *__restrict__ mult,
                                                       int nlines, int n, int is3d, int My, int ny1, Sched sc,
                                                       Sched sci, int nl, int gthr,
                                                       const typename Pol::tw_t *__restrict__ tw,
@@ -923,10 +933,10 @@ size_t pass_smem(int M, int nl) { return (size_t)nl * line_stride<Pol>(M) * size
 inline int round32(int x) { return ((x + 31) / 32) * 32; }
 
 template <class Pol>
-bool make_cfg(int M, int nl, int emax, PassCfg *c)
+bool make_cfg(int M, int nl, int emax, PassCfg *c, int maxt = kMaxThreads)
 {
     const int gthr = std::max(32, round32((M + emax - 1) / emax));
-    if (gthr > kMaxThreads || nl < 1 || nl * gthr > kMaxThreads) return false;
+    if (gthr > maxt || nl < 1 || nl * gthr > maxt) return false;
     if (gthr > 32 && nl > 1 && nl > 15) return false;
     if (pass_smem<Pol>(M, nl) > 200 * 1024) return false;
     c->nl = nl;
@@ -940,12 +950,13 @@ bool make_cfg(int M, int nl, int emax, PassCfg *c)
 // Default shape before any tuning: 8 elements per thread when a line fits
 // 512 threads that way, else 16; as many lines as requested that fit.
 template <class Pol>
-PassCfg choose_cfg(int M, int nl_want)
+PassCfg choose_cfg(int M, int nl_want, bool conv = false)
 {
     PassCfg c;
     const int emax = (M <= 8 * kMaxThreads) ? 8 : 16;
+    const int maxt = conv ? conv_max_threads<Pol>(emax) : kMaxThreads;
     for (int nl = std::max(1, nl_want); nl >= 1; nl /= 2)
-        if (make_cfg<Pol>(M, nl, emax, &c)) return c;
+        if (make_cfg<Pol>(M, nl, emax, &c, maxt)) return c;
     make_cfg<Pol>(M, 1, 16, &c);
     return c;
 }
@@ -968,9 +979,9 @@ gsm_status_t configure_t(Plan *p)
     if (d == 3) {
         p->cfg_yf = choose_cfg<Pol>(p->M[1], cw);
         p->cfg_yi = p->cfg_yf;
-        p->cfg_conv = choose_cfg<Pol>(p->M[2], std::max(1, 4096 / p->M[2]));
+        p->cfg_conv = choose_cfg<Pol>(p->M[2], std::max(1, 4096 / p->M[2]), true);
     } else {
-        p->cfg_conv = choose_cfg<Pol>(p->M[1], std::max(1, 4096 / p->M[1]));
+        p->cfg_conv = choose_cfg<Pol>(p->M[1], std::max(1, 4096 / p->M[1]), true);
         // long lines: two half-length transforms per line on a cluster of two CTAs
         // (options.debug bit 1 keeps one CTA per line, for comparisons)
         p->split_conv = p->M[1] >= kSplitMinM && (p->opt.debug & 2) == 0;
@@ -1257,6 +1268,14 @@ bool pass_uses_rr(const Plan *p, int pass)
 }
 
 // The split 2D conv has a fixed launch shape and half-length schedules of its own.
+// Largest CTA of a pass's kernel for a shape with emax elements per thread.
+template <class Pol>
+int pass_max_threads(const Plan *p, int pass, int emax)
+{
+    const bool conv = p->d == 3 ? pass == 2 : pass == 1;
+    return conv ? conv_max_threads<Pol>(emax) : kMaxThreads;
+}
+
 bool pass_is_split(const Plan *p, int pass)
 {
     return p->d == 2 && ((pass == 1 && p->split_conv) || (pass == 0 && p->split_x));
@@ -1430,7 +1449,7 @@ gsm_status_t autotune_t(Plan *p, cudaStream_t st, std::string *report)
             std::lock_guard<std::mutex> lock(g_tune_mutex);
             PassCfg c;
             Sched a, b;
-            if (cache_lookup(cache, key, &cnl, &cem, &cf, &ci) && make_cfg<Pol>(M, cnl, cem, &c) &&
+            if (cache_lookup(cache, key, &cnl, &cem, &cf, &ci) && make_cfg<Pol>(M, cnl, cem, &c, pass_max_threads<Pol>(p, pass, cem)) &&
                 sched_parse(cf.c_str(), p->M[axis], true, &a) && sched_parse(ci.c_str(), p->M[axis], false, &b) &&
                 raise_pass_smem<Pol>(p, pass, c) == cudaSuccess) {
                 s = apply_axis_pair(p, axis, df ? a : p->sched_f[axis], di ? b : p->sched_i[axis], st);
@@ -1476,7 +1495,7 @@ gsm_status_t autotune_t(Plan *p, cudaStream_t st, std::string *report)
         for (int emax : {8, 16}) {
             for (int nl : nls) {
                 PassCfg c;
-                if (!make_cfg<Pol>(M, nl, emax, &c)) continue;
+                if (!make_cfg<Pol>(M, nl, emax, &c, pass_max_threads<Pol>(p, pass, emax))) continue;
                 if (raise_pass_smem<Pol>(p, pass, c) != cudaSuccess) continue;
                 *cfg = c;
                 const float ms = time_pass<Pol>(p, pass, rho, u, st, e0, e1, &e);
@@ -1857,7 +1876,7 @@ template <class Pol>
 gsm_status_t set_pass_shape_t(Plan *p, int pass, int nl, int emax)
 {
     PassCfg c;
-    if (!make_cfg<Pol>(pass_len(p, pass), nl, emax, &c)) {
+    if (!make_cfg<Pol>(pass_len(p, pass), nl, emax, &c, pass_max_threads<Pol>(p, pass, emax))) {
         set_error("launch shape not valid for this pass");
         return GSM_ERR_INVALID_ARG;
     }
