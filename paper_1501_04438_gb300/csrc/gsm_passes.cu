@@ -89,6 +89,16 @@ __device__ __forceinline__ const double *g8_table(const typename Pol::tw_t *tw, 
 // touch one line are done by its group; the transposed side of a pass is
 // done by the whole CTA, with one __syncthreads between it and the FFTs.
 
+// The double-float x and y kernels with 8 elements per thread are compiled
+// for four resident CTAs of up to 256 threads per SM (a 64-register bound):
+// more warps to hide their global-memory and barrier waits (measured at
+// 256^3: x forward 0.27 -> 0.25 ms, y inverse 0.53 -> 0.49, x inverse 0.29 ->
+// 0.25).  Their launch shapes keep to 256 threads.
+template <class Pol>
+constexpr int xy_max_threads(int emax) { return (std::is_same<Pol, DF64>::value && emax == 8) ? 256 : kMaxThreads; }
+template <class Pol>
+constexpr int xy_min_ctas(int emax) { return (std::is_same<Pol, DF64>::value && emax == 8) ? 4 : 1; }
+
 // ------------------------------------------------------------------ pass xf
 // Each pass is a __device__ body taking its tile (bx, by) explicitly, so that
 // the single-plan kernels and the grouped batch kernels share it.
@@ -135,7 +145,7 @@ __device__ __forceinline__ void body_xf(const typename Pol::io_t *__restrict__ r
 }
 
 template <class Pol, int EMAX>
-__global__ void __launch_bounds__(kMaxThreads) k_xf(const typename Pol::io_t *__restrict__ rho,
+__global__ void __launch_bounds__(xy_max_threads<Pol>(EMAX), xy_min_ctas<Pol>(EMAX)) k_xf(const typename Pol::io_t *__restrict__ rho,
                                                     S_t<Pol> *__restrict__ W1, int nx, int ny, int hx,
                                                     Sched sc, int nl, int gthr,
                                                     const typename Pol::tw_t *__restrict__ tw)
@@ -181,7 +191,7 @@ __device__ __forceinline__ void body_yf(const S_t<Pol> *__restrict__ W1, S_t<Pol
 }
 
 template <class Pol, int EMAX>
-__global__ void __launch_bounds__(kMaxThreads) k_yf(const S_t<Pol> *__restrict__ W1, S_t<Pol> *__restrict__ W2,
+__global__ void __launch_bounds__(xy_max_threads<Pol>(EMAX), xy_min_ctas<Pol>(EMAX)) k_yf(const S_t<Pol> *__restrict__ W1, S_t<Pol> *__restrict__ W2,
                                                     int ny, int nz, int hx, Sched sc, int nl, int gthr,
                                                     const typename Pol::tw_t *__restrict__ tw)
 {
@@ -312,7 +322,7 @@ __device__ __forceinline__ void body_yi(const S_t<Pol> *__restrict__ W2, S_t<Pol
 }
 
 template <class Pol, int EMAX>
-__global__ void __launch_bounds__(kMaxThreads) k_yi(const S_t<Pol> *__restrict__ W2, S_t<Pol> *__restrict__ W1,
+__global__ void __launch_bounds__(xy_max_threads<Pol>(EMAX), xy_min_ctas<Pol>(EMAX)) k_yi(const S_t<Pol> *__restrict__ W2, S_t<Pol> *__restrict__ W1,
                                                     int ny, int nz, int hx, Sched sc, int nl, int gthr,
                                                     const typename Pol::tw_t *__restrict__ tw)
 {
@@ -373,7 +383,7 @@ __device__ __forceinline__ void body_xi(const S_t<Pol> *__restrict__ W1, typenam
 }
 
 template <class Pol, int EMAX>
-__global__ void __launch_bounds__(kMaxThreads) k_xi(const S_t<Pol> *__restrict__ W1, typename Pol::io_t *__restrict__ u,
+__global__ void __launch_bounds__(xy_max_threads<Pol>(EMAX), xy_min_ctas<Pol>(EMAX)) k_xi(const S_t<Pol> *__restrict__ W1, typename Pol::io_t *__restrict__ u,
                                                     int nx, int ny, int hx, Sched sc, int nl, int gthr,
                                                     const typename Pol::tw_t *__restrict__ tw)
 {
@@ -954,7 +964,7 @@ PassCfg choose_cfg(int M, int nl_want, bool conv = false)
 {
     PassCfg c;
     const int emax = (M <= 8 * kMaxThreads) ? 8 : 16;
-    const int maxt = conv ? conv_max_threads<Pol>(emax) : kMaxThreads;
+    const int maxt = conv ? conv_max_threads<Pol>(emax) : xy_max_threads<Pol>(emax);
     for (int nl = std::max(1, nl_want); nl >= 1; nl /= 2)
         if (make_cfg<Pol>(M, nl, emax, &c, maxt)) return c;
     make_cfg<Pol>(M, 1, 16, &c);
@@ -1273,7 +1283,7 @@ template <class Pol>
 int pass_max_threads(const Plan *p, int pass, int emax)
 {
     const bool conv = p->d == 3 ? pass == 2 : pass == 1;
-    return conv ? conv_max_threads<Pol>(emax) : kMaxThreads;
+    return conv ? conv_max_threads<Pol>(emax) : xy_max_threads<Pol>(emax);
 }
 
 bool pass_is_split(const Plan *p, int pass)
