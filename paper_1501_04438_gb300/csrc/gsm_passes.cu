@@ -495,8 +495,10 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kSplitBoundThreads<P
 // Two lines of Mh per SM overlap each other's barrier-separated phases, where
 // one line of 2 Mh per CTA filled an SM alone.  (The x inverse stays one line
 // per CTA: split the same way, with the halves summed through distributed
-// shared memory as in the conv, it was no faster: 1.19 -> 1.21 ms in FP64 at
-// 4096^2.)  sc: length Mh; tw: its tables; twM: the M twiddles w_M^m.
+// shared memory as in the conv, it was no faster, 1.19 -> 1.21 ms in FP64 at
+// 4096^2; split by output parity, each CTA reading the whole half spectrum and
+// writing every other output, it was slower, 1.19 -> 1.27 ms.)  sc: length
+// Mh; tw: its tables; twM: the M twiddles w_M^m.
 template <class Pol, int EMAX>
 __global__ void __launch_bounds__(kSplitBoundThreads<Pol>, kSplitCtasPerSm<Pol>)
     k_xf_split(const typename Pol::io_t *__restrict__ rho, S_t<Pol> *__restrict__ W1, int nx, int ny, int hx,
