@@ -56,6 +56,14 @@ def test_status_strings_without_gpu(libpath):
     assert lib.gsm_plan(ctypes.byref(h), 0, 2, 1.0, n, 0.0, None, None) == 1   # wrong d
     assert lib.gsm_plan(ctypes.byref(h), 0, 3, -1.0, n, 0.0, None, None) == 1  # L <= 0
     assert b"L" in lib.gsm_last_error()
+    # batches: an empty one is a no-op; a negative count, NULL arrays or a bad
+    # handle are refused on the host before any CUDA call
+    assert lib.gsm_apply_batched(0, None, None, None, None) == 0
+    assert lib.gsm_apply_batched(-1, None, None, None, None) == 1
+    assert lib.gsm_apply_batched(2, None, None, None, None) == 1
+    plans = (ctypes.c_void_p * 1)(None)
+    arrs = (ctypes.c_void_p * 1)(None)
+    assert lib.gsm_apply_batched(1, plans, arrs, arrs, None) == 7
 
 
 def test_box_and_saved_plan_errors_without_gpu(libpath):
