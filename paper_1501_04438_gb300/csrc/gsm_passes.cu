@@ -730,9 +730,10 @@ __device__ __forceinline__ void queue_pass(const QueueArgs &a, const QueueItem &
 
 template <class Pol, int D>
 // Resident CTAs per SM asked of the compiler: FP64 and double-float 2 (a
-// 128-register cap), FP32 4 (64 registers; its tiles are short, and more
-// resident CTAs cover their ticket and acquire: measured 4 % faster than 3)
-__global__ void __launch_bounds__(32 * kBatchMaxLines, std::is_same<Pol, F32>::value ? 4 : 2)
+// 128-register cap), FP32 5 (51 registers; its tiles are short, and more
+// resident CTAs cover their ticket and acquire: measured 4 % faster with 4
+// than with 3, 2 % faster again with 5, slower with 6)
+__global__ void __launch_bounds__(32 * kBatchMaxLines, std::is_same<Pol, F32>::value ? 5 : 2)
     k_batch_queue(const __grid_constant__ QueueArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
