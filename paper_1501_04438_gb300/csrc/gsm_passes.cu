@@ -145,10 +145,9 @@ __device__ __forceinline__ void body_xf(const typename Pol::io_t *__restrict__ r
 }
 
 template <class Pol, int EMAX>
-__global__ void __launch_bounds__(xy_max_threads<Pol>(EMAX), xy_min_ctas<Pol>(EMAX)) k_xf(const typename Pol::io_t *__restrict__ rho,
-                                                    S_t<Pol> *__restrict__ W1, int nx, int ny, int hx,
-                                                    Sched sc, int nl, int gthr,
-                                                    const typename Pol::tw_t *__restrict__ tw)
+__global__ void __launch_bounds__(xy_max_threads<Pol>(EMAX), xy_min_ctas<Pol>(EMAX))
+    k_xf(const typename Pol::io_t *__restrict__ rho, S_t<Pol> *__restrict__ W1, int nx, int ny, int hx,
+         Sched sc, int nl, int gthr, const typename Pol::tw_t *__restrict__ tw)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     body_xf<Pol, EMAX>(rho, W1, nx, ny, hx, sc, nl, gthr, tw, blockIdx.x, blockIdx.y, smem_raw);
@@ -191,9 +190,9 @@ __device__ __forceinline__ void body_yf(const S_t<Pol> *__restrict__ W1, S_t<Pol
 }
 
 template <class Pol, int EMAX>
-__global__ void __launch_bounds__(xy_max_threads<Pol>(EMAX), xy_min_ctas<Pol>(EMAX)) k_yf(const S_t<Pol> *__restrict__ W1, S_t<Pol> *__restrict__ W2,
-                                                    int ny, int nz, int hx, Sched sc, int nl, int gthr,
-                                                    const typename Pol::tw_t *__restrict__ tw)
+__global__ void __launch_bounds__(xy_max_threads<Pol>(EMAX), xy_min_ctas<Pol>(EMAX))
+    k_yf(const S_t<Pol> *__restrict__ W1, S_t<Pol> *__restrict__ W2, int ny, int nz, int hx, Sched sc,
+         int nl, int gthr, const typename Pol::tw_t *__restrict__ tw)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     body_yf<Pol, EMAX>(W1, W2, ny, nz, hx, sc, nl, gthr, tw, blockIdx.x, blockIdx.y, smem_raw);
@@ -322,9 +321,9 @@ __device__ __forceinline__ void body_yi(const S_t<Pol> *__restrict__ W2, S_t<Pol
 }
 
 template <class Pol, int EMAX>
-__global__ void __launch_bounds__(xy_max_threads<Pol>(EMAX), xy_min_ctas<Pol>(EMAX)) k_yi(const S_t<Pol> *__restrict__ W2, S_t<Pol> *__restrict__ W1,
-                                                    int ny, int nz, int hx, Sched sc, int nl, int gthr,
-                                                    const typename Pol::tw_t *__restrict__ tw)
+__global__ void __launch_bounds__(xy_max_threads<Pol>(EMAX), xy_min_ctas<Pol>(EMAX))
+    k_yi(const S_t<Pol> *__restrict__ W2, S_t<Pol> *__restrict__ W1, int ny, int nz, int hx, Sched sc,
+         int nl, int gthr, const typename Pol::tw_t *__restrict__ tw)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     body_yi<Pol, EMAX>(W2, W1, ny, nz, hx, sc, nl, gthr, tw, blockIdx.x, blockIdx.y, smem_raw);
@@ -383,9 +382,9 @@ __device__ __forceinline__ void body_xi(const S_t<Pol> *__restrict__ W1, typenam
 }
 
 template <class Pol, int EMAX>
-__global__ void __launch_bounds__(xy_max_threads<Pol>(EMAX), xy_min_ctas<Pol>(EMAX)) k_xi(const S_t<Pol> *__restrict__ W1, typename Pol::io_t *__restrict__ u,
-                                                    int nx, int ny, int hx, Sched sc, int nl, int gthr,
-                                                    const typename Pol::tw_t *__restrict__ tw)
+__global__ void __launch_bounds__(xy_max_threads<Pol>(EMAX), xy_min_ctas<Pol>(EMAX))
+    k_xi(const S_t<Pol> *__restrict__ W1, typename Pol::io_t *__restrict__ u, int nx, int ny, int hx,
+         Sched sc, int nl, int gthr, const typename Pol::tw_t *__restrict__ tw)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     body_xi<Pol, EMAX>(W1, u, nx, ny, hx, sc, nl, gthr, tw, blockIdx.x, blockIdx.y, smem_raw);
